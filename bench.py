@@ -1,0 +1,362 @@
+"""Throughput of the single-pass AMR raycaster on one GB300 (or N, one process per GPU).
+
+A step is one frame: every pixel's ray is traversed through the kD-tree leaves and
+sampled, shaded and composited (the whole hot path), on the cosmology-like 5-level
+hierarchy (2,219 patches, 1.33e8 cells, 602 MB of FP32 bricks) at 2048x2048 with
+central-difference Phong shading.  The hierarchy, tree and bricks are built once before
+timing (the paper's preprocessing).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank renders its own view (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gsamples/s and frames/s at 2048² (fraction of HBM roofline); learned-skip speedup at PSNR≥45 dB"
+UNIT = "Gsamples/s"
+SIZE = 2048
+BYTES_PER_SAMPLE = {0: 32, 1: 224}  # trilinear stencil, x7 with the six gradient stencils
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _march_sha() -> str:
+    h = hashlib.sha1()
+    for f in ("march.cuh", "march_launch.cuh", "amr_device.h"):
+        with open(os.path.join(ROOT, "paper_1212_3333_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def _profiled_traffic(shade: int, storage: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "march_c2_traffic.md")
+    if not os.path.exists(path):
+        return None
+    sha = _march_sha()
+    for line in open(path):
+        parts = line.strip().split("|")
+        parts = [p.strip() for p in parts if p.strip()]
+        if len(parts) >= 5 and parts[0] == sha and parts[1] == storage and parts[2] == str(shade):
+            try:
+                return float(parts[4])
+            except ValueError:
+                return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) > 8:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def _max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(hier, cam, tf, vmin, vmax, shade, budget_s=15.0, seed=0):
+    """The FP64 oracle, as it stands, on a bounded random sample of the same frame's
+    pixels; returns samples/s and how the sample was taken."""
+    import oracle
+
+    o = oracle.Oracle(hier)
+    op = oracle.OracleParams(vmin=vmin, vmax=vmax, shade=shade)
+    threads = oracle.max_threads()
+    rng = np.random.default_rng(seed)
+    n = 64
+    total_s, total_samples, total_pix = 0.0, 0, 0
+    while total_s < budget_s:
+        pix = np.stack([rng.integers(0, cam.width, n), rng.integers(0, cam.height, n)], 1)
+        t = time.perf_counter()
+        _, smp = o.render(cam, tf, op, pixels=pix.astype(np.int32))
+        dt = time.perf_counter() - t
+        total_s += dt
+        total_samples += int(smp.sum())
+        total_pix += n
+        if dt < budget_s / 8:
+            n *= 2
+    return {"value": total_samples / total_s / 1e9, "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": f"{total_pix} seeded random pixels of the {cam.width}x{cam.height} frame "
+                      f"({total_samples} samples, {total_s:.1f} s), FP64 oracle, {threads} threads"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import synth
+
+    hier = synth.make_c2(device="cpu")
+    vmin, vmax = synth.amr.percentile_range(hier)
+    cam = synth.orbit_camera(2, SIZE, SIZE)
+    tf = synth.ramp_tf()
+    vals = []
+    cb = None
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(hier, cam, tf, vmin, vmax, args.shade,
+                          budget_s=max(2.0, 60.0 / (args.warmup + args.steps)), seed=s)
+        if s >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(hier, args, "oracle"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(hier, args, storage):
+    return {"workload": (f"c2: lognormal 5-level AMR, {hier.num_patches} patches, "
+                         f"{hier.n_cells():.3g} FP32 cells; {SIZE}x{SIZE} view; "
+                         f"{'Phong' if args.shade else 'unshaded'} trilinear; step 0.5 h^l; "
+                         f"ERT eps {args.ert}"),
+            "storage": storage, "image": [SIZE, SIZE], "shade": args.shade,
+            "l2": "inputs larger than L2: 602 MB of bricks vs 129 MB L2, no flush"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="ptr",
+                    choices=["ptr", "texobj", "atlas_linear", "atlas_tex3d"])
+    ap.add_argument("--shade", type=int, default=1)
+    ap.add_argument("--ert", type=float, default=1e-4)
+    ap.add_argument("--compare", type=int, default=1, help="time every storage briefly")
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    world, rank, local = _dist()
+    import torch
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_1212_3333_gb300 as amr
+    import synth
+
+    hier = synth.make_c2(device="cuda")
+    vmin, vmax = synth.amr.percentile_range(hier)
+    cam = synth.orbit_camera(2 + rank, SIZE, SIZE)   # each rank its own view
+    tf_h = synth.ramp_tf()
+    tf = torch.as_tensor(tf_h, device="cuda")
+    ctx = amr.from_hierarchy(hier)
+    t0 = time.perf_counter()
+    ctx.amr_build_kdtree(args.storage)
+    build_s = time.perf_counter() - t0
+    st = ctx.amr_get_stats()
+    params = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
+    out = torch.empty((SIZE, SIZE, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    samples = ctx.amr_render(cam, tf, params, out, count_samples=True)  # also checks status
+    for _ in range(args.warmup):
+        ctx.amr_render(cam, tf, params, out)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    _barrier(world)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for k in range(args.steps):
+        starts[k].record(stream)
+        ctx.amr_render(cam, tf, params, out)
+        ends[k].record(stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    clk = clocks.stop() if clocks else None
+    total_ms = g0.elapsed_time(g1)
+    kern_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms = _max_over_ranks(world, total_ms)
+    all_samples = _sum_over_ranks(world, float(samples)) * args.steps
+    ms_per_step = total_ms / args.steps
+    value = all_samples / (total_ms * 1e-3) / 1e9
+    fps = 1e3 / ms_per_step
+
+    # end to end through the public API with host buffers: TF in, image out, every step
+    tf_pin = torch.as_tensor(tf_h).pin_memory()
+    img_pin = torch.empty((SIZE, SIZE, 4), dtype=torch.float32).pin_memory()
+    ctx.amr_render_host(cam, tf_pin, params, img_pin)
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.amr_render_host(cam, tf_pin, params, img_pin)
+    e2e_s = _max_over_ranks(world, time.perf_counter() - e0)
+    e2e = {"value": all_samples / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(tf_h.nbytes), "d2h_bytes_per_step": int(img_pin.numel() * 4)}
+
+    if rank != 0:
+        return
+    peak, peak_kind = _peaks()
+    bps = BYTES_PER_SAMPLE[args.shade]
+    achieved = samples * bps / (kern_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": _profiled_traffic(args.shade, args.storage),
+            "peak_kind": peak_kind, "bytes_per_sample": bps,
+            "kernel": "march_kernel<storage, trilinear, phong>",
+            "kernel_ms": kern_ms}
+    extra = {"frames_per_s": fps, "samples_per_frame": samples, "build_s": build_s,
+             "tree": {"nodes": st.num_nodes, "leaves": st.num_leaves, "depth": st.max_depth,
+                      "brick_mb": st.brick_bytes / 1e6}}
+    if args.compare:
+        comp = {}
+        for s in ("ptr", "texobj", "atlas_linear", "atlas_tex3d"):
+            c2 = amr.from_hierarchy(hier)
+            c2.amr_build_kdtree(s)
+            for shade in (0, 1):
+                p2 = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=shade, ert_eps=args.ert)
+                n2 = c2.amr_render(cam, tf, p2, out, count_samples=True)
+                for _ in range(2):
+                    c2.amr_render(cam, tf, p2, out)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(3):
+                    c2.amr_render(cam, tf, p2, out)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / 3
+                comp[f"{s}/{'phong' if shade else 'plain'}"] = {
+                    "gsamples_s": n2 / ms / 1e6, "ms": ms,
+                    "frac_hbm": n2 * BYTES_PER_SAMPLE[shade] / (ms * 1e-3) / 1e9 / peak}
+            if s == "atlas_linear":
+                s2 = c2.amr_get_stats()
+                extra["atlas"] = {"dims": list(s2.atlas_dims), "efficiency": s2.atlas_efficiency,
+                                  "efficiency_with_halo": s2.atlas_efficiency_halo}
+            c2.amr_destroy()
+        extra["storages"] = comp
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(hier, args, args.storage), "gpu_launches": args.steps,
+            "e2e": e2e, "roofline": roof, "clocks": clk, "extra": extra}
+    if args.cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(hier, cam, tf_h, vmin, vmax, args.shade)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

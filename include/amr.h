@@ -1,0 +1,184 @@
+/*
+ * amr.h - C ABI of the GB300 single-pass raycaster for structured AMR data.
+ *
+ * Method: Kaehler & Abel, "Single-Pass GPU-Raycasting for Structured Adaptive Mesh
+ * Refinement Data" (arXiv 1212.3333).  The library partitions overlapping AMR patches
+ * into a kD-tree of non-overlapping, single-level leaves (Sec. 3.1), stores one brick per
+ * patch (Sec. 4), and marches every pixel's ray front to back through the leaves with
+ * kd-restart (Sec. 3.3), sampling each leaf at a step proportional to its level's cell
+ * size, with trilinear interpolation, optional gradient Phong shading across block
+ * boundaries (Sec. 4, Fig. 6) and emission-absorption compositing (Sec. 3, Sec. 5).
+ *
+ * Conventions
+ *   - Every call returns an amr_status; nothing aborts or exits.  amr_last_error() gives
+ *     a message for the last failing call on a context (per context, not thread-safe:
+ *     use one context per thread at a time).
+ *   - Level l has spacing h^l = h^0 / r^l per axis (Sec. 2).  Patch boxes are int64[6]
+ *     {lo_x, lo_y, lo_z, hi_x, hi_y, hi_z}, half-open, in level-l cell indices.  Level 0
+ *     must tile its bounding box (the kD root, Sec. 3.1); same-level patches must be
+ *     disjoint; every patch must lie inside the root.
+ *   - Cell data is one float32 per cell, x fastest: index i + nx*(j + ny*k).
+ *   - Tree coordinates are int32 cells of the finest level (L-1).
+ *   - Device pointers are plain CUDA device addresses (e.g. torch tensor data_ptr());
+ *     streams are cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - The context owns every device allocation it makes; outputs and streams belong to
+ *     the caller.  Rendering is asynchronous on the given stream.
+ */
+#ifndef AMR_H
+#define AMR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amr_ctx amr_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  AMR_OK = 0,
+  AMR_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, bad box, bad enum) */
+  AMR_ERR_OVERLAP = 2,    /* two patches of one level overlap */
+  AMR_ERR_NOT_TILED = 3,  /* level 0 does not tile its bounding box */
+  AMR_ERR_STATE = 4,      /* call out of order (e.g. render before build) */
+  AMR_ERR_OOM = 5,        /* host or device allocation failed */
+  AMR_ERR_CUDA = 6,       /* a CUDA runtime call failed */
+  AMR_ERR_CAPACITY = 7,   /* a bounded device loop hit its limit (segments, samples) */
+  AMR_ERR_DEVICE = 8      /* the device reported an inconsistent structure */
+} amr_status;
+
+typedef enum { AMR_F32 = 0, AMR_F16 = 1, AMR_BF16 = 2 } amr_dtype;
+
+/* Brick storage strategies (Sec. 4).  The paper's GL designs are a packed memory-pool
+ * texture (Sec. 4.1) and bindless texture handles (Sec. 4.2); these are their CUDA
+ * counterparts. */
+typedef enum {
+  AMR_STORE_PTR = 0,          /* per-patch table of device pointers into one brick pool */
+  AMR_STORE_TEXOBJ = 1,       /* per-patch table of cudaTextureObject_t, one 3D array each */
+  AMR_STORE_ATLAS_LINEAR = 2, /* NFDH-packed atlas (Sec. 4.1) in linear device memory */
+  AMR_STORE_ATLAS_TEX3D = 3   /* NFDH-packed atlas in one 3D cudaArray, read as a texture */
+} amr_storage;
+
+/* Pinhole camera.  Pixel (i, j), row 0 at the top, has the ray o = eye,
+ * d = fwd + u*right + v*up with u = (2(i+0.5)/W - 1) * tan_half_fov_y * W/H and
+ * v = (1 - 2(j+0.5)/H) * tan_half_fov_y (d is not normalised). */
+typedef struct {
+  double eye[3], fwd[3], right[3], up[3];
+  double tan_half_fov_y;
+  int32_t width, height;
+} amr_camera;
+
+typedef enum { AMR_INTERP_NEAREST = 0, AMR_INTERP_TRILINEAR = 1 } amr_interp;
+
+typedef struct {
+  double step_factor; /* sample step = step_factor * h^l of the leaf's level (Sec. 3.3) */
+  double kappa;       /* extinction scale: sigma = kappa * alpha_TF (world^-1) */
+  double ert_eps;     /* early ray termination once A >= 1 - ert_eps; <= 0 disables */
+  double vmin, vmax;  /* value range mapped onto the transfer function */
+  double ka, kd, ks, shininess; /* headlight Phong constants (shade = 1) */
+  double gamma;       /* gradient floor: n = g / max(|g|, gamma (vmax-vmin) / h^l) */
+  int32_t interp;     /* amr_interp */
+  int32_t shade;      /* 0: unshaded, 1: central-difference gradient Phong (Sec. 4, Fig. 6) */
+  int32_t row0;       /* first image row to render (band partitioning); 0 for all */
+  int32_t rows;       /* number of rows; <= 0: all rows from row0 */
+  int32_t skip;       /* 0: none; 1: exact leaf min/max empty-space skipping */
+  int32_t max_segments; /* per-ray segment bound; <= 0: 4 * nodes + 64 */
+} amr_render_params;
+
+/* Fills p with the defaults: step 0.5, kappa 8, ert_eps 1e-4, vmin 0, vmax 1, ka 0.3,
+ * kd 0.6, ks 0.3, shininess 32, gamma 1e-3, trilinear, unshaded, all rows, no skip. */
+void amr_default_params(amr_render_params* p);
+
+/* Create a context from an AMR hierarchy (Sec. 2: h^l = h^0 / r^l, patches Gamma^l_m).
+ *   num_levels    L >= 1;  refine_ratio r >= 2 (constant, as in the paper's notation)
+ *   domain_lo[3]  world position of level-0 cell index 0;  h0[3] level-0 spacing
+ *   num_patches   P >= 1;  patch_level[P] in [0, L);  patch_box[6P] as above
+ *   cell_data[P]  host pointers, float32, x fastest; copied (the caller keeps ownership)
+ *   dtype         device storage type of the bricks (AMR_F32; F16/BF16 halve the bytes)
+ * Returns AMR_ERR_ARG for malformed input; tiling and overlaps are checked at build. */
+amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double domain_lo[3],
+                      const double h0[3], int32_t num_patches, const int32_t* patch_level,
+                      const int64_t* patch_box, const float* const* cell_data,
+                      amr_dtype dtype, amr_ctx** out);
+
+/* Build the kD-tree (Sec. 3.1: min-crossing planes, balanced tie-break, level-by-level
+ * refinement), the per-patch bricks with a one-cell halo (Sec. 4: one brick per subgrid),
+ * the chosen storage (Sec. 4.1 packing / 4.2 handle table) and upload everything on
+ * `cuda_stream`.  The call returns after the uploads complete. */
+amr_status amr_build_kdtree(amr_ctx* ctx, amr_storage storage, void* cuda_stream);
+
+/* Host-only part of amr_build_kdtree (tree, bricks, packing), for inspecting the tree
+ * without a GPU.  amr_build_kdtree may follow it (it then only uploads). */
+amr_status amr_build_host(amr_ctx* ctx, amr_storage storage);
+
+/* Render one image (Sec. 3.3 ray traversal, Sec. 3 compositing) into out_rgba_dev:
+ * caller-owned device float32 [rows][W][4], premultiplied RGBA, row 0 = image row row0.
+ * tf_rgba_dev: device float32 [tf_n][4] (2 <= tf_n <= 2048), linear between entries over
+ * [vmin, vmax].  Both device buffers must be 16-byte aligned.  Asynchronous on cuda_stream.  samples_out (nullable, host): when given,
+ * the call synchronises the stream, checks the device status word and stores the exact
+ * number of samples taken (sum over segments of the per-segment sample count). */
+amr_status amr_render(amr_ctx* ctx, const amr_camera* cam, const float* tf_rgba_dev,
+                      int32_t tf_n, const amr_render_params* params, float* out_rgba_dev,
+                      void* cuda_stream, uint64_t* samples_out);
+
+/* amr_render with host buffers: copies tf_rgba_host to the device, renders, copies the
+ * image back to out_rgba_host ([rows][W][4] float32) and synchronises.  Page-locked host
+ * buffers make the copies asynchronous with respect to other streams. */
+amr_status amr_render_host(amr_ctx* ctx, const amr_camera* cam, const float* tf_rgba_host,
+                           int32_t tf_n, const amr_render_params* params, float* out_rgba_host,
+                           void* cuda_stream, uint64_t* samples_out);
+
+/* Release the context and every device allocation it owns (NULL-safe). */
+amr_status amr_destroy(amr_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none; ctx may be NULL for a failed
+ * amr_create, which reports through a process-wide slot). */
+const char* amr_last_error(const amr_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------- */
+/* inspection and test hooks                                                            */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct {
+  int64_t num_nodes, num_leaves, num_patches, num_cells;
+  int64_t brick_bytes;      /* device bytes of cell data incl. halos (all storages) */
+  int64_t tree_bytes;       /* device bytes of nodes + leaves + patch table */
+  int32_t atlas_dims[3];    /* atlas extent in texels (atlas storages), else 0 */
+  double atlas_efficiency;  /* cells / atlas texels (halos excluded), atlas storages */
+  double atlas_efficiency_halo; /* brick texels incl. halos / atlas texels */
+  double build_seconds;     /* host build time (tree + bricks + packing) */
+  int32_t max_depth;        /* deepest leaf (root = 0) */
+  int32_t storage;          /* amr_storage in use, -1 before build */
+} amr_stats;
+
+amr_status amr_get_stats(const amr_ctx* ctx, amr_stats* out);
+
+/* Leaves in canonical order (pre-order over the tree): box int32[6*n] in finest cells,
+ * patch id, level.  cap = capacity in leaves; *n receives the leaf count (also when cap
+ * is too small, which returns AMR_ERR_CAPACITY). */
+amr_status amr_get_leaves(const amr_ctx* ctx, int32_t* box6, int32_t* patch, int32_t* level,
+                          int64_t cap, int64_t* n);
+
+/* Nodes in pre-order: axis (-1 for a leaf), split plane (finest cells), pre-order ids of
+ * the two children (-1 for a leaf), leaf id (-1 for an internal node). */
+amr_status amr_get_nodes(const amr_ctx* ctx, int32_t* axis, int32_t* split, int32_t* left,
+                         int32_t* right, int32_t* leaf, int64_t cap, int64_t* n);
+
+/* The host brick of patch p with its one-cell halo: float32 [(nz+2)][(ny+2)][(nx+2)],
+ * brick index b = level cell c - lo + 1.  cap in floats; *n receives the brick size. */
+amr_status amr_get_brick(const amr_ctx* ctx, int32_t patch, float* out, int64_t cap,
+                         int64_t* n);
+
+/* Per-pixel traversal (Sec. 3.3 kd-restart) on the device: for pixel (i, j) with
+ * p = j*W + i, leaf_seq_dev[p*max_len + k] is the k-th leaf id, t_seq_dev (nullable)
+ * [p*max_len + k][2] its entry/exit ray parameters (float64), seq_len_dev[p] the number
+ * of segments (0 for a miss, -1 when more than max_len).  All device buffers. */
+amr_status amr_trace(amr_ctx* ctx, const amr_camera* cam, int32_t* leaf_seq_dev,
+                     double* t_seq_dev, int32_t* seq_len_dev, int32_t max_len,
+                     void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMR_H */

@@ -1,0 +1,102 @@
+// Device-resident records of the raycaster and the kernel argument blocks.
+//
+// Layout in HBM (all arrays written once by amr_build_kdtree, read-only while rendering):
+//   DNode  nodes[N]   8 B each, breadth-first order, siblings adjacent (left = c, right =
+//                      c + 1), so the top of the tree is a contiguous prefix that one
+//                      cache line per few nodes serves to a whole warp (Sec. 3.2 stores the
+//                      second child at the next texel for the same reason).
+//   DLeaf  leaves[M]  48 B each, canonical (pre-order) leaf id order.
+//   DPatch patches[P] 48 B each: where a patch's brick lives and how to address it.
+//   bricks            one brick per patch with a one-cell halo (Sec. 4), float32, x fastest,
+//                      in the layout of the chosen storage strategy.
+#pragma once
+#include <stdint.h>
+
+#include <cuda_runtime.h>
+
+namespace amr {
+
+constexpr int kMaxLevels = 32;
+constexpr int kLeafAxis = 3;            // DNode axis value that marks a leaf
+constexpr uint32_t kIndexMask = 0x3fffffffu;
+constexpr int kMaxDepth = 256;          // descent bound (tree depth is checked at build)
+constexpr int kMaxSamplesPerSegment = 1 << 22;
+
+// status bits raised by kernels (OR-ed into counters[1])
+constexpr unsigned long long kStatusCapacity = 1ull;   // segment or sample bound hit
+constexpr unsigned long long kStatusDevice = 2ull;     // malformed tree reached
+
+struct DNode {
+  uint32_t meta;  // bits 31..30: split axis (3 = leaf); bits 29..0: first child or leaf id
+  int32_t split;  // split plane, finest-level cell index
+};
+
+struct DLeaf {
+  int32_t lo[3], hi[3];  // box, finest-level cells
+  int32_t patch;
+  int32_t level;
+  float vmin, vmax;      // range of every value a sample of this leaf can interpolate
+  int32_t pad[2];
+};
+
+struct DPatch {
+  long long base;      // pointer table: device address of the brick; linear atlas: element
+                       // offset; texture table: cudaTextureObject_t; 3D atlas: unused
+  int32_t sy, sz;      // element strides of y and z (linear storages)
+  int32_t lo[3];       // patch box lo, level cells (brick index = cell - lo + 1)
+  int32_t dim[3];      // brick extent with halo: nx+2, ny+2, nz+2
+  int32_t org[3];      // 3D atlas: texel origin of the brick
+  int32_t pad;
+};
+
+struct DLevel {
+  double h[3];       // spacing h^l
+  double inv_h[3];   // 1 / h^l
+  double step;       // sample step f * min_a h^l_a (world units)
+  int32_t sc;        // finest cells per level-l cell, r^(L-1-l)
+  float inv_sc;      // 1 / sc
+  float hmin;        // min_a h^l_a as float (gradient floor)
+  int32_t pad;
+};
+
+struct RayArgs {
+  double eye[3], fwd[3], right[3], up[3];
+  double tan_half_fov_y;
+  int32_t width, height;
+  int32_t row0, rows;
+  double dlo[3];        // domain origin
+  double hf[3];         // finest spacing h^(L-1)
+  double root_w[6];     // root box, world coordinates
+  int32_t root_f[6];    // root box, finest cells
+};
+
+struct RenderArgs {
+  RayArgs ray;
+  DLevel lv[kMaxLevels];
+  const DNode* nodes;
+  const DLeaf* leaves;
+  const DPatch* patches;
+  const void* pool;            // linear atlas base (element type of the storage)
+  cudaTextureObject_t atlas;   // 3D atlas texture
+  const float4* tf;            // transfer function [tf_n]
+  int32_t tf_n;
+  int32_t max_segments;
+  int32_t skip;                // exact min/max empty-space skipping
+  float kappa, ert_thresh, vmin, inv_range;
+  float ka, kd, ks, shininess, gfloor_num;  // gfloor = gfloor_num / hmin_l
+  float4* out;
+  unsigned long long* counters;  // [0] samples, [1] status bits
+};
+
+struct TraceArgs {
+  RayArgs ray;
+  const DNode* nodes;
+  int32_t* leaf_seq;
+  double* t_seq;
+  int32_t* seq_len;
+  int32_t max_len;
+  int32_t max_segments;
+  unsigned long long* counters;
+};
+
+}  // namespace amr

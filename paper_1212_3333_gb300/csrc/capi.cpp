@@ -1,0 +1,453 @@
+// C ABI of the raycaster: argument checking, context lifecycle and kernel argument
+// marshalling.  Declarations and contracts: include/amr.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "ctx.h"
+
+using namespace amr;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? AMR_ERR_OOM : AMR_ERR_CUDA,    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+amr_status check_camera(amr_ctx* c, const amr_camera* cam) {
+  if (!cam) return fail(c, AMR_ERR_ARG, "camera is NULL");
+  if (cam->width <= 0 || cam->height <= 0 || cam->width > (1 << 16) || cam->height > (1 << 16))
+    return fail(c, AMR_ERR_ARG, "image size out of range");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(cam->eye[a]) || !std::isfinite(cam->fwd[a]) ||
+        !std::isfinite(cam->right[a]) || !std::isfinite(cam->up[a]))
+      return fail(c, AMR_ERR_ARG, "camera has a non-finite component");
+  if (!std::isfinite(cam->tan_half_fov_y) || cam->tan_half_fov_y <= 0.0)
+    return fail(c, AMR_ERR_ARG, "tan_half_fov_y must be positive");
+  return AMR_OK;
+}
+
+}  // namespace
+
+namespace amr {
+
+void fill_ray(const amr_ctx* c, const amr_camera* cam, int row0, int rows, RayArgs* ra) {
+  std::memset(ra, 0, sizeof *ra);
+  for (int a = 0; a < 3; ++a) {
+    ra->eye[a] = cam->eye[a];
+    ra->fwd[a] = cam->fwd[a];
+    ra->right[a] = cam->right[a];
+    ra->up[a] = cam->up[a];
+    ra->dlo[a] = c->dlo[a];
+    ra->hf[a] = c->h0[a] / (double)c->R;
+    ra->root_w[a] = c->dlo[a] + (double)c->root[a] * ra->hf[a];
+    ra->root_w[3 + a] = c->dlo[a] + (double)c->root[3 + a] * ra->hf[a];
+    ra->root_f[a] = (int32_t)c->root[a];
+    ra->root_f[3 + a] = (int32_t)c->root[3 + a];
+  }
+  ra->tan_half_fov_y = cam->tan_half_fov_y;
+  ra->width = cam->width;
+  ra->height = cam->height;
+  ra->row0 = row0;
+  ra->rows = rows;
+}
+
+void fill_levels(const amr_ctx* c, DLevel* lv, double step_factor) {
+  for (int l = 0; l < c->L; ++l) {
+    DLevel& d = lv[l];
+    std::memset(&d, 0, sizeof d);
+    double hmin = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      d.h[a] = c->h0[a] / (double)c->rpow[l];
+      d.inv_h[a] = 1.0 / d.h[a];
+      if (a == 0 || d.h[a] < hmin) hmin = d.h[a];
+    }
+    d.step = step_factor * hmin;
+    d.sc = (int32_t)c->rpow[c->L - 1 - l];
+    d.inv_sc = 1.0f / (float)d.sc;
+    d.hmin = (float)hmin;
+  }
+}
+
+}  // namespace amr
+
+extern "C" {
+
+void amr_default_params(amr_render_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->step_factor = 0.5;
+  p->kappa = 8.0;
+  p->ert_eps = 1e-4;
+  p->vmin = 0.0;
+  p->vmax = 1.0;
+  p->ka = 0.3;
+  p->kd = 0.6;
+  p->ks = 0.3;
+  p->shininess = 32.0;
+  p->gamma = 1e-3;
+  p->interp = AMR_INTERP_TRILINEAR;
+  p->shade = 0;
+  p->row0 = 0;
+  p->rows = 0;
+  p->skip = 0;
+  p->max_segments = 0;
+}
+
+amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double domain_lo[3],
+                      const double h0[3], int32_t num_patches, const int32_t* patch_level,
+                      const int64_t* patch_box, const float* const* cell_data, amr_dtype dtype,
+                      amr_ctx** out) {
+  g_create_error.clear();
+  auto bad = [](const char* m) {
+    g_create_error = m;
+    return AMR_ERR_ARG;
+  };
+  if (!out) return bad("out is NULL");
+  *out = nullptr;
+  if (num_levels < 1 || num_levels > kMaxLevels) return bad("num_levels out of range");
+  if (refine_ratio < 2 || refine_ratio > 64) return bad("refine_ratio out of range");
+  if (!domain_lo || !h0 || !patch_level || !patch_box || !cell_data) return bad("NULL array");
+  if (num_patches < 1) return bad("num_patches must be positive");
+  if (dtype != AMR_F32) return bad("only AMR_F32 storage is available");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(domain_lo[a]) || !std::isfinite(h0[a]) || !(h0[a] > 0.0))
+      return bad("domain_lo / h0 must be finite, h0 positive");
+  amr_ctx* c = new (std::nothrow) amr_ctx();
+  if (!c) {
+    g_create_error = "out of host memory";
+    return AMR_ERR_OOM;
+  }
+  c->L = num_levels;
+  c->r = refine_ratio;
+  c->dtype = dtype;
+  for (int a = 0; a < 3; ++a) {
+    c->dlo[a] = domain_lo[a];
+    c->h0[a] = h0[a];
+  }
+  c->rpow[0] = 1;
+  for (int k = 1; k < 40; ++k) {
+    c->rpow[k] = c->rpow[k - 1] * refine_ratio;
+    if (c->rpow[k] > ((int64_t)1 << 40)) c->rpow[k] = ((int64_t)1 << 40);
+  }
+  if (c->rpow[num_levels - 1] >= ((int64_t)1 << 30)) {
+    delete c;
+    return bad("refine_ratio^(num_levels-1) too large");
+  }
+  c->R = c->rpow[num_levels - 1];
+  try {
+    c->patches.resize((size_t)num_patches);
+    for (int p = 0; p < num_patches; ++p) {
+      Patch& q = c->patches[p];
+      q.level = patch_level[p];
+      if (q.level < 0 || q.level >= num_levels) {
+        delete c;
+        return bad("patch level out of range");
+      }
+      int64_t sc = c->rpow[num_levels - 1 - q.level];
+      int64_t cells = 1;
+      for (int k = 0; k < 3; ++k) {
+        q.box[k] = patch_box[6 * p + k];
+        q.box[3 + k] = patch_box[6 * p + 3 + k];
+        if (q.box[k] >= q.box[3 + k]) {
+          delete c;
+          return bad("patch box with lo >= hi");
+        }
+        if (std::llabs(q.box[k]) > ((int64_t)1 << 30) || std::llabs(q.box[3 + k]) > ((int64_t)1 << 30) ||
+            std::llabs(q.box[k] * sc) >= ((int64_t)1 << 31) ||
+            std::llabs(q.box[3 + k] * sc) >= ((int64_t)1 << 31)) {
+          delete c;
+          return bad("patch box exceeds the int32 finest index space");
+        }
+        q.n[k] = q.box[3 + k] - q.box[k];
+        q.fbox[k] = q.box[k] * sc;
+        q.fbox[3 + k] = q.box[3 + k] * sc;
+        cells *= q.n[k];
+      }
+      if (!cell_data[p]) {
+        delete c;
+        return bad("cell_data entry is NULL");
+      }
+      q.data.assign(cell_data[p], cell_data[p] + cells);
+    }
+  } catch (const std::bad_alloc&) {
+    delete c;
+    g_create_error = "out of host memory";
+    return AMR_ERR_OOM;
+  }
+  *out = c;
+  return AMR_OK;
+}
+
+amr_status amr_build_host(amr_ctx* c, amr_storage storage) {
+  if (!c) return AMR_ERR_ARG;
+  if (storage < AMR_STORE_PTR || storage > AMR_STORE_ATLAS_TEX3D)
+    return fail(c, AMR_ERR_ARG, "unknown storage");
+  auto t0 = std::chrono::steady_clock::now();
+  try {
+    if (!c->host_built) {
+      amr_status s = validate_hierarchy(c);
+      if (s != AMR_OK) return s;
+      s = build_tree(c);
+      if (s != AMR_OK) return s;
+      s = build_bricks(c);
+      if (s != AMR_OK) return s;
+      c->host_built = true;
+    }
+    if ((storage == AMR_STORE_ATLAS_LINEAR || storage == AMR_STORE_ATLAS_TEX3D) &&
+        c->packing.org.empty()) {
+      amr_status s = pack_atlas(c);
+      if (s != AMR_OK) return s;
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(c, AMR_ERR_OOM, "out of host memory during the build");
+  }
+  if (c->storage != (int)storage && c->device_built) release_device(c);
+  c->storage = (int)storage;
+  c->build_seconds +=
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  c->err.clear();
+  return AMR_OK;
+}
+
+amr_status amr_build_kdtree(amr_ctx* c, amr_storage storage, void* cuda_stream) {
+  if (!c) return AMR_ERR_ARG;
+  amr_status s = amr_build_host(c, storage);
+  if (s != AMR_OK) return s;
+  try {
+    return upload(c, cuda_stream);
+  } catch (const std::bad_alloc&) {
+    return fail(c, AMR_ERR_OOM, "out of host memory during the upload");
+  }
+}
+
+static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n,
+                                 const amr_render_params* p, RenderArgs* a) {
+  if (!c) return AMR_ERR_ARG;
+  if (!c->device_built) return fail(c, AMR_ERR_STATE, "render before amr_build_kdtree");
+  amr_status s = check_camera(c, cam);
+  if (s != AMR_OK) return s;
+  if (!p) return fail(c, AMR_ERR_ARG, "params is NULL");
+  if (tf_n < 2 || tf_n > 2048) return fail(c, AMR_ERR_ARG, "tf_n must be in [2, 2048]");
+  if (!(p->vmax > p->vmin)) return fail(c, AMR_ERR_ARG, "vmax must exceed vmin");
+  if (!(p->step_factor > 0.0) || !std::isfinite(p->step_factor))
+    return fail(c, AMR_ERR_ARG, "step_factor must be positive");
+  if (!(p->kappa >= 0.0)) return fail(c, AMR_ERR_ARG, "kappa must be non-negative");
+  if (p->interp != 0 && p->interp != 1) return fail(c, AMR_ERR_ARG, "unknown interp");
+  if (p->shade != 0 && p->shade != 1) return fail(c, AMR_ERR_ARG, "unknown shade");
+  if (p->row0 < 0 || p->row0 >= cam->height) return fail(c, AMR_ERR_ARG, "row0 out of range");
+  int rows = p->rows <= 0 ? cam->height - p->row0 : std::min(p->rows, cam->height - p->row0);
+  std::memset(a, 0, sizeof *a);
+  fill_ray(c, cam, p->row0, rows, &a->ray);
+  fill_levels(c, a->lv, p->step_factor);
+  a->nodes = c->dev.nodes;
+  a->leaves = c->dev.leaves;
+  a->patches = c->dev.patches;
+  a->pool = c->dev.pool;
+  a->atlas = c->dev.atlas_tex;
+  a->tf_n = tf_n;
+  int64_t ms = p->max_segments > 0 ? p->max_segments : 4 * (int64_t)c->tree.axis.size() + 64;
+  a->max_segments = (int32_t)std::min<int64_t>(ms, INT32_MAX);
+  a->skip = p->skip ? 1 : 0;
+  a->kappa = (float)p->kappa;
+  a->ert_thresh = p->ert_eps > 0.0 ? (float)(1.0 - p->ert_eps) : 2.0f;
+  a->vmin = (float)p->vmin;
+  a->inv_range = (float)(1.0 / (p->vmax - p->vmin));
+  a->ka = (float)p->ka;
+  a->kd = (float)p->kd;
+  a->ks = (float)p->ks;
+  a->shininess = (float)p->shininess;
+  a->gfloor_num = (float)(p->gamma * (p->vmax - p->vmin));
+  a->counters = c->dev.counters;
+  return AMR_OK;
+}
+
+static amr_status finish_render(amr_ctx* c, cudaStream_t st, uint64_t* samples_out) {
+  if (!samples_out) return AMR_OK;
+  unsigned long long h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, c->dev.counters, sizeof h, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *samples_out = h[0];
+  if (h[1] & kStatusDevice) return fail(c, AMR_ERR_DEVICE, "device reported a malformed tree");
+  if (h[1] & kStatusCapacity)
+    return fail(c, AMR_ERR_CAPACITY, "a ray exceeded the segment or sample bound");
+  return AMR_OK;
+}
+
+amr_status amr_render(amr_ctx* c, const amr_camera* cam, const float* tf_rgba_dev, int32_t tf_n,
+                      const amr_render_params* params, float* out_rgba_dev, void* cuda_stream,
+                      uint64_t* samples_out) {
+  RenderArgs a;
+  amr_status s = prepare_render(c, cam, tf_n, params, &a);
+  if (s != AMR_OK) return s;
+  if (!tf_rgba_dev || !out_rgba_dev) return fail(c, AMR_ERR_ARG, "NULL device buffer");
+  if (((uintptr_t)tf_rgba_dev | (uintptr_t)out_rgba_dev) & 15)
+    return fail(c, AMR_ERR_ARG, "device buffers must be 16-byte aligned");
+  a.tf = reinterpret_cast<const float4*>(tf_rgba_dev);
+  a.out = reinterpret_cast<float4*>(out_rgba_dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(cudaMemsetAsync(c->dev.counters, 0, 2 * sizeof(unsigned long long), st));
+  s = launch_render(c, a, c->storage, params->interp, params->shade, cuda_stream);
+  if (s != AMR_OK) return s;
+  return finish_render(c, st, samples_out);
+}
+
+amr_status amr_render_host(amr_ctx* c, const amr_camera* cam, const float* tf_rgba_host,
+                           int32_t tf_n, const amr_render_params* params, float* out_rgba_host,
+                           void* cuda_stream, uint64_t* samples_out) {
+  RenderArgs a;
+  amr_status s = prepare_render(c, cam, tf_n, params, &a);
+  if (s != AMR_OK) return s;
+  if (!tf_rgba_host || !out_rgba_host) return fail(c, AMR_ERR_ARG, "NULL host buffer");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  DeviceState& d = c->dev;
+  if (d.tf_scratch_n < tf_n) {
+    cudaFree(d.tf_scratch);
+    d.tf_scratch = nullptr;
+    d.tf_scratch_n = 0;
+    CK(cudaMalloc(&d.tf_scratch, (size_t)tf_n * sizeof(float4)));
+    d.tf_scratch_n = tf_n;
+  }
+  const size_t img_bytes = (size_t)a.ray.rows * a.ray.width * sizeof(float4);
+  if (d.img_scratch_bytes < img_bytes) {
+    cudaFree(d.img_scratch);
+    d.img_scratch = nullptr;
+    d.img_scratch_bytes = 0;
+    CK(cudaMalloc(&d.img_scratch, img_bytes));
+    d.img_scratch_bytes = img_bytes;
+  }
+  CK(cudaMemcpyAsync(d.tf_scratch, tf_rgba_host, (size_t)tf_n * sizeof(float4),
+                     cudaMemcpyHostToDevice, st));
+  a.tf = d.tf_scratch;
+  a.out = d.img_scratch;
+  CK(cudaMemsetAsync(d.counters, 0, 2 * sizeof(unsigned long long), st));
+  s = launch_render(c, a, c->storage, params->interp, params->shade, cuda_stream);
+  if (s != AMR_OK) return s;
+  CK(cudaMemcpyAsync(out_rgba_host, d.img_scratch, img_bytes, cudaMemcpyDeviceToHost, st));
+  if (samples_out) return finish_render(c, st, samples_out);
+  CK(cudaStreamSynchronize(st));
+  return AMR_OK;
+}
+
+amr_status amr_destroy(amr_ctx* c) {
+  if (!c) return AMR_OK;
+  release_device(c);
+  delete c;
+  return AMR_OK;
+}
+
+const char* amr_last_error(const amr_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+amr_status amr_get_stats(const amr_ctx* c, amr_stats* out) {
+  if (!c || !out) return AMR_ERR_ARG;
+  std::memset(out, 0, sizeof *out);
+  out->num_patches = (int64_t)c->patches.size();
+  for (const Patch& p : c->patches) out->num_cells += p.n[0] * p.n[1] * p.n[2];
+  out->storage = c->storage;
+  out->build_seconds = c->build_seconds;
+  if (!c->host_built) return AMR_OK;
+  out->num_nodes = (int64_t)c->tree.axis.size();
+  out->num_leaves = (int64_t)c->tree.leaf_patch.size();
+  out->max_depth = c->tree.max_depth;
+  int64_t brick = 0;
+  for (const auto& b : c->bricks) brick += (int64_t)b.size();
+  out->brick_bytes = c->device_built ? (int64_t)c->dev.pool_bytes : brick * 4;
+  out->tree_bytes = out->num_nodes * (int64_t)sizeof(DNode) +
+                    out->num_leaves * (int64_t)sizeof(DLeaf) +
+                    out->num_patches * (int64_t)sizeof(DPatch);
+  if (!c->packing.org.empty()) {
+    double vol = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      out->atlas_dims[a] = (int32_t)c->packing.dims[a];
+      vol *= (double)c->packing.dims[a];
+    }
+    out->atlas_efficiency = (double)out->num_cells / vol;
+    out->atlas_efficiency_halo = (double)brick / vol;
+  }
+  return AMR_OK;
+}
+
+amr_status amr_get_leaves(const amr_ctx* c, int32_t* box6, int32_t* patch, int32_t* level,
+                          int64_t cap, int64_t* n) {
+  if (!c || !n) return AMR_ERR_ARG;
+  if (!c->host_built) return AMR_ERR_STATE;
+  const int64_t m = (int64_t)c->tree.leaf_patch.size();
+  *n = m;
+  if (cap < m) return AMR_ERR_CAPACITY;
+  if (!box6 || !patch || !level) return AMR_ERR_ARG;
+  std::memcpy(box6, c->tree.leaf_box.data(), sizeof(int32_t) * 6 * (size_t)m);
+  std::memcpy(patch, c->tree.leaf_patch.data(), sizeof(int32_t) * (size_t)m);
+  std::memcpy(level, c->tree.leaf_level.data(), sizeof(int32_t) * (size_t)m);
+  return AMR_OK;
+}
+
+amr_status amr_get_nodes(const amr_ctx* c, int32_t* axis, int32_t* split, int32_t* left,
+                         int32_t* right, int32_t* leaf, int64_t cap, int64_t* n) {
+  if (!c || !n) return AMR_ERR_ARG;
+  if (!c->host_built) return AMR_ERR_STATE;
+  const int64_t m = (int64_t)c->tree.axis.size();
+  *n = m;
+  if (cap < m) return AMR_ERR_CAPACITY;
+  if (!axis || !split || !left || !right || !leaf) return AMR_ERR_ARG;
+  const size_t b = sizeof(int32_t) * (size_t)m;
+  std::memcpy(axis, c->tree.axis.data(), b);
+  std::memcpy(split, c->tree.split.data(), b);
+  std::memcpy(left, c->tree.left.data(), b);
+  std::memcpy(right, c->tree.right.data(), b);
+  std::memcpy(leaf, c->tree.leaf.data(), b);
+  return AMR_OK;
+}
+
+amr_status amr_get_brick(const amr_ctx* c, int32_t patch, float* out, int64_t cap, int64_t* n) {
+  if (!c || !n) return AMR_ERR_ARG;
+  if (!c->host_built) return AMR_ERR_STATE;
+  if (patch < 0 || patch >= (int32_t)c->patches.size()) return AMR_ERR_ARG;
+  const std::vector<float>& b = c->bricks[(size_t)patch];
+  *n = (int64_t)b.size();
+  if (cap < *n) return AMR_ERR_CAPACITY;
+  if (!out) return AMR_ERR_ARG;
+  std::memcpy(out, b.data(), sizeof(float) * b.size());
+  return AMR_OK;
+}
+
+amr_status amr_trace(amr_ctx* c, const amr_camera* cam, int32_t* leaf_seq_dev, double* t_seq_dev,
+                     int32_t* seq_len_dev, int32_t max_len, void* cuda_stream) {
+  if (!c) return AMR_ERR_ARG;
+  if (!c->device_built) return fail(c, AMR_ERR_STATE, "trace before amr_build_kdtree");
+  amr_status s = check_camera(c, cam);
+  if (s != AMR_OK) return s;
+  if (!leaf_seq_dev || !seq_len_dev || max_len < 1)
+    return fail(c, AMR_ERR_ARG, "bad trace buffers");
+  TraceArgs a;
+  std::memset(&a, 0, sizeof a);
+  fill_ray(c, cam, 0, cam->height, &a.ray);
+  a.nodes = c->dev.nodes;
+  a.leaf_seq = leaf_seq_dev;
+  a.t_seq = t_seq_dev;
+  a.seq_len = seq_len_dev;
+  a.max_len = max_len;
+  a.max_segments = (int32_t)std::min<int64_t>(4 * (int64_t)c->tree.axis.size() + 64, INT32_MAX);
+  a.counters = c->dev.counters;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(cudaMemsetAsync(c->dev.counters, 0, 2 * sizeof(unsigned long long), st));
+  s = launch_trace(c, a, cuda_stream);
+  if (s != AMR_OK) return s;
+  unsigned long long h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, c->dev.counters, sizeof h, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h[1] & kStatusDevice) return fail(c, AMR_ERR_DEVICE, "device reported a malformed tree");
+  if (h[1] & kStatusCapacity) return fail(c, AMR_ERR_CAPACITY, "segment bound exceeded");
+  return AMR_OK;
+}
+
+}  // extern "C"

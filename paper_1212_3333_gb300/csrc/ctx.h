@@ -1,0 +1,95 @@
+// Host-side context of the raycaster: the AMR hierarchy, the kD-tree, the bricks and the
+// device allocations that mirror them.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/amr.h"
+#include "amr_device.h"
+
+namespace amr {
+
+struct Patch {
+  int level;
+  int64_t box[6];   // level-l cells
+  int64_t fbox[6];  // finest cells
+  int64_t n[3];     // nx, ny, nz
+  std::vector<float> data;
+};
+
+// Canonical tree in pre-order (what the test hooks return and the device arrays encode).
+struct Tree {
+  std::vector<int32_t> axis, split, left, right, leaf;  // per node, pre-order
+  std::vector<int32_t> leaf_box;                        // 6 per leaf, finest cells
+  std::vector<int32_t> leaf_patch, leaf_level;
+  int max_depth = 0;
+};
+
+struct Packing {
+  int64_t dims[3] = {0, 0, 0};
+  std::vector<int64_t> org;  // 3 per patch
+};
+
+struct DeviceState {
+  DNode* nodes = nullptr;
+  DLeaf* leaves = nullptr;
+  DPatch* patches = nullptr;
+  void* pool = nullptr;  // brick pool (pointer table) or linear atlas
+  size_t pool_bytes = 0;
+  std::vector<void*> arrays;                     // cudaArray_t per patch (texture table)
+  std::vector<cudaTextureObject_t> texobjs;
+  void* atlas_array = nullptr;                   // cudaArray_t of the 3D atlas
+  cudaTextureObject_t atlas_tex = 0;
+  unsigned long long* counters = nullptr;        // [0] samples, [1] status
+  float4* tf_scratch = nullptr;                  // staging for amr_render_host
+  int tf_scratch_n = 0;
+  float4* img_scratch = nullptr;
+  size_t img_scratch_bytes = 0;
+  int device = -1;
+};
+
+}  // namespace amr
+
+struct amr_ctx {
+  int L = 0, r = 0;
+  double dlo[3] = {0, 0, 0}, h0[3] = {0, 0, 0};
+  amr_dtype dtype = AMR_F32;
+  std::vector<amr::Patch> patches;
+  int64_t R = 1;                // r^(L-1)
+  int64_t rpow[40] = {0};
+  int64_t root[6] = {0, 0, 0, 0, 0, 0};
+  amr::Tree tree;
+  std::vector<std::vector<float>> bricks;  // per patch, with halo
+  std::vector<float> leaf_vmin, leaf_vmax;
+  amr::Packing packing;
+  int storage = -1;
+  bool host_built = false;
+  bool device_built = false;
+  double build_seconds = 0.0;
+  amr::DeviceState dev;
+  std::string err;
+};
+
+namespace amr {
+
+// kdtree.cpp
+amr_status validate_hierarchy(amr_ctx* c);
+amr_status build_tree(amr_ctx* c);
+// bricks.cpp
+amr_status build_bricks(amr_ctx* c);
+amr_status pack_atlas(amr_ctx* c);
+// device.cpp
+amr_status upload(amr_ctx* c, void* stream);
+void release_device(amr_ctx* c);
+// kernels (march.cu)
+amr_status launch_render(amr_ctx* c, const RenderArgs& a, int storage, int interp, int shade,
+                         void* stream);
+amr_status launch_trace(amr_ctx* c, const TraceArgs& a, void* stream);
+void fill_levels(const amr_ctx* c, DLevel* lv, double step_factor);
+void fill_ray(const amr_ctx* c, const amr_camera* cam, int row0, int rows, RayArgs* ra);
+
+amr_status fail(amr_ctx* c, amr_status s, const std::string& msg);
+
+}  // namespace amr

@@ -1,0 +1,222 @@
+// Upload of the tree, leaves, patch table and bricks to the device, in one of the four
+// brick storage strategies (Sec. 4.1 packed pool, Sec. 4.2 handle table, rebuilt for CUDA).
+#include <cstring>
+#include <deque>
+
+#include "ctx.h"
+
+namespace amr {
+
+namespace {
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? AMR_ERR_OOM : AMR_ERR_CUDA,    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                \
+  } while (0)
+
+// breadth-first re-layout: children of a node are adjacent, the top levels contiguous
+std::vector<DNode> layout_nodes(const Tree& t) {
+  const size_t n = t.axis.size();
+  std::vector<DNode> out(n);
+  std::deque<std::pair<int, int>> q;  // (pre-order id, bfs slot)
+  q.push_back({0, 0});
+  int next = 1;
+  while (!q.empty()) {
+    auto [pre, slot] = q.front();
+    q.pop_front();
+    DNode d;
+    if (t.axis[pre] < 0) {
+      d.meta = ((uint32_t)kLeafAxis << 30) | ((uint32_t)t.leaf[pre] & kIndexMask);
+      d.split = 0;
+    } else {
+      int first = next;
+      next += 2;
+      d.meta = ((uint32_t)t.axis[pre] << 30) | ((uint32_t)first & kIndexMask);
+      d.split = t.split[pre];
+      q.push_back({t.left[pre], first});
+      q.push_back({t.right[pre], first + 1});
+    }
+    out[slot] = d;
+  }
+  return out;
+}
+
+}  // namespace
+
+void release_device(amr_ctx* c) {
+  DeviceState& d = c->dev;
+  if (d.device >= 0) cudaSetDevice(d.device);
+  if (d.atlas_tex) cudaDestroyTextureObject(d.atlas_tex);
+  for (auto t : d.texobjs)
+    if (t) cudaDestroyTextureObject(t);
+  for (void* a : d.arrays)
+    if (a) cudaFreeArray((cudaArray_t)a);
+  if (d.atlas_array) cudaFreeArray((cudaArray_t)d.atlas_array);
+  cudaFree(d.nodes);
+  cudaFree(d.leaves);
+  cudaFree(d.patches);
+  cudaFree(d.pool);
+  cudaFree(d.counters);
+  cudaFree(d.tf_scratch);
+  cudaFree(d.img_scratch);
+  d = DeviceState();
+  c->device_built = false;
+}
+
+amr_status upload(amr_ctx* c, void* stream_v) {
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  if (c->device_built) release_device(c);
+  DeviceState& d = c->dev;
+  CK(cudaGetDevice(&d.device));
+  const Tree& t = c->tree;
+  const size_t P = c->patches.size();
+  const size_t M = t.leaf_patch.size();
+  if (t.axis.size() >= (size_t)kIndexMask || M >= (size_t)kIndexMask)
+    return fail(c, AMR_ERR_CAPACITY, "tree too large for 30-bit node indices");
+  std::vector<DNode> nodes = layout_nodes(t);
+  std::vector<DLeaf> leaves(M);
+  for (size_t m = 0; m < M; ++m) {
+    DLeaf& l = leaves[m];
+    std::memset(&l, 0, sizeof l);
+    for (int k = 0; k < 6; ++k) (k < 3 ? l.lo[k] : l.hi[k - 3]) = t.leaf_box[6 * m + k];
+    l.patch = t.leaf_patch[m];
+    l.level = t.leaf_level[m];
+    l.vmin = c->leaf_vmin[m];
+    l.vmax = c->leaf_vmax[m];
+  }
+  std::vector<DPatch> pt(P);
+  for (size_t p = 0; p < P; ++p) {
+    std::memset(&pt[p], 0, sizeof(DPatch));
+    for (int a = 0; a < 3; ++a) {
+      pt[p].lo[a] = (int32_t)c->patches[p].box[a];
+      pt[p].dim[a] = (int32_t)(c->patches[p].n[a] + 2);
+    }
+  }
+  CK(cudaMalloc(&d.nodes, nodes.size() * sizeof(DNode)));
+  CK(cudaMalloc(&d.leaves, std::max<size_t>(1, M) * sizeof(DLeaf)));
+  CK(cudaMalloc(&d.patches, P * sizeof(DPatch)));
+  CK(cudaMalloc(&d.counters, 4 * sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(d.counters, 0, 4 * sizeof(unsigned long long), stream));
+
+  size_t brick_elems = 0;
+  const int storage = c->storage;
+  if (storage == AMR_STORE_PTR) {
+    // one pool, each brick 128-byte aligned; the table holds the device addresses
+    std::vector<size_t> off(P);
+    for (size_t p = 0; p < P; ++p) {
+      off[p] = brick_elems;
+      brick_elems += (c->bricks[p].size() + 31) & ~(size_t)31;
+    }
+    d.pool_bytes = brick_elems * sizeof(float);
+    CK(cudaMalloc(&d.pool, d.pool_bytes));
+    for (size_t p = 0; p < P; ++p) {
+      float* dst = (float*)d.pool + off[p];
+      CK(cudaMemcpyAsync(dst, c->bricks[p].data(), c->bricks[p].size() * sizeof(float),
+                         cudaMemcpyHostToDevice, stream));
+      pt[p].base = (long long)(uintptr_t)dst;
+      pt[p].sy = pt[p].dim[0];
+      pt[p].sz = pt[p].dim[0] * pt[p].dim[1];
+    }
+  } else if (storage == AMR_STORE_TEXOBJ) {
+    d.arrays.assign(P, nullptr);
+    d.texobjs.assign(P, 0);
+    cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
+    for (size_t p = 0; p < P; ++p) {
+      cudaExtent ext = make_cudaExtent(pt[p].dim[0], pt[p].dim[1], pt[p].dim[2]);
+      cudaArray_t arr = nullptr;
+      CK(cudaMalloc3DArray(&arr, &ch, ext));
+      d.arrays[p] = arr;
+      cudaMemcpy3DParms cp;
+      std::memset(&cp, 0, sizeof cp);
+      cp.srcPtr = make_cudaPitchedPtr(c->bricks[p].data(), pt[p].dim[0] * sizeof(float),
+                                      pt[p].dim[0], pt[p].dim[1]);
+      cp.dstArray = arr;
+      cp.extent = ext;
+      cp.kind = cudaMemcpyHostToDevice;
+      CK(cudaMemcpy3DAsync(&cp, stream));
+      cudaResourceDesc rd;
+      std::memset(&rd, 0, sizeof rd);
+      rd.resType = cudaResourceTypeArray;
+      rd.res.array.array = arr;
+      cudaTextureDesc td;
+      std::memset(&td, 0, sizeof td);
+      td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+      td.filterMode = cudaFilterModePoint;
+      td.readMode = cudaReadModeElementType;
+      td.normalizedCoords = 0;
+      cudaTextureObject_t tex = 0;
+      CK(cudaCreateTextureObject(&tex, &rd, &td, nullptr));
+      d.texobjs[p] = tex;
+      pt[p].base = (long long)tex;
+      brick_elems += c->bricks[p].size();
+    }
+  } else {
+    // packed atlas (NFDH), linear memory or one 3D array
+    const int64_t AX = c->packing.dims[0], AY = c->packing.dims[1], AZ = c->packing.dims[2];
+    const size_t total = (size_t)(AX * AY * AZ);
+    std::vector<float> img(total, 0.0f);
+    for (size_t p = 0; p < P; ++p) {
+      const int64_t* o = &c->packing.org[3 * p];
+      const int64_t d0 = pt[p].dim[0], d1 = pt[p].dim[1], d2 = pt[p].dim[2];
+      for (int64_t k = 0; k < d2; ++k)
+        for (int64_t j = 0; j < d1; ++j)
+          std::memcpy(&img[(size_t)(o[0] + AX * ((o[1] + j) + AY * (o[2] + k)))],
+                      &c->bricks[p][(size_t)(d0 * (j + d1 * k))], sizeof(float) * (size_t)d0);
+      for (int a = 0; a < 3; ++a) pt[p].org[a] = (int32_t)o[a];
+      pt[p].base = (long long)(o[0] + AX * (o[1] + AY * o[2]));
+      pt[p].sy = (int32_t)AX;
+      pt[p].sz = (int32_t)(AX * AY);
+    }
+    brick_elems = total;
+    if (storage == AMR_STORE_ATLAS_LINEAR) {
+      d.pool_bytes = total * sizeof(float);
+      CK(cudaMalloc(&d.pool, d.pool_bytes));
+      CK(cudaMemcpyAsync(d.pool, img.data(), d.pool_bytes, cudaMemcpyHostToDevice, stream));
+      CK(cudaStreamSynchronize(stream));
+    } else {
+      cudaDeviceProp prop;
+      CK(cudaGetDeviceProperties(&prop, d.device));
+      if (AX > prop.maxTexture3D[0] || AY > prop.maxTexture3D[1] || AZ > prop.maxTexture3D[2])
+        return fail(c, AMR_ERR_CAPACITY, "atlas exceeds the 3D texture extent limit");
+      cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
+      cudaExtent ext = make_cudaExtent(AX, AY, AZ);
+      cudaArray_t arr = nullptr;
+      CK(cudaMalloc3DArray(&arr, &ch, ext));
+      d.atlas_array = arr;
+      cudaMemcpy3DParms cp;
+      std::memset(&cp, 0, sizeof cp);
+      cp.srcPtr = make_cudaPitchedPtr(img.data(), AX * sizeof(float), AX, AY);
+      cp.dstArray = arr;
+      cp.extent = ext;
+      cp.kind = cudaMemcpyHostToDevice;
+      CK(cudaMemcpy3DAsync(&cp, stream));
+      cudaResourceDesc rd;
+      std::memset(&rd, 0, sizeof rd);
+      rd.resType = cudaResourceTypeArray;
+      rd.res.array.array = arr;
+      cudaTextureDesc td;
+      std::memset(&td, 0, sizeof td);
+      td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+      td.filterMode = cudaFilterModePoint;
+      td.readMode = cudaReadModeElementType;
+      td.normalizedCoords = 0;
+      CK(cudaCreateTextureObject(&d.atlas_tex, &rd, &td, nullptr));
+      CK(cudaStreamSynchronize(stream));
+    }
+  }
+  CK(cudaMemcpyAsync(d.nodes, nodes.data(), nodes.size() * sizeof(DNode), cudaMemcpyHostToDevice,
+                     stream));
+  if (M)
+    CK(cudaMemcpyAsync(d.leaves, leaves.data(), M * sizeof(DLeaf), cudaMemcpyHostToDevice,
+                       stream));
+  CK(cudaMemcpyAsync(d.patches, pt.data(), P * sizeof(DPatch), cudaMemcpyHostToDevice, stream));
+  CK(cudaStreamSynchronize(stream));
+  d.pool_bytes = brick_elems * sizeof(float);
+  c->device_built = true;
+  return AMR_OK;
+}
+
+}  // namespace amr

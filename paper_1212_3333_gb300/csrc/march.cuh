@@ -1,0 +1,517 @@
+// Device side of the single-pass AMR raycaster (Sec. 3.3 of Kaehler & Abel).
+//
+// One thread per pixel; a 128-thread block covers an 8x16 pixel tile and each warp an 8x4
+// sub-tile, so the rays of a warp traverse nearly the same leaves and read nearly the same
+// brick cache lines.  Per ray:
+//   ray generation and root slab test in FP64 (exact operation order, no FMA);
+//   kd-restart: descend from the root to the leaf holding the ray at t0, narrowing t1 to
+//     the nearest split plane crossed (Sec. 3.3), in FP64 so that the leaf sequence and
+//     segment bounds are bit-identical to the FP64 reference;
+//   per segment: n = max(1, ceil(len / (f h^l))) midpoint samples (Sec. 3.3, sampling rate
+//     proportional to the level's cell size), stepped in FP32 brick coordinates;
+//   per sample: trilinear interpolation from the leaf's patch brick, transfer function
+//     from shared memory, alpha = 1 - exp(-kappa a delta), optional central-difference
+//     gradient Phong (neighbours may lie in other leaves, patches or levels: found by a
+//     point descent of the same tree), front-to-back compositing, early termination.
+// Every device loop is bounded; exceeding a bound sets a status bit, never traps.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "amr_device.h"
+
+namespace amr {
+
+enum { ST_PTR = 0, ST_TEXOBJ = 1, ST_ATLAS_LINEAR = 2, ST_ATLAS_TEX3D = 3 };
+
+__device__ __forceinline__ double sel3(int a, double x, double y, double z) {
+  return a == 0 ? x : (a == 1 ? y : z);
+}
+__device__ __forceinline__ float sel3f(int a, float x, float y, float z) {
+  return a == 0 ? x : (a == 1 ? y : z);
+}
+__device__ __forceinline__ int sel3i(int a, int x, int y, int z) {
+  return a == 0 ? x : (a == 1 ? y : z);
+}
+
+struct Ray {
+  double o[3], d[3], inv[3];
+  double t_in, t_out;
+  bool hit;
+};
+
+// Pixel (i, j) -> ray and root interval; the operation order is part of the contract
+// (the FP64 reference computes the same expressions in the same order).
+__device__ __forceinline__ void make_ray(const RayArgs& A, int i, int j, Ray& r) {
+  const double W = (double)A.width, H = (double)A.height;
+  const double aspect = __ddiv_rn(W, H);
+  const double u = __dmul_rn(
+      __dmul_rn(__dsub_rn(__ddiv_rn(__dmul_rn(2.0, __dadd_rn((double)i, 0.5)), W), 1.0),
+                A.tan_half_fov_y),
+      aspect);
+  const double v = __dmul_rn(
+      __dsub_rn(1.0, __ddiv_rn(__dmul_rn(2.0, __dadd_rn((double)j, 0.5)), H)), A.tan_half_fov_y);
+  double t_in = 0.0, t_out = __longlong_as_double(0x7ff0000000000000ll);
+  bool hit = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    r.o[a] = A.eye[a];
+    r.d[a] = __dadd_rn(__dadd_rn(A.fwd[a], __dmul_rn(u, A.right[a])), __dmul_rn(v, A.up[a]));
+    r.inv[a] = r.d[a] != 0.0 ? __ddiv_rn(1.0, r.d[a]) : 0.0;
+    const double lo = A.root_w[a], hi = A.root_w[3 + a];
+    if (r.d[a] != 0.0) {
+      const double ta = __dmul_rn(__dsub_rn(lo, r.o[a]), r.inv[a]);
+      const double tb = __dmul_rn(__dsub_rn(hi, r.o[a]), r.inv[a]);
+      const double tn = ta < tb ? ta : tb;
+      const double tf = ta < tb ? tb : ta;
+      if (tn > t_in) t_in = tn;
+      if (tf < t_out) t_out = tf;
+    } else if (r.o[a] < lo || r.o[a] >= hi) {
+      hit = false;
+    }
+  }
+  if (!(t_in < t_out)) hit = false;
+  r.t_in = t_in;
+  r.t_out = t_out;
+  r.hit = hit;
+}
+
+// kd-restart descent (Sec. 3.3): the leaf holding the ray just after t0; narrows t1 to the
+// first split plane beyond t0 on the way down.  Returns the leaf id, or -1 (status) on a
+// malformed tree.  Near child = the side entered first (d_a > 0: lower); t_s >= t1 ->
+// near only; t_s <= t0 -> far only; else near with t1 = t_s; d_a == 0 -> the origin's side.
+__device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const RayArgs& A,
+                                       const Ray& r, double t0, double& t1) {
+  uint32_t i = 0;
+  for (int depth = 0; depth < kMaxDepth; ++depth) {
+    const DNode nd = nodes[i];
+    const uint32_t ax = nd.meta >> 30;
+    const uint32_t idx = nd.meta & kIndexMask;
+    if (ax == kLeafAxis) return (int)idx;
+    const double o = sel3(ax, r.o[0], r.o[1], r.o[2]);
+    const double d = sel3(ax, r.d[0], r.d[1], r.d[2]);
+    const double sw = __dadd_rn(sel3(ax, A.dlo[0], A.dlo[1], A.dlo[2]),
+                                __dmul_rn((double)nd.split, sel3(ax, A.hf[0], A.hf[1], A.hf[2])));
+    if (d == 0.0) {
+      i = idx + (o < sw ? 0u : 1u);
+      continue;
+    }
+    const double ts = __dmul_rn(__dsub_rn(sw, o), sel3(ax, r.inv[0], r.inv[1], r.inv[2]));
+    const uint32_t near_c = idx + (d > 0.0 ? 0u : 1u);
+    const uint32_t far_c = idx + (d > 0.0 ? 1u : 0u);
+    if (ts >= t1) {
+      i = near_c;
+    } else if (ts <= t0) {
+      i = far_c;
+    } else {
+      i = near_c;
+      t1 = ts;
+    }
+  }
+  return -1;
+}
+
+// Point location by integer finest-cell coordinates (left iff f_a < split).
+__device__ __forceinline__ int locate_cell(const DNode* __restrict__ nodes, int f0, int f1,
+                                           int f2) {
+  uint32_t i = 0;
+  for (int depth = 0; depth < kMaxDepth; ++depth) {
+    const DNode nd = nodes[i];
+    const uint32_t ax = nd.meta >> 30;
+    const uint32_t idx = nd.meta & kIndexMask;
+    if (ax == kLeafAxis) return (int)idx;
+    i = idx + (sel3i(ax, f0, f1, f2) < nd.split ? 0u : 1u);
+  }
+  return -1;
+}
+
+// Brick of one patch as held in registers while a segment is sampled.
+struct BrickRef {
+  long long base;  // pointer / element offset / texture object
+  int sy, sz;
+  int dim[3];
+  int lo[3];
+  int org[3];
+};
+
+__device__ __forceinline__ BrickRef load_brick(const DPatch* __restrict__ pt, int p) {
+  const DPatch q = pt[p];
+  BrickRef b;
+  b.base = q.base;
+  b.sy = q.sy;
+  b.sz = q.sz;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    b.dim[a] = q.dim[a];
+    b.lo[a] = q.lo[a];
+    b.org[a] = q.org[a];
+  }
+  return b;
+}
+
+template <int ST>
+__device__ __forceinline__ float fetch(const RenderArgs& A, const BrickRef& b, long long lin, int i,
+                                       int j, int k) {
+  if constexpr (ST == ST_PTR) {
+    return __ldg(reinterpret_cast<const float*>(b.base) + lin);
+  } else if constexpr (ST == ST_ATLAS_LINEAR) {
+    return __ldg(reinterpret_cast<const float*>(A.pool) + b.base + lin);
+  } else if constexpr (ST == ST_TEXOBJ) {
+    return tex3D<float>((cudaTextureObject_t)b.base, (float)i + 0.5f, (float)j + 0.5f,
+                        (float)k + 0.5f);
+  } else {
+    return tex3D<float>(A.atlas, (float)(b.org[0] + i) + 0.5f, (float)(b.org[1] + j) + 0.5f,
+                        (float)(b.org[2] + k) + 0.5f);
+  }
+}
+
+// Trilinear interpolation at brick coordinate beta (brick index = cell - lo + 1, cell
+// centres at integer beta).  Coordinates are clamped into the brick, which reproduces edge
+// replication where the brick touches the domain boundary.
+template <int ST>
+__device__ __forceinline__ float trilinear(const RenderArgs& A, const BrickRef& b, float bx,
+                                           float by, float bz) {
+  bx = fminf(fmaxf(bx, 0.0f), (float)(b.dim[0] - 1));
+  by = fminf(fmaxf(by, 0.0f), (float)(b.dim[1] - 1));
+  bz = fminf(fmaxf(bz, 0.0f), (float)(b.dim[2] - 1));
+  const int ix = min((int)bx, b.dim[0] - 2);
+  const int iy = min((int)by, b.dim[1] - 2);
+  const int iz = min((int)bz, b.dim[2] - 2);
+  const float wx = bx - (float)ix, wy = by - (float)iy, wz = bz - (float)iz;
+  const long long l0 = (long long)ix + (long long)b.sy * iy + (long long)b.sz * iz;
+  const float v000 = fetch<ST>(A, b, l0, ix, iy, iz);
+  const float v100 = fetch<ST>(A, b, l0 + 1, ix + 1, iy, iz);
+  const float v010 = fetch<ST>(A, b, l0 + b.sy, ix, iy + 1, iz);
+  const float v110 = fetch<ST>(A, b, l0 + b.sy + 1, ix + 1, iy + 1, iz);
+  const float v001 = fetch<ST>(A, b, l0 + b.sz, ix, iy, iz + 1);
+  const float v101 = fetch<ST>(A, b, l0 + b.sz + 1, ix + 1, iy, iz + 1);
+  const float v011 = fetch<ST>(A, b, l0 + b.sz + b.sy, ix, iy + 1, iz + 1);
+  const float v111 = fetch<ST>(A, b, l0 + b.sz + b.sy + 1, ix + 1, iy + 1, iz + 1);
+  const float c00 = fmaf(wx, v100 - v000, v000);
+  const float c10 = fmaf(wx, v110 - v010, v010);
+  const float c01 = fmaf(wx, v101 - v001, v001);
+  const float c11 = fmaf(wx, v111 - v011, v011);
+  const float c0 = fmaf(wy, c10 - c00, c00);
+  const float c1 = fmaf(wy, c11 - c01, c01);
+  return fmaf(wz, c1 - c0, c0);
+}
+
+// Nearest cell value at integer brick index (clamped).
+template <int ST>
+__device__ __forceinline__ float cell_at(const RenderArgs& A, const BrickRef& b, int i, int j,
+                                         int k) {
+  i = min(max(i, 0), b.dim[0] - 1);
+  j = min(max(j, 0), b.dim[1] - 1);
+  k = min(max(k, 0), b.dim[2] - 1);
+  return fetch<ST>(A, b, (long long)i + (long long)b.sy * j + (long long)b.sz * k, i, j, k);
+}
+
+// State of the segment being sampled.
+struct SegState {
+  BrickRef brick;
+  int level;
+  int leaf;
+  int leaf_lo[3];     // finest cells
+  float bl[3], bh[3]; // leaf box in brick coordinates
+  float margin;       // bound on the FP32 brick-coordinate error of this segment's samples
+  double t0, dt;
+};
+
+// Position of sample k, exactly as the FP64 reference computes it.
+__device__ __forceinline__ double sample_x(const Ray& r, const SegState& s, int k, int a) {
+  const double t = __dadd_rn(s.t0, __dmul_rn(__dadd_rn((double)k, 0.5), s.dt));
+  return __dadd_rn(sel3(a, r.o[0], r.o[1], r.o[2]), __dmul_rn(t, sel3(a, r.d[0], r.d[1], r.d[2])));
+}
+
+// Value of the AMR field at the gradient neighbour x_k + sign * h^l e_a (Sec. 4: shading
+// reads across block boundaries).  Inside the current leaf (beyond the error margin) it is
+// the current brick; otherwise the finest leaf holding the point is found by descending
+// the tree on finest-cell coordinates, with an exact FP64 recomputation whenever the
+// FP32 position is within the error margin of a decision plane.
+template <int ST, int INTERP>
+__device__ float neighbour_value(const RenderArgs& A, const Ray& r, const SegState& s,
+                                 const float* beta, int a, float sign, int k) {
+  float bn[3] = {beta[0], beta[1], beta[2]};
+  bn[a] += sign;
+  const float m = s.margin;
+  bool inside = true;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) inside = inside && (bn[q] >= s.bl[q] + m) && (bn[q] < s.bh[q] - m);
+  if (inside) {
+    if constexpr (INTERP == 1) {
+      return trilinear<ST>(A, s.brick, bn[0], bn[1], bn[2]);
+    } else {
+      // nearest: the cell decision itself is filtered too
+      const float fx = bn[0] + 0.5f, fy = bn[1] + 0.5f, fz = bn[2] + 0.5f;
+      const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
+      if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > m)
+        return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
+    }
+  }
+  const DLevel& lv = A.lv[s.level];
+  const int sc = lv.sc;
+  const float scf = (float)sc;
+  const float mf = m * scf;
+  // finest coordinates relative to the current leaf's lower corner
+  float xr[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) xr[q] = (bn[q] - s.bl[q]) * scf;
+  bool amb = false;
+  uint32_t i = 0;
+  int lid = -1;
+  for (int depth = 0; depth < kMaxDepth; ++depth) {
+    const DNode nd = A.nodes[i];
+    const uint32_t ax = nd.meta >> 30;
+    const uint32_t idx = nd.meta & kIndexMask;
+    if (ax == kLeafAxis) {
+      lid = (int)idx;
+      break;
+    }
+    const float diff = sel3f(ax, xr[0], xr[1], xr[2]) -
+                       (float)(nd.split - sel3i(ax, s.leaf_lo[0], s.leaf_lo[1], s.leaf_lo[2]));
+    if (fabsf(diff) <= mf) {
+      amb = true;
+      break;
+    }
+    i = idx + (diff < 0.0f ? 0u : 1u);
+  }
+  double xe[3];
+  if (amb) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) xe[q] = sample_x(r, s, k, q);
+    const double hq = sel3(a, lv.h[0], lv.h[1], lv.h[2]);
+    if (a == 0) xe[0] = sign > 0.0f ? __dadd_rn(xe[0], hq) : __dsub_rn(xe[0], hq);
+    if (a == 1) xe[1] = sign > 0.0f ? __dadd_rn(xe[1], hq) : __dsub_rn(xe[1], hq);
+    if (a == 2) xe[2] = sign > 0.0f ? __dadd_rn(xe[2], hq) : __dsub_rn(xe[2], hq);
+    int f[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double qv = floor(__ddiv_rn(__dsub_rn(xe[q], A.ray.dlo[q]), A.ray.hf[q]));
+      if (qv < (double)A.ray.root_f[q]) f[q] = A.ray.root_f[q];
+      else if (qv > (double)(A.ray.root_f[3 + q] - 1)) f[q] = A.ray.root_f[3 + q] - 1;
+      else f[q] = (int)qv;
+    }
+    lid = locate_cell(A.nodes, f[0], f[1], f[2]);
+  }
+  if (lid < 0) return 0.0f;
+  const DLeaf lf = A.leaves[lid];
+  const BrickRef nb = (lid == s.leaf) ? s.brick : load_brick(A.patches, lf.patch);
+  const DLevel& lw = A.lv[lf.level];
+  float bq[3];
+  if (amb) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      bq[q] = (float)((xe[q] - A.ray.dlo[q]) * lw.inv_h[q] + (0.5 - (double)nb.lo[q]));
+  } else {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      bq[q] = fmaf(xr[q], lw.inv_sc,
+                   (float)(s.leaf_lo[q] - nb.lo[q] * lw.sc) * lw.inv_sc + 0.5f);
+  }
+  if constexpr (INTERP == 1) {
+    return trilinear<ST>(A, nb, bq[0], bq[1], bq[2]);
+  } else {
+    if (amb) {
+      int c[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        c[q] = (int)floor(__ddiv_rn(__dsub_rn(xe[q], A.ray.dlo[q]), lw.h[q])) - nb.lo[q] + 1;
+      return cell_at<ST>(A, nb, c[0], c[1], c[2]);
+    }
+    const float fx = bq[0] + 0.5f, fy = bq[1] + 0.5f, fz = bq[2] + 0.5f;
+    const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
+    const float mq = m * scf * lw.inv_sc;
+    if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > mq)
+      return cell_at<ST>(A, nb, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
+    // too close to a cell face in FP32: decide in FP64
+#pragma unroll
+    for (int q = 0; q < 3; ++q) xe[q] = sample_x(r, s, k, q);
+    const double hq = sel3(a, A.lv[s.level].h[0], A.lv[s.level].h[1], A.lv[s.level].h[2]);
+    if (a == 0) xe[0] = sign > 0.0f ? __dadd_rn(xe[0], hq) : __dsub_rn(xe[0], hq);
+    if (a == 1) xe[1] = sign > 0.0f ? __dadd_rn(xe[1], hq) : __dsub_rn(xe[1], hq);
+    if (a == 2) xe[2] = sign > 0.0f ? __dadd_rn(xe[2], hq) : __dsub_rn(xe[2], hq);
+    int c[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      c[q] = (int)floor(__ddiv_rn(__dsub_rn(xe[q], A.ray.dlo[q]), lw.h[q])) - nb.lo[q] + 1;
+    return cell_at<ST>(A, nb, c[0], c[1], c[2]);
+  }
+}
+
+// Value at the sample itself (the segment's own leaf and level, Sec. 3.3).
+template <int ST, int INTERP>
+__device__ __forceinline__ float sample_value(const RenderArgs& A, const Ray& r, const SegState& s,
+                                              const float* beta, int k) {
+  if constexpr (INTERP == 1) {
+    return trilinear<ST>(A, s.brick, beta[0], beta[1], beta[2]);
+  } else {
+    const float fx = beta[0] + 0.5f, fy = beta[1] + 0.5f, fz = beta[2] + 0.5f;
+    const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
+    if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > s.margin)
+      return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
+    const DLevel& lv = A.lv[s.level];
+    int c[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      c[q] = (int)floor(__ddiv_rn(__dsub_rn(sample_x(r, s, k, q), A.ray.dlo[q]), lv.h[q])) -
+             s.brick.lo[q] + 1;
+    return cell_at<ST>(A, s.brick, c[0], c[1], c[2]);
+  }
+}
+
+__device__ __forceinline__ float4 tf_lookup(const float4* __restrict__ tf, int n, float v,
+                                            float vmin, float inv_range) {
+  float u = (v - vmin) * inv_range;
+  u = fminf(fmaxf(u, 0.0f), 1.0f) * (float)(n - 1);
+  const int i = min((int)u, n - 2);
+  const float w = u - (float)i;
+  const float4 a = tf[i], b = tf[i + 1];
+  return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y), fmaf(w, b.z - a.z, a.z),
+                     fmaf(w, b.w - a.w, a.w));
+}
+
+// true when the transfer function is fully transparent over [v0, v1] (conservative)
+__device__ __forceinline__ bool tf_transparent(const int* __restrict__ nz_prefix, int n, float v0,
+                                               float v1, float vmin, float inv_range) {
+  float u0 = fminf(fmaxf((v0 - vmin) * inv_range, 0.0f), 1.0f) * (float)(n - 1);
+  float u1 = fminf(fmaxf((v1 - vmin) * inv_range, 0.0f), 1.0f) * (float)(n - 1);
+  const int i0 = max((int)u0 - 1, 0);
+  const int i1 = min((int)u1 + 2, n - 1);
+  return nz_prefix[i1 + 1] - nz_prefix[i0] == 0;
+}
+
+template <int ST, int INTERP, int SHADE>
+__global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ RenderArgs A) {
+  extern __shared__ float4 smem[];
+  float4* s_tf = smem;
+  int* s_nz = reinterpret_cast<int*>(smem + A.tf_n);
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  for (int k = tid; k < A.tf_n; k += blockDim.x * blockDim.y) s_tf[k] = A.tf[k];
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    s_nz[0] = 0;
+    for (int k = 0; k < A.tf_n; ++k) {
+      acc += s_tf[k].w != 0.0f ? 1 : 0;
+      s_nz[k + 1] = acc;
+    }
+  }
+  __syncthreads();
+
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jr = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = A.ray.row0 + jr;
+  const bool active = i < A.ray.width && jr < A.ray.rows && j < A.ray.height;
+  float C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
+  unsigned nsamp = 0;
+  unsigned long long status = 0;
+  if (active) {
+    Ray r;
+    make_ray(A.ray, i, j, r);
+    if (r.hit) {
+      const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(r.d[0], r.d[0]),
+                                                       __dmul_rn(r.d[1], r.d[1])),
+                                             __dmul_rn(r.d[2], r.d[2])));
+      const float inv_dn = (float)(1.0 / dn);
+      const float Lx = -(float)r.d[0] * inv_dn, Ly = -(float)r.d[1] * inv_dn,
+                  Lz = -(float)r.d[2] * inv_dn;
+      double t0 = r.t_in;
+      int seg = 0;
+      bool done = false;
+      while (!done && t0 < r.t_out) {
+        if (seg >= A.max_segments) {
+          status |= kStatusCapacity;
+          break;
+        }
+        ++seg;
+        double t1 = r.t_out;
+        const int lid = descend(A.nodes, A.ray, r, t0, t1);
+        if (lid < 0) {
+          status |= kStatusDevice;
+          break;
+        }
+        const DLeaf lf = A.leaves[lid];
+        const DLevel& lv = A.lv[lf.level];
+        const double dtt = __dsub_rn(t1, t0);
+        const double len = __dmul_rn(dtt, dn);
+        const double nf = ceil(__ddiv_rn(len, lv.step));
+        int n = nf < 1.0 ? 1 : (nf > (double)kMaxSamplesPerSegment ? kMaxSamplesPerSegment : (int)nf);
+        if (nf > (double)kMaxSamplesPerSegment) status |= kStatusCapacity;
+        if (A.skip && tf_transparent(s_nz, A.tf_n, lf.vmin, lf.vmax, A.vmin, A.inv_range)) {
+          t0 = t1;
+          continue;
+        }
+        SegState s;
+        s.brick = load_brick(A.patches, lf.patch);
+        s.level = lf.level;
+        s.leaf = lid;
+        s.t0 = t0;
+        s.dt = __ddiv_rn(dtt, (double)n);
+        const float delta = (float)__ddiv_rn(len, (double)n);
+        const double tm = t0 + 0.5 * s.dt;
+        float b0[3], db[3];
+        float bmax = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const double xa = r.o[a] + tm * r.d[a];
+          b0[a] = (float)((xa - A.ray.dlo[a]) * lv.inv_h[a] + (0.5 - (double)s.brick.lo[a]));
+          db[a] = (float)(s.dt * r.d[a] * lv.inv_h[a]);
+          s.leaf_lo[a] = lf.lo[a];
+          s.bl[a] = (float)(lf.lo[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
+          s.bh[a] = (float)(lf.hi[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
+          bmax = fmaxf(bmax, fabsf(b0[a]) + (float)n * fabsf(db[a]) + (float)s.brick.dim[a]);
+        }
+        // |FP32 beta - exact| <= u (|b0| + k |db| + |beta|) plus the rounding of the
+        // relative coordinates; 2^-21 (bmax + 2) bounds all of it with room to spare
+        s.margin = ldexpf(bmax + 2.0f, -21);
+        for (int k = 0; k < n; ++k) {
+          float beta[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, db[a], b0[a]);
+          const float v = sample_value<ST, INTERP>(A, r, s, beta, k);
+          const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
+          ++nsamp;
+          if (c.w <= 0.0f) continue;
+          const float alpha = -expm1f(-A.kappa * c.w * delta);
+          float cr = c.x, cg = c.y, cb = c.z;
+          if constexpr (SHADE == 1) {
+            float g[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              const float vp = neighbour_value<ST, INTERP>(A, r, s, beta, a, 1.0f, k);
+              const float vm = neighbour_value<ST, INTERP>(A, r, s, beta, a, -1.0f, k);
+              g[a] = (vp - vm) * (0.5f * (float)lv.inv_h[a]);
+            }
+            const float gn = sqrtf(fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2])));
+            const float gf = A.gfloor_num / lv.hmin;
+            const float den = fmaxf(gn, gf);
+            const float inv = den > 0.0f ? 1.0f / den : 0.0f;
+            const float ndl = fabsf((g[0] * Lx + g[1] * Ly + g[2] * Lz) * inv);
+            const float spec = A.ks * __powf(ndl, A.shininess);
+            const float diff = fmaf(A.kd, ndl, A.ka);
+            cr = fminf(fmaxf(fmaf(cr, diff, spec), 0.0f), 1.0f);
+            cg = fminf(fmaxf(fmaf(cg, diff, spec), 0.0f), 1.0f);
+            cb = fminf(fmaxf(fmaf(cb, diff, spec), 0.0f), 1.0f);
+          }
+          const float w = (1.0f - Acc) * alpha;
+          C0 = fmaf(w, cr, C0);
+          C1 = fmaf(w, cg, C1);
+          C2 = fmaf(w, cb, C2);
+          Acc += w;
+          if (Acc >= A.ert_thresh) {
+            done = true;
+            break;
+          }
+        }
+        t0 = t1;
+      }
+    }
+    A.out[(size_t)jr * A.ray.width + i] = make_float4(C0, C1, C2, Acc);
+  }
+  // exact sample count: one atomic per warp
+  const unsigned total = __reduce_add_sync(0xffffffffu, nsamp);
+  if ((tid & 31) == 0 && total) atomicAdd(A.counters, (unsigned long long)total);
+  if (status) atomicOr(A.counters + 1, status);
+}
+
+}  // namespace amr

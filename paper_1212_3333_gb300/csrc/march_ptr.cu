@@ -1,0 +1,8 @@
+// March kernels for the per-patch pointer table (bricks in one device pool).
+#include "march_launch.cuh"
+
+namespace amr {
+amr_status launch_ptr(amr_ctx* c, const RenderArgs& a, int interp, int shade, cudaStream_t s) {
+  return launch_storage<ST_PTR>(c, a, interp, shade, s);
+}
+}  // namespace amr

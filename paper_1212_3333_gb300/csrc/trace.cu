@@ -1,0 +1,68 @@
+// Per-pixel traversal sequences (Sec. 3.3 kd-restart) and the render dispatcher.
+#include "march_launch.cuh"
+
+namespace amr {
+
+__global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ TraceArgs A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= A.ray.width || j >= A.ray.height) return;
+  const size_t p = (size_t)j * A.ray.width + i;
+  Ray r;
+  make_ray(A.ray, i, j, r);
+  if (!r.hit) {
+    A.seq_len[p] = 0;
+    return;
+  }
+  double t0 = r.t_in;
+  int n = 0;
+  unsigned long long status = 0;
+  while (t0 < r.t_out) {
+    if (n >= A.max_segments) {
+      status |= kStatusCapacity;
+      break;
+    }
+    double t1 = r.t_out;
+    const int lid = descend(A.nodes, A.ray, r, t0, t1);
+    if (lid < 0) {
+      status |= kStatusDevice;
+      break;
+    }
+    if (n < A.max_len) {
+      const size_t q = p * (size_t)A.max_len + n;
+      A.leaf_seq[q] = lid;
+      if (A.t_seq) {
+        A.t_seq[2 * q] = t0;
+        A.t_seq[2 * q + 1] = t1;
+      }
+    }
+    ++n;
+    t0 = t1;
+  }
+  A.seq_len[p] = n <= A.max_len ? n : -1;
+  if (status) atomicOr(A.counters + 1, status);
+}
+
+amr_status launch_trace(amr_ctx* c, const TraceArgs& a, void* stream) {
+  const dim3 block(8, 16);
+  const dim3 grid((unsigned)((a.ray.width + 7) / 8), (unsigned)((a.ray.height + 15) / 16));
+  trace_kernel<<<grid, block, 0, (cudaStream_t)stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(c, AMR_ERR_CUDA, std::string("trace launch: ") + cudaGetErrorString(e));
+  return AMR_OK;
+}
+
+amr_status launch_render(amr_ctx* c, const RenderArgs& a, int storage, int interp, int shade,
+                         void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (storage) {
+    case ST_PTR: return launch_ptr(c, a, interp, shade, s);
+    case ST_TEXOBJ: return launch_texobj(c, a, interp, shade, s);
+    case ST_ATLAS_LINEAR: return launch_atlas_linear(c, a, interp, shade, s);
+    case ST_ATLAS_TEX3D: return launch_atlas_tex3d(c, a, interp, shade, s);
+    default: return fail(c, AMR_ERR_ARG, "unknown storage");
+  }
+}
+
+}  // namespace amr

@@ -222,7 +222,7 @@ def random_hierarchy(seed: int, n0: int = 8, num_levels: int = 3, ratio: int = 2
         placed = []
         for _ in range(patches_per_level):
             for _try in range(50):
-                size = rng.integers(1, max_size + 1, size=3)
+                size = np.minimum(rng.integers(1, max_size + 1, size=3), n_l)
                 lo = np.array([rng.integers(0, n_l - size[k] + 1) for k in range(3)])
                 cand = [int(lo[0]), int(lo[1]), int(lo[2]), int(lo[0] + size[0]),
                         int(lo[1] + size[1]), int(lo[2] + size[2])]
