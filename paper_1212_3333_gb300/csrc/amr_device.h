@@ -56,7 +56,7 @@ struct DLevel {
   int32_t sc;        // finest cells per level-l cell, r^(L-1-l)
   float inv_sc;      // 1 / sc
   float hmin;        // min_a h^l_a as float (gradient floor)
-  int32_t pad;
+  float inv_step;    // 1 / step as float
 };
 
 struct RayArgs {

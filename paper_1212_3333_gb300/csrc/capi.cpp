@@ -74,6 +74,7 @@ void fill_levels(const amr_ctx* c, DLevel* lv, double step_factor) {
     d.sc = (int32_t)c->rpow[c->L - 1 - l];
     d.inv_sc = 1.0f / (float)d.sc;
     d.hmin = (float)hmin;
+    d.inv_step = (float)(1.0 / d.step);
   }
 }
 

@@ -2,17 +2,21 @@
 //
 // One thread per pixel; a 128-thread block covers an 8x16 pixel tile and each warp an 8x4
 // sub-tile, so the rays of a warp traverse nearly the same leaves and read nearly the same
-// brick cache lines.  Per ray:
-//   ray generation and root slab test in FP64 (exact operation order, no FMA);
-//   kd-restart: descend from the root to the leaf holding the ray at t0, narrowing t1 to
-//     the nearest split plane crossed (Sec. 3.3), in FP64 so that the leaf sequence and
-//     segment bounds are bit-identical to the FP64 reference;
-//   per segment: n = max(1, ceil(len / (f h^l))) midpoint samples (Sec. 3.3, sampling rate
-//     proportional to the level's cell size), stepped in FP32 brick coordinates;
-//   per sample: trilinear interpolation from the leaf's patch brick, transfer function
-//     from shared memory, alpha = 1 - exp(-kappa a delta), optional central-difference
-//     gradient Phong (neighbours may lie in other leaves, patches or levels: found by a
-//     point descent of the same tree), front-to-back compositing, early termination.
+// brick cache lines.
+//
+// Exactness without FP64 throughput.  The reference semantics are FP64: ray parameters of
+// split planes t_s = (plane - o) / d decide the kd-restart descent, and the per-segment
+// sample count n = max(1, ceil(len / step)) depends on exact t0, t1.  GB300 issues FP64 at
+// a small fraction of its FP32 rate, so the kernel works in an FP32 frame
+// tau = t - t_in (the ray parameter measured from the root entry point, which keeps the
+// magnitudes small) and carries, for every FP32 quantity, a rigorous bound on its distance
+// from the FP64 value.  A decision is taken in FP32 only when the bound cannot flip it;
+// otherwise the exact FP64 quantities are recomputed from plane ids (each t0 / t1 is
+// remembered as the split plane that produced it) and the decision is taken exactly.
+// The same filtering guards the cell decisions of cross-leaf gradient lookups and of
+// nearest sampling.  The traversal sequence and segment bounds therefore match the FP64
+// reference bit for bit while the hot loops issue FP32 only.
+//
 // Every device loop is bounded; exceeding a bound sets a status bit, never traps.
 #pragma once
 #include <cuda_runtime.h>
@@ -24,6 +28,10 @@ namespace amr {
 
 enum { ST_PTR = 0, ST_TEXOBJ = 1, ST_ATLAS_LINEAR = 2, ST_ATLAS_TEX3D = 3 };
 
+// plane ids: split * 4 + axis; the two ray ends use axis field 3
+constexpr int kPidIn = 3;
+constexpr int kPidOut = 7;
+
 __device__ __forceinline__ double sel3(int a, double x, double y, double z) {
   return a == 0 ? x : (a == 1 ? y : z);
 }
@@ -34,15 +42,25 @@ __device__ __forceinline__ int sel3i(int a, int x, int y, int z) {
   return a == 0 ? x : (a == 1 ? y : z);
 }
 
-struct Ray {
-  double o[3], d[3], inv[3];
+// Exact ray (FP64), used by the rare exact paths.
+struct RayX {
+  double o[3], d[3];
   double t_in, t_out;
-  bool hit;
 };
 
-// Pixel (i, j) -> ray and root interval; the operation order is part of the contract
-// (the FP64 reference computes the same expressions in the same order).
-__device__ __forceinline__ void make_ray(const RayArgs& A, int i, int j, Ray& r) {
+// FP32 frame of the ray.  tau_s(s) = s * B[a] + C[a] approximates t_s - t_in of split
+// plane s on axis a within Ef[a]; X(tau) = Xe + tau * Dd approximates the position in
+// finest-cell units (x - dlo) / h_f.
+struct RayF {
+  float B[3], C[3], Ef[3];
+  float Xe[3], Dd[3];
+  float tau_out, e_out;
+  float dn;
+};
+
+// Pixel (i, j) -> exact ray and root interval.  The operation order is part of the
+// contract: the FP64 reference evaluates the same expressions in the same order.
+__device__ __forceinline__ bool make_ray(const RayArgs& A, int i, int j, RayX& r) {
   const double W = (double)A.width, H = (double)A.height;
   const double aspect = __ddiv_rn(W, H);
   const double u = __dmul_rn(
@@ -57,11 +75,11 @@ __device__ __forceinline__ void make_ray(const RayArgs& A, int i, int j, Ray& r)
   for (int a = 0; a < 3; ++a) {
     r.o[a] = A.eye[a];
     r.d[a] = __dadd_rn(__dadd_rn(A.fwd[a], __dmul_rn(u, A.right[a])), __dmul_rn(v, A.up[a]));
-    r.inv[a] = r.d[a] != 0.0 ? __ddiv_rn(1.0, r.d[a]) : 0.0;
     const double lo = A.root_w[a], hi = A.root_w[3 + a];
     if (r.d[a] != 0.0) {
-      const double ta = __dmul_rn(__dsub_rn(lo, r.o[a]), r.inv[a]);
-      const double tb = __dmul_rn(__dsub_rn(hi, r.o[a]), r.inv[a]);
+      const double inv = __ddiv_rn(1.0, r.d[a]);
+      const double ta = __dmul_rn(__dsub_rn(lo, r.o[a]), inv);
+      const double tb = __dmul_rn(__dsub_rn(hi, r.o[a]), inv);
       const double tn = ta < tb ? ta : tb;
       const double tf = ta < tb ? tb : ta;
       if (tn > t_in) t_in = tn;
@@ -73,39 +91,114 @@ __device__ __forceinline__ void make_ray(const RayArgs& A, int i, int j, Ray& r)
   if (!(t_in < t_out)) hit = false;
   r.t_in = t_in;
   r.t_out = t_out;
-  r.hit = hit;
+  return hit;
 }
 
-// kd-restart descent (Sec. 3.3): the leaf holding the ray just after t0; narrows t1 to the
-// first split plane beyond t0 on the way down.  Returns the leaf id, or -1 (status) on a
-// malformed tree.  Near child = the side entered first (d_a > 0: lower); t_s >= t1 ->
-// near only; t_s <= t0 -> far only; else near with t1 = t_s; d_a == 0 -> the origin's side.
+// Exact FP64 ray parameter of a plane id (the reference's t_s, t_in or t_out).
+static __device__ __noinline__ double exact_t(const RayArgs& A, const RayX& r, int pid) {
+  if (pid == kPidIn) return r.t_in;
+  if (pid == kPidOut) return r.t_out;
+  const int ax = pid & 3;
+  const int s = pid >> 2;
+  const double o = sel3(ax, r.o[0], r.o[1], r.o[2]);
+  const double d = sel3(ax, r.d[0], r.d[1], r.d[2]);
+  const double sw = __dadd_rn(sel3(ax, A.dlo[0], A.dlo[1], A.dlo[2]),
+                              __dmul_rn((double)s, sel3(ax, A.hf[0], A.hf[1], A.hf[2])));
+  return __dmul_rn(__dsub_rn(sw, o), __ddiv_rn(1.0, d));
+}
+
+// Build the FP32 frame.  Error bounds: tau_s = fma(s, B, C) with B, C rounded once from
+// FP64 is within u (|s B| + |C| + |tau_s|) of t_s - t_in (plus FP64 rounding, ~1e-15
+// relative); |tau_s| <= |s B| + |C|, so 4u (2 max|s B| + 2|C| + 1) bounds it with room.
+__device__ __forceinline__ void make_frame(const RayArgs& A, const RayX& r, RayF& f) {
+  const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(r.d[0], r.d[0]),
+                                                   __dmul_rn(r.d[1], r.d[1])),
+                                         __dmul_rn(r.d[2], r.d[2])));
+  f.dn = (float)dn;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double e = r.o[a] + r.t_in * r.d[a];  // entry point (accuracy only)
+    const double smax = (double)max(abs(A.root_f[a]), abs(A.root_f[3 + a]));
+    if (r.d[a] != 0.0) {
+      const double inv = 1.0 / r.d[a];
+      const double B = A.hf[a] * inv;
+      const double C = (A.dlo[a] - e) * inv;
+      // B == 0 must mean d_a == 0: keep the sign of a B that would underflow
+      f.B[a] = (float)B != 0.0f ? (float)B : copysignf(1e-38f, (float)inv);
+      f.C[a] = (float)C;
+      const double ef = ldexp(2.0 * smax * fabs(B) + 2.0 * fabs(C) + 1.0, -22);
+      // an axis whose frame does not fit FP32 always takes the exact path
+      f.Ef[a] = (fabs(B) * smax < 1e30 && fabs(C) < 1e30 && fabs(B) > 1e-30) ? (float)ef
+                                                                           : __int_as_float(0x7f800000);
+    } else {
+      f.B[a] = 0.0f;
+      f.C[a] = 0.0f;
+      f.Ef[a] = __int_as_float(0x7f800000);
+    }
+    f.Xe[a] = (float)((e - A.dlo[a]) / A.hf[a]);
+    f.Dd[a] = (float)(r.d[a] / A.hf[a]);
+  }
+  const double tau_out = r.t_out - r.t_in;
+  f.tau_out = (float)tau_out;
+  f.e_out = ldexpf(f.tau_out + 1.0f, -22);
+}
+
+// kd-restart descent (Sec. 3.3) from the root for the segment starting at (pid0, tau0):
+// returns the leaf holding the ray just after t0 and narrows (pid1, tau1, e1) to the
+// first split plane beyond t0.  Near child = the side entered first (d_a > 0: lower);
+// t_s >= t1 -> near only; t_s <= t0 -> far only; otherwise near with t1 = t_s;
+// d_a == 0 -> the side holding the origin.  Returns -1 on a malformed tree.
 __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const RayArgs& A,
-                                       const Ray& r, double t0, double& t1) {
+                                       const RayX& rx, const RayF& rf, int pid0, float tau0,
+                                       float e0, int& pid1, float& tau1, float& e1) {
   uint32_t i = 0;
   for (int depth = 0; depth < kMaxDepth; ++depth) {
     const DNode nd = nodes[i];
     const uint32_t ax = nd.meta >> 30;
     const uint32_t idx = nd.meta & kIndexMask;
     if (ax == kLeafAxis) return (int)idx;
-    const double o = sel3(ax, r.o[0], r.o[1], r.o[2]);
-    const double d = sel3(ax, r.d[0], r.d[1], r.d[2]);
-    const double sw = __dadd_rn(sel3(ax, A.dlo[0], A.dlo[1], A.dlo[2]),
-                                __dmul_rn((double)nd.split, sel3(ax, A.hf[0], A.hf[1], A.hf[2])));
-    if (d == 0.0) {
+    const float B = sel3f(ax, rf.B[0], rf.B[1], rf.B[2]);
+    if (B == 0.0f) {  // ray parallel to the plane: the origin's side (exact)
+      const double o = sel3(ax, rx.o[0], rx.o[1], rx.o[2]);
+      const double sw = __dadd_rn(sel3(ax, A.dlo[0], A.dlo[1], A.dlo[2]),
+                                  __dmul_rn((double)nd.split, sel3(ax, A.hf[0], A.hf[1], A.hf[2])));
       i = idx + (o < sw ? 0u : 1u);
       continue;
     }
-    const double ts = __dmul_rn(__dsub_rn(sw, o), sel3(ax, r.inv[0], r.inv[1], r.inv[2]));
-    const uint32_t near_c = idx + (d > 0.0 ? 0u : 1u);
-    const uint32_t far_c = idx + (d > 0.0 ? 1u : 0u);
-    if (ts >= t1) {
-      i = near_c;
-    } else if (ts <= t0) {
+    const int pid = nd.split * 4 + (int)ax;
+    const uint32_t near_c = idx + (B > 0.0f ? 0u : 1u);
+    const uint32_t far_c = idx + (B > 0.0f ? 1u : 0u);
+    if (pid == pid0) {  // the plane that produced t0: t_s == t0
       i = far_c;
-    } else {
+      continue;
+    }
+    if (pid == pid1) {  // the plane that produced t1: t_s == t1
       i = near_c;
-      t1 = ts;
+      continue;
+    }
+    const float ts = fmaf((float)nd.split, B, sel3f(ax, rf.C[0], rf.C[1], rf.C[2]));
+    const float es = sel3f(ax, rf.Ef[0], rf.Ef[1], rf.Ef[2]);
+    if (ts - tau1 > es + e1) {
+      i = near_c;
+    } else if (tau0 - ts > es + e0) {
+      i = far_c;
+    } else if (tau1 - ts > es + e1 && ts - tau0 > es + e0) {
+      i = near_c;
+      pid1 = pid;
+      tau1 = ts;
+      e1 = es;
+    } else {  // too close to call in FP32: decide on the exact FP64 values
+      const double t = exact_t(A, rx, pid);
+      if (t >= exact_t(A, rx, pid1)) {
+        i = near_c;
+      } else if (t <= exact_t(A, rx, pid0)) {
+        i = far_c;
+      } else {
+        i = near_c;
+        pid1 = pid;
+        tau1 = ts;
+        e1 = es;
+      }
     }
   }
   return -1;
@@ -213,24 +306,40 @@ struct SegState {
   int leaf;
   int leaf_lo[3];     // finest cells
   float bl[3], bh[3]; // leaf box in brick coordinates
-  float margin;       // bound on the FP32 brick-coordinate error of this segment's samples
-  double t0, dt;
+  float margin;       // bound on |FP32 beta - beta of the exact FP64 sample position|
+  int pid0, pid1, n;  // exact segment: t0, t1 by plane id, n samples
 };
 
-// Position of sample k, exactly as the FP64 reference computes it.
-__device__ __forceinline__ double sample_x(const Ray& r, const SegState& s, int k, int a) {
-  const double t = __dadd_rn(s.t0, __dmul_rn(__dadd_rn((double)k, 0.5), s.dt));
-  return __dadd_rn(sel3(a, r.o[0], r.o[1], r.o[2]), __dmul_rn(t, sel3(a, r.d[0], r.d[1], r.d[2])));
+// Position of sample k, exactly as the FP64 reference computes it (rare path).
+static __device__ __noinline__ void sample_x_exact(const RenderArgs& A, const RayX& r, const SegState& s,
+                                            int k, double* x) {
+  const double t0 = exact_t(A.ray, r, s.pid0);
+  const double t1 = exact_t(A.ray, r, s.pid1);
+  const double dt = __ddiv_rn(__dsub_rn(t1, t0), (double)s.n);
+  const double t = __dadd_rn(t0, __dmul_rn(__dadd_rn((double)k, 0.5), dt));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) x[a] = __dadd_rn(r.o[a], __dmul_rn(t, r.d[a]));
 }
+
+// finest cell of an exact point, clamped into the root (the reference's rule)
+__device__ __forceinline__ int finest_cell_exact(const RayArgs& A, double x, int a) {
+  const double q = floor(__ddiv_rn(__dsub_rn(x, A.dlo[a]), A.hf[a]));
+  if (q < (double)A.root_f[a]) return A.root_f[a];
+  if (q > (double)(A.root_f[3 + a] - 1)) return A.root_f[3 + a] - 1;
+  return (int)q;
+}
+
+template <int ST, int INTERP>
+__device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayX& r, const SegState& s,
+                                             const float* bn, int a, float sign, int k);
 
 // Value of the AMR field at the gradient neighbour x_k + sign * h^l e_a (Sec. 4: shading
 // reads across block boundaries).  Inside the current leaf (beyond the error margin) it is
-// the current brick; otherwise the finest leaf holding the point is found by descending
-// the tree on finest-cell coordinates, with an exact FP64 recomputation whenever the
-// FP32 position is within the error margin of a decision plane.
+// the current brick; otherwise the slow path locates the finest leaf holding the point.
 template <int ST, int INTERP>
-__device__ float neighbour_value(const RenderArgs& A, const Ray& r, const SegState& s,
-                                 const float* beta, int a, float sign, int k) {
+__device__ __forceinline__ float neighbour_value(const RenderArgs& A, const RayX& r,
+                                                 const SegState& s, const float* beta, int a,
+                                                 float sign, int k) {
   float bn[3] = {beta[0], beta[1], beta[2]};
   bn[a] += sign;
   const float m = s.margin;
@@ -241,18 +350,23 @@ __device__ float neighbour_value(const RenderArgs& A, const Ray& r, const SegSta
     if constexpr (INTERP == 1) {
       return trilinear<ST>(A, s.brick, bn[0], bn[1], bn[2]);
     } else {
-      // nearest: the cell decision itself is filtered too
       const float fx = bn[0] + 0.5f, fy = bn[1] + 0.5f, fz = bn[2] + 0.5f;
       const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
       if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > m)
         return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
     }
   }
+  return neighbour_slow<ST, INTERP>(A, r, s, bn, a, sign, k);
+}
+
+// Cross-leaf neighbour: descend the tree on finest-cell coordinates relative to the current
+// leaf corner; any split within the error margin sends the decision to FP64.
+template <int ST, int INTERP>
+__device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayX& r, const SegState& s,
+                                             const float* bn, int a, float sign, int k) {
   const DLevel& lv = A.lv[s.level];
-  const int sc = lv.sc;
-  const float scf = (float)sc;
-  const float mf = m * scf;
-  // finest coordinates relative to the current leaf's lower corner
+  const float scf = (float)lv.sc;
+  const float mf = s.margin * scf;
   float xr[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) xr[q] = (bn[q] - s.bl[q]) * scf;
@@ -277,21 +391,13 @@ __device__ float neighbour_value(const RenderArgs& A, const Ray& r, const SegSta
   }
   double xe[3];
   if (amb) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) xe[q] = sample_x(r, s, k, q);
+    sample_x_exact(A, r, s, k, xe);
     const double hq = sel3(a, lv.h[0], lv.h[1], lv.h[2]);
     if (a == 0) xe[0] = sign > 0.0f ? __dadd_rn(xe[0], hq) : __dsub_rn(xe[0], hq);
     if (a == 1) xe[1] = sign > 0.0f ? __dadd_rn(xe[1], hq) : __dsub_rn(xe[1], hq);
     if (a == 2) xe[2] = sign > 0.0f ? __dadd_rn(xe[2], hq) : __dsub_rn(xe[2], hq);
-    int f[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const double qv = floor(__ddiv_rn(__dsub_rn(xe[q], A.ray.dlo[q]), A.ray.hf[q]));
-      if (qv < (double)A.ray.root_f[q]) f[q] = A.ray.root_f[q];
-      else if (qv > (double)(A.ray.root_f[3 + q] - 1)) f[q] = A.ray.root_f[3 + q] - 1;
-      else f[q] = (int)qv;
-    }
-    lid = locate_cell(A.nodes, f[0], f[1], f[2]);
+    lid = locate_cell(A.nodes, finest_cell_exact(A.ray, xe[0], 0), finest_cell_exact(A.ray, xe[1], 1),
+                      finest_cell_exact(A.ray, xe[2], 2));
   }
   if (lid < 0) return 0.0f;
   const DLeaf lf = A.leaves[lid];
@@ -305,31 +411,23 @@ __device__ float neighbour_value(const RenderArgs& A, const Ray& r, const SegSta
   } else {
 #pragma unroll
     for (int q = 0; q < 3; ++q)
-      bq[q] = fmaf(xr[q], lw.inv_sc,
-                   (float)(s.leaf_lo[q] - nb.lo[q] * lw.sc) * lw.inv_sc + 0.5f);
+      bq[q] = fmaf(xr[q], lw.inv_sc, (float)(s.leaf_lo[q] - nb.lo[q] * lw.sc) * lw.inv_sc + 0.5f);
   }
   if constexpr (INTERP == 1) {
     return trilinear<ST>(A, nb, bq[0], bq[1], bq[2]);
   } else {
-    if (amb) {
-      int c[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-        c[q] = (int)floor(__ddiv_rn(__dsub_rn(xe[q], A.ray.dlo[q]), lw.h[q])) - nb.lo[q] + 1;
-      return cell_at<ST>(A, nb, c[0], c[1], c[2]);
+    if (!amb) {
+      const float fx = bq[0] + 0.5f, fy = bq[1] + 0.5f, fz = bq[2] + 0.5f;
+      const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
+      const float mq = mf * lw.inv_sc;
+      if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > mq)
+        return cell_at<ST>(A, nb, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
+      sample_x_exact(A, r, s, k, xe);
+      const double hq = sel3(a, lv.h[0], lv.h[1], lv.h[2]);
+      if (a == 0) xe[0] = sign > 0.0f ? __dadd_rn(xe[0], hq) : __dsub_rn(xe[0], hq);
+      if (a == 1) xe[1] = sign > 0.0f ? __dadd_rn(xe[1], hq) : __dsub_rn(xe[1], hq);
+      if (a == 2) xe[2] = sign > 0.0f ? __dadd_rn(xe[2], hq) : __dsub_rn(xe[2], hq);
     }
-    const float fx = bq[0] + 0.5f, fy = bq[1] + 0.5f, fz = bq[2] + 0.5f;
-    const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
-    const float mq = m * scf * lw.inv_sc;
-    if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > mq)
-      return cell_at<ST>(A, nb, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
-    // too close to a cell face in FP32: decide in FP64
-#pragma unroll
-    for (int q = 0; q < 3; ++q) xe[q] = sample_x(r, s, k, q);
-    const double hq = sel3(a, A.lv[s.level].h[0], A.lv[s.level].h[1], A.lv[s.level].h[2]);
-    if (a == 0) xe[0] = sign > 0.0f ? __dadd_rn(xe[0], hq) : __dsub_rn(xe[0], hq);
-    if (a == 1) xe[1] = sign > 0.0f ? __dadd_rn(xe[1], hq) : __dsub_rn(xe[1], hq);
-    if (a == 2) xe[2] = sign > 0.0f ? __dadd_rn(xe[2], hq) : __dsub_rn(xe[2], hq);
     int c[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q)
@@ -340,7 +438,7 @@ __device__ float neighbour_value(const RenderArgs& A, const Ray& r, const SegSta
 
 // Value at the sample itself (the segment's own leaf and level, Sec. 3.3).
 template <int ST, int INTERP>
-__device__ __forceinline__ float sample_value(const RenderArgs& A, const Ray& r, const SegState& s,
+__device__ __forceinline__ float sample_value(const RenderArgs& A, const RayX& r, const SegState& s,
                                               const float* beta, int k) {
   if constexpr (INTERP == 1) {
     return trilinear<ST>(A, s.brick, beta[0], beta[1], beta[2]);
@@ -350,11 +448,12 @@ __device__ __forceinline__ float sample_value(const RenderArgs& A, const Ray& r,
     if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > s.margin)
       return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
     const DLevel& lv = A.lv[s.level];
+    double x[3];
+    sample_x_exact(A, r, s, k, x);
     int c[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q)
-      c[q] = (int)floor(__ddiv_rn(__dsub_rn(sample_x(r, s, k, q), A.ray.dlo[q]), lv.h[q])) -
-             s.brick.lo[q] + 1;
+      c[q] = (int)floor(__ddiv_rn(__dsub_rn(x[q], A.ray.dlo[q]), lv.h[q])) - s.brick.lo[q] + 1;
     return cell_at<ST>(A, s.brick, c[0], c[1], c[2]);
   }
 }
@@ -378,6 +477,34 @@ __device__ __forceinline__ bool tf_transparent(const int* __restrict__ nz_prefix
   const int i0 = max((int)u0 - 1, 0);
   const int i1 = min((int)u1 + 2, n - 1);
   return nz_prefix[i1 + 1] - nz_prefix[i0] == 0;
+}
+
+// Exact sample count of a segment: n = max(1, ceil(len / step)), len = (t1 - t0) |d|.
+// The FP32 estimate decides unless the quotient lies within its error bound of an integer.
+static __device__ __noinline__ int exact_count(const RenderArgs& A, const RayX& r, int pid0, int pid1,
+                                        double step) {
+  const double t0 = exact_t(A.ray, r, pid0), t1 = exact_t(A.ray, r, pid1);
+  const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(r.d[0], r.d[0]),
+                                                   __dmul_rn(r.d[1], r.d[1])),
+                                         __dmul_rn(r.d[2], r.d[2])));
+  const double len = __dmul_rn(__dsub_rn(t1, t0), dn);
+  const double nf = ceil(__ddiv_rn(len, step));
+  return nf < 1.0 ? 1 : (nf > (double)kMaxSamplesPerSegment ? kMaxSamplesPerSegment + 1 : (int)nf);
+}
+
+__device__ __forceinline__ int segment_count(const RenderArgs& A, const RayX& r, const RayF& f,
+                                             int pid0, float tau0, float e0, int pid1, float tau1,
+                                             float e1, const DLevel& lv) {
+  const float inv_step = lv.inv_step;
+  const float lenf = (tau1 - tau0) * f.dn;
+  const float q = lenf * inv_step;
+  // |q - exact| <= ((e0 + e1) |d| + 2^-21 (tau0 + tau1 + 1) |d|) / step + 2^-21 q
+  const float eq = ((e0 + e1) * f.dn + ldexpf((tau0 + tau1 + 1.0f) * f.dn, -21)) * inv_step +
+                   ldexpf(q + 1.0f, -21);
+  if (q + eq <= 1.0f) return 1;
+  const float c = ceilf(q);
+  if (c - q > eq && q - (c - 1.0f) > eq && c <= (float)kMaxSamplesPerSegment) return (int)c;
+  return exact_count(A, r, pid0, pid1, lv.step);
 }
 
 template <int ST, int INTERP, int SHADE>
@@ -406,69 +533,79 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Rend
   unsigned nsamp = 0;
   unsigned long long status = 0;
   if (active) {
-    Ray r;
-    make_ray(A.ray, i, j, r);
-    if (r.hit) {
-      const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(r.d[0], r.d[0]),
-                                                       __dmul_rn(r.d[1], r.d[1])),
-                                             __dmul_rn(r.d[2], r.d[2])));
-      const float inv_dn = (float)(1.0 / dn);
-      const float Lx = -(float)r.d[0] * inv_dn, Ly = -(float)r.d[1] * inv_dn,
-                  Lz = -(float)r.d[2] * inv_dn;
-      double t0 = r.t_in;
+    RayX rx;
+    if (make_ray(A.ray, i, j, rx)) {
+      RayF rf;
+      make_frame(A.ray, rx, rf);
+      const float inv_dn = 1.0f / rf.dn;
+      const float Lx = -rf.Dd[0] * (float)A.ray.hf[0] * inv_dn;
+      const float Ly = -rf.Dd[1] * (float)A.ray.hf[1] * inv_dn;
+      const float Lz = -rf.Dd[2] * (float)A.ray.hf[2] * inv_dn;
+      int pid0 = kPidIn;
+      float tau0 = 0.0f, e0 = 0.0f;
       int seg = 0;
-      bool done = false;
-      while (!done && t0 < r.t_out) {
+      while (pid0 != kPidOut) {
         if (seg >= A.max_segments) {
           status |= kStatusCapacity;
           break;
         }
         ++seg;
-        double t1 = r.t_out;
-        const int lid = descend(A.nodes, A.ray, r, t0, t1);
+        int pid1 = kPidOut;
+        float tau1 = rf.tau_out, e1 = rf.e_out;
+        const int lid = descend(A.nodes, A.ray, rx, rf, pid0, tau0, e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;
           break;
         }
         const DLeaf lf = A.leaves[lid];
         const DLevel& lv = A.lv[lf.level];
-        const double dtt = __dsub_rn(t1, t0);
-        const double len = __dmul_rn(dtt, dn);
-        const double nf = ceil(__ddiv_rn(len, lv.step));
-        int n = nf < 1.0 ? 1 : (nf > (double)kMaxSamplesPerSegment ? kMaxSamplesPerSegment : (int)nf);
-        if (nf > (double)kMaxSamplesPerSegment) status |= kStatusCapacity;
+        int n = segment_count(A, rx, rf, pid0, tau0, e0, pid1, tau1, e1, lv);
+        if (n > kMaxSamplesPerSegment) {
+          status |= kStatusCapacity;
+          n = kMaxSamplesPerSegment;
+        }
         if (A.skip && tf_transparent(s_nz, A.tf_n, lf.vmin, lf.vmax, A.vmin, A.inv_range)) {
-          t0 = t1;
+          pid0 = pid1;
+          tau0 = tau1;
+          e0 = e1;
           continue;
         }
         SegState s;
         s.brick = load_brick(A.patches, lf.patch);
         s.level = lf.level;
         s.leaf = lid;
-        s.t0 = t0;
-        s.dt = __ddiv_rn(dtt, (double)n);
-        const float delta = (float)__ddiv_rn(len, (double)n);
-        const double tm = t0 + 0.5 * s.dt;
+        s.pid0 = pid0;
+        s.pid1 = pid1;
+        s.n = n;
+        const float nfl = (float)n;
+        const float dtau = (tau1 - tau0) / nfl;
+        const float delta = dtau * rf.dn;
+        const float taum = fmaf(0.5f, dtau, tau0);
+        // error of the FP32 sample parameters: tau ends within max(e0, e1), a few
+        // roundings of the tau arithmetic, then the position and brick-space roundings
+        const float etau = fmaxf(e0, e1) + ldexpf(tau1 + 1.0f, -21);
         float b0[3], db[3];
-        float bmax = 0.0f;
+        float ex = 0.0f, bmax = 0.0f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const double xa = r.o[a] + tm * r.d[a];
-          b0[a] = (float)((xa - A.ray.dlo[a]) * lv.inv_h[a] + (0.5 - (double)s.brick.lo[a]));
-          db[a] = (float)(s.dt * r.d[a] * lv.inv_h[a]);
+          const float xm = fmaf(taum, rf.Dd[a], rf.Xe[a]);  // finest units
+          const float lo05 = 0.5f - (float)s.brick.lo[a];
+          b0[a] = fmaf(xm, lv.inv_sc, lo05);
+          db[a] = dtau * rf.Dd[a] * lv.inv_sc;
           s.leaf_lo[a] = lf.lo[a];
           s.bl[a] = (float)(lf.lo[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
           s.bh[a] = (float)(lf.hi[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
-          bmax = fmaxf(bmax, fabsf(b0[a]) + (float)n * fabsf(db[a]) + (float)s.brick.dim[a]);
+          const float ea = fabsf(rf.Dd[a]) * etau +
+                           ldexpf(fabsf(rf.Xe[a]) + fabsf(xm) + nfl * fabsf(dtau * rf.Dd[a]) + 1.0f, -21);
+          ex = fmaxf(ex, ea);
+          bmax = fmaxf(bmax, fabsf(b0[a]) + nfl * fabsf(db[a]) + (float)s.brick.dim[a]);
         }
-        // |FP32 beta - exact| <= u (|b0| + k |db| + |beta|) plus the rounding of the
-        // relative coordinates; 2^-21 (bmax + 2) bounds all of it with room to spare
-        s.margin = ldexpf(bmax + 2.0f, -21);
+        s.margin = ex * lv.inv_sc + ldexpf(bmax + 2.0f, -21);
         for (int k = 0; k < n; ++k) {
           float beta[3];
 #pragma unroll
           for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, db[a], b0[a]);
-          const float v = sample_value<ST, INTERP>(A, r, s, beta, k);
+          const float v = sample_value<ST, INTERP>(A, rx, s, beta, k);
           const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
           ++nsamp;
           if (c.w <= 0.0f) continue;
@@ -478,8 +615,8 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Rend
             float g[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              const float vp = neighbour_value<ST, INTERP>(A, r, s, beta, a, 1.0f, k);
-              const float vm = neighbour_value<ST, INTERP>(A, r, s, beta, a, -1.0f, k);
+              const float vp = neighbour_value<ST, INTERP>(A, rx, s, beta, a, 1.0f, k);
+              const float vm = neighbour_value<ST, INTERP>(A, rx, s, beta, a, -1.0f, k);
               g[a] = (vp - vm) * (0.5f * (float)lv.inv_h[a]);
             }
             const float gn = sqrtf(fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2])));
@@ -499,11 +636,13 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Rend
           C2 = fmaf(w, cb, C2);
           Acc += w;
           if (Acc >= A.ert_thresh) {
-            done = true;
+            pid1 = kPidOut;  // done
             break;
           }
         }
-        t0 = t1;
+        pid0 = pid1;
+        tau0 = tau1;
+        e0 = e1;
       }
     }
     A.out[(size_t)jr * A.ray.width + i] = make_float4(C0, C1, C2, Acc);

@@ -8,22 +8,25 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= A.ray.width || j >= A.ray.height) return;
   const size_t p = (size_t)j * A.ray.width + i;
-  Ray r;
-  make_ray(A.ray, i, j, r);
-  if (!r.hit) {
+  RayX rx;
+  if (!make_ray(A.ray, i, j, rx)) {
     A.seq_len[p] = 0;
     return;
   }
-  double t0 = r.t_in;
+  RayF rf;
+  make_frame(A.ray, rx, rf);
+  int pid0 = kPidIn;
+  float tau0 = 0.0f, e0 = 0.0f;
   int n = 0;
   unsigned long long status = 0;
-  while (t0 < r.t_out) {
+  while (pid0 != kPidOut) {
     if (n >= A.max_segments) {
       status |= kStatusCapacity;
       break;
     }
-    double t1 = r.t_out;
-    const int lid = descend(A.nodes, A.ray, r, t0, t1);
+    int pid1 = kPidOut;
+    float tau1 = rf.tau_out, e1 = rf.e_out;
+    const int lid = descend(A.nodes, A.ray, rx, rf, pid0, tau0, e0, pid1, tau1, e1);
     if (lid < 0) {
       status |= kStatusDevice;
       break;
@@ -32,12 +35,14 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
       const size_t q = p * (size_t)A.max_len + n;
       A.leaf_seq[q] = lid;
       if (A.t_seq) {
-        A.t_seq[2 * q] = t0;
-        A.t_seq[2 * q + 1] = t1;
+        A.t_seq[2 * q] = exact_t(A.ray, rx, pid0);
+        A.t_seq[2 * q + 1] = exact_t(A.ray, rx, pid1);
       }
     }
     ++n;
-    t0 = t1;
+    pid0 = pid1;
+    tau0 = tau1;
+    e0 = e1;
   }
   A.seq_len[p] = n <= A.max_len ? n : -1;
   if (status) atomicOr(A.counters + 1, status);
