@@ -51,7 +51,7 @@ def _march_sha() -> str:
     return h.hexdigest()[:12]
 
 
-def _profiled_traffic(shade: int, storage: str):
+def _profiled_traffic(shade: int, storage: str, size: int):
     """dram bytes per launch from the committed ncu summary, if it was taken on the
     current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "march_c2_traffic.md")
@@ -61,7 +61,8 @@ def _profiled_traffic(shade: int, storage: str):
     for line in open(path):
         parts = line.strip().split("|")
         parts = [p.strip() for p in parts if p.strip()]
-        if len(parts) >= 5 and parts[0] == sha and parts[1] == storage and parts[2] == str(shade):
+        if (len(parts) >= 5 and parts[0] == sha and parts[1] == storage and parts[2] == str(shade)
+                and parts[3] == str(size)):
             try:
                 return float(parts[4])
             except ValueError:
@@ -186,9 +187,11 @@ def run_reference(args):
         return
     import synth
 
-    hier = synth.make_c2(device="cpu")
+    # the same seeded inputs as the GPU arm (generated on the GPU when one is present, so
+    # both arms see bit-identical hierarchies); only the oracle's rendering is timed
+    hier = synth.make_c2(device=None)
     vmin, vmax = synth.amr.percentile_range(hier)
-    cam = synth.orbit_camera(2, SIZE, SIZE)
+    cam = synth.orbit_camera(2, args.size, args.size)
     tf = synth.ramp_tf()
     vals = []
     cb = None
@@ -201,19 +204,19 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(hier, args, "oracle"),
+            "config": _config(hier, args, "oracle", args.size),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def _config(hier, args, storage):
+def _config(hier, args, storage, size=SIZE):
     return {"workload": (f"c2: lognormal 5-level AMR, {hier.num_patches} patches, "
-                         f"{hier.n_cells():.3g} FP32 cells; {SIZE}x{SIZE} view; "
+                         f"{hier.n_cells():.3g} FP32 cells; {size}x{size} view; "
                          f"{'Phong' if args.shade else 'unshaded'} trilinear; step 0.5 h^l; "
                          f"ERT eps {args.ert}"),
-            "storage": storage, "image": [SIZE, SIZE], "shade": args.shade,
+            "storage": storage, "image": [size, size], "shade": args.shade,
             "l2": "inputs larger than L2: 602 MB of bricks vs 129 MB L2, no flush"}
 
 
@@ -229,6 +232,8 @@ def main():
     ap.add_argument("--ert", type=float, default=1e-4)
     ap.add_argument("--compare", type=int, default=1, help="time every storage briefly")
     ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--e2e", type=int, default=1, help="also time the host-buffer entry point")
+    ap.add_argument("--size", type=int, default=SIZE, help="image side (the metric is at 2048)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -248,7 +253,8 @@ def main():
 
     hier = synth.make_c2(device="cuda")
     vmin, vmax = synth.amr.percentile_range(hier)
-    cam = synth.orbit_camera(2 + rank, SIZE, SIZE)   # each rank its own view
+    size = args.size
+    cam = synth.orbit_camera(2 + rank, size, size)   # each rank its own view
     tf_h = synth.ramp_tf()
     tf = torch.as_tensor(tf_h, device="cuda")
     ctx = amr.from_hierarchy(hier)
@@ -257,7 +263,7 @@ def main():
     build_s = time.perf_counter() - t0
     st = ctx.amr_get_stats()
     params = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
-    out = torch.empty((SIZE, SIZE, 4), dtype=torch.float32, device="cuda")
+    out = torch.empty((size, size, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     samples = ctx.amr_render(cam, tf, params, out, count_samples=True)  # also checks status
@@ -293,17 +299,20 @@ def main():
     fps = 1e3 / ms_per_step
 
     # end to end through the public API with host buffers: TF in, image out, every step
-    tf_pin = torch.as_tensor(tf_h).pin_memory()
-    img_pin = torch.empty((SIZE, SIZE, 4), dtype=torch.float32).pin_memory()
-    ctx.amr_render_host(cam, tf_pin, params, img_pin)
-    _barrier(world)
-    torch.cuda.synchronize()
-    e0 = time.perf_counter()
-    for _ in range(args.steps):
+    e2e = None
+    if args.e2e:
+        tf_pin = torch.as_tensor(tf_h).pin_memory()
+        img_pin = torch.empty((size, size, 4), dtype=torch.float32).pin_memory()
         ctx.amr_render_host(cam, tf_pin, params, img_pin)
-    e2e_s = _max_over_ranks(world, time.perf_counter() - e0)
-    e2e = {"value": all_samples / e2e_s / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": int(tf_h.nbytes), "d2h_bytes_per_step": int(img_pin.numel() * 4)}
+        _barrier(world)
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.amr_render_host(cam, tf_pin, params, img_pin)
+        e2e_s = _max_over_ranks(world, time.perf_counter() - e0)
+        e2e = {"value": all_samples / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(tf_h.nbytes),
+               "d2h_bytes_per_step": int(img_pin.numel() * 4)}
 
     if rank != 0:
         return
@@ -311,7 +320,7 @@ def main():
     bps = BYTES_PER_SAMPLE[args.shade]
     achieved = samples * bps / (kern_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": _profiled_traffic(args.shade, args.storage),
+            "frac": achieved / peak, "traffic": _profiled_traffic(args.shade, args.storage, size),
             "peak_kind": peak_kind, "bytes_per_sample": bps,
             "kernel": "march_kernel<storage, trilinear, phong>",
             "kernel_ms": kern_ms}
@@ -347,7 +356,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(hier, args, args.storage), "gpu_launches": args.steps,
+            "config": _config(hier, args, args.storage, size), "gpu_launches": args.steps,
             "e2e": e2e, "roofline": roof, "clocks": clk, "extra": extra}
     if args.cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(hier, cam, tf_h, vmin, vmax, args.shade)
