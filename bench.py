@@ -216,7 +216,8 @@ def _config(hier, args, storage, size=SIZE):
                          f"{hier.n_cells():.3g} FP32 cells; {size}x{size} view; "
                          f"{'Phong' if args.shade else 'unshaded'} trilinear; step 0.5 h^l; "
                          f"ERT eps {args.ert}"),
-            "storage": storage, "image": [size, size], "shade": args.shade,
+            "storage": storage + ("+gradient bricks" if getattr(args, "gradient", 0) else ""),
+            "image": [size, size], "shade": args.shade,
             "l2": "inputs larger than L2: 602 MB of bricks vs 129 MB L2, no flush"}
 
 
@@ -234,6 +235,8 @@ def main():
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e", type=int, default=1, help="also time the host-buffer entry point")
     ap.add_argument("--size", type=int, default=SIZE, help="image side (the metric is at 2048)")
+    ap.add_argument("--schedule", type=int, default=0, help="0 per-ray loop, 1 warp wavefront")
+    ap.add_argument("--gradient", type=int, default=1, help="build gradient bricks")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -259,10 +262,11 @@ def main():
     tf = torch.as_tensor(tf_h, device="cuda")
     ctx = amr.from_hierarchy(hier)
     t0 = time.perf_counter()
-    ctx.amr_build_kdtree(args.storage)
+    ctx.amr_build_kdtree(args.storage, gradient=bool(args.gradient))
     build_s = time.perf_counter() - t0
     st = ctx.amr_get_stats()
-    params = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
+    params = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
+                                    schedule=args.schedule)
     out = torch.empty((size, size, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -322,18 +326,23 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": _profiled_traffic(args.shade, args.storage, size),
             "peak_kind": peak_kind, "bytes_per_sample": bps,
-            "kernel": "march_kernel<storage, trilinear, phong>",
+            "kernel": ("march_kernel" if args.schedule == 0 else "wave_kernel") +
+                      "<storage, trilinear, phong>",
             "kernel_ms": kern_ms}
     extra = {"frames_per_s": fps, "samples_per_frame": samples, "build_s": build_s,
              "tree": {"nodes": st.num_nodes, "leaves": st.num_leaves, "depth": st.max_depth,
                       "brick_mb": st.brick_bytes / 1e6}}
     if args.compare:
         comp = {}
-        for s in ("ptr", "texobj", "atlas_linear", "atlas_tex3d"):
+        for s, grad in (("ptr", 0), ("ptr", 1), ("texobj", 0), ("texobj", 1),
+                        ("atlas_linear", 0), ("atlas_linear", 1), ("atlas_tex3d", 0),
+                        ("atlas_tex3d", 1)):
             c2 = amr.from_hierarchy(hier)
-            c2.amr_build_kdtree(s)
-            for shade in (0, 1):
-                p2 = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=shade, ert_eps=args.ert)
+            c2.amr_build_kdtree(s, gradient=bool(grad))
+            combos = ((0, 0), (1, 0), (0, 1), (1, 1)) if not grad else ((1, 0), (1, 1))
+            for shade, sched in combos:
+                p2 = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=shade, ert_eps=args.ert,
+                                            schedule=sched)
                 n2 = c2.amr_render(cam, tf, p2, out, count_samples=True)
                 for _ in range(2):
                     c2.amr_render(cam, tf, p2, out)
@@ -344,7 +353,8 @@ def main():
                 b.record(stream)
                 torch.cuda.synchronize()
                 ms = a.elapsed_time(b) / 3
-                comp[f"{s}/{'phong' if shade else 'plain'}"] = {
+                comp[f"{s}{'+grad' if grad else ''}/{'phong' if shade else 'plain'}/"
+                     f"{'wave' if sched else 'ray'}"] = {
                     "gsamples_s": n2 / ms / 1e6, "ms": ms,
                     "frac_hbm": n2 * BYTES_PER_SAMPLE[shade] / (ms * 1e-3) / 1e9 / peak}
             if s == "atlas_linear":

@@ -56,7 +56,12 @@ typedef enum {
   AMR_STORE_PTR = 0,          /* per-patch table of device pointers into one brick pool */
   AMR_STORE_TEXOBJ = 1,       /* per-patch table of cudaTextureObject_t, one 3D array each */
   AMR_STORE_ATLAS_LINEAR = 2, /* NFDH-packed atlas (Sec. 4.1) in linear device memory */
-  AMR_STORE_ATLAS_TEX3D = 3   /* NFDH-packed atlas in one 3D cudaArray, read as a texture */
+  AMR_STORE_ATLAS_TEX3D = 3,  /* NFDH-packed atlas in one 3D cudaArray, read as a texture */
+  /* flag, OR-ed with a strategy: also build gradient bricks (float4 per cell: value and the
+   * three central differences of the cell values, 4x the brick bytes).  Shaded trilinear
+   * renders then read one float4 stencil per opaque sample instead of 32 cells whenever
+   * all six gradient neighbours lie in the sample's leaf; results are unchanged. */
+  AMR_STORE_GRADIENT = 0x100
 } amr_storage;
 
 /* Pinhole camera.  Pixel (i, j), row 0 at the top, has the ray o = eye,
@@ -83,10 +88,15 @@ typedef struct {
   int32_t rows;       /* number of rows; <= 0: all rows from row0 */
   int32_t skip;       /* 0: none; 1: exact leaf min/max empty-space skipping */
   int32_t max_segments; /* per-ray segment bound; <= 0: 4 * nodes + 64 */
+  int32_t schedule;   /* 0: one loop per ray (default); 1: warp wavefront (the samples of a
+                         warp's current segments spread over its lanes, shading on the
+                         compacted opaque samples; pays off when rays diverge, e.g. small
+                         views of a large volume) */
 } amr_render_params;
 
 /* Fills p with the defaults: step 0.5, kappa 8, ert_eps 1e-4, vmin 0, vmax 1, ka 0.3,
- * kd 0.6, ks 0.3, shininess 32, gamma 1e-3, trilinear, unshaded, all rows, no skip. */
+ * kd 0.6, ks 0.3, shininess 32, gamma 1e-3, trilinear, unshaded, all rows, no skip,
+ * per-ray schedule. */
 void amr_default_params(amr_render_params* p);
 
 /* Create a context from an AMR hierarchy (Sec. 2: h^l = h^0 / r^l, patches Gamma^l_m).
@@ -104,7 +114,8 @@ amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double dom
 /* Build the kD-tree (Sec. 3.1: min-crossing planes, balanced tie-break, level-by-level
  * refinement), the per-patch bricks with a one-cell halo (Sec. 4: one brick per subgrid),
  * the chosen storage (Sec. 4.1 packing / 4.2 handle table) and upload everything on
- * `cuda_stream`.  The call returns after the uploads complete. */
+ * `cuda_stream`.  `storage` is an amr_storage strategy, optionally OR AMR_STORE_GRADIENT.
+ * The call returns after the uploads complete. */
 amr_status amr_build_kdtree(amr_ctx* ctx, amr_storage storage, void* cuda_stream);
 
 /* Host-only part of amr_build_kdtree (tree, bricks, packing), for inspecting the tree

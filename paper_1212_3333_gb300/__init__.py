@@ -13,8 +13,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import (AMR_STORE_ATLAS_LINEAR, AMR_STORE_ATLAS_TEX3D, AMR_STORE_PTR,  # noqa: F401
-                   AMR_STORE_TEXOBJ, STORAGES, amr_camera, amr_render_params, amr_stats)
+from ._lib import (AMR_STORE_ATLAS_LINEAR, AMR_STORE_ATLAS_TEX3D, AMR_STORE_GRADIENT,  # noqa: F401
+                   AMR_STORE_PTR, AMR_STORE_TEXOBJ, STORAGES, amr_camera, amr_render_params,
+                   amr_stats)
 
 
 class AmrError(RuntimeError):
@@ -72,12 +73,17 @@ class AmrContext:
         self._lib = _lib.load()
 
     # ----------------------------------------------------------------- lifecycle
-    def amr_build_kdtree(self, storage="ptr", stream=None) -> None:
+    @staticmethod
+    def _storage_code(storage, gradient: bool) -> int:
         st = STORAGES[storage] if isinstance(storage, str) else int(storage)
+        return st | (AMR_STORE_GRADIENT if gradient else 0)
+
+    def amr_build_kdtree(self, storage="ptr", stream=None, gradient: bool = False) -> None:
+        st = self._storage_code(storage, gradient)
         _check(self._lib.amr_build_kdtree(self._h, st, C.c_void_p(_stream_ptr(stream))), self._h)
 
-    def amr_build_host(self, storage="ptr") -> None:
-        st = STORAGES[storage] if isinstance(storage, str) else int(storage)
+    def amr_build_host(self, storage="ptr", gradient: bool = False) -> None:
+        st = self._storage_code(storage, gradient)
         _check(self._lib.amr_build_host(self._h, st), self._h)
 
     def amr_destroy(self) -> None:

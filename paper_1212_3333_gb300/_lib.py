@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "AMR_OK", 1: "AMR_ERR_ARG", 2: "AMR_ERR_OVERLAP", 3: "AMR_ERR
 
 AMR_F32, AMR_F16, AMR_BF16 = 0, 1, 2
 AMR_STORE_PTR, AMR_STORE_TEXOBJ, AMR_STORE_ATLAS_LINEAR, AMR_STORE_ATLAS_TEX3D = 0, 1, 2, 3
+AMR_STORE_GRADIENT = 0x100
 STORAGES = {"ptr": AMR_STORE_PTR, "texobj": AMR_STORE_TEXOBJ,
             "atlas_linear": AMR_STORE_ATLAS_LINEAR, "atlas_tex3d": AMR_STORE_ATLAS_TEX3D}
 
@@ -36,7 +37,7 @@ class amr_render_params(C.Structure):
                 ("kd", C.c_double), ("ks", C.c_double), ("shininess", C.c_double),
                 ("gamma", C.c_double), ("interp", C.c_int32), ("shade", C.c_int32),
                 ("row0", C.c_int32), ("rows", C.c_int32), ("skip", C.c_int32),
-                ("max_segments", C.c_int32)]
+                ("max_segments", C.c_int32), ("schedule", C.c_int32)]
 
 
 class amr_stats(C.Structure):

@@ -42,11 +42,12 @@ struct DLeaf {
 struct DPatch {
   long long base;      // pointer table: device address of the brick; linear atlas: element
                        // offset; texture table: cudaTextureObject_t; 3D atlas: unused
+  long long gbase;     // the same for the gradient brick (float4 per cell), 0 if absent
   int32_t sy, sz;      // element strides of y and z (linear storages)
   int32_t lo[3];       // patch box lo, level cells (brick index = cell - lo + 1)
   int32_t dim[3];      // brick extent with halo: nx+2, ny+2, nz+2
   int32_t org[3];      // 3D atlas: texel origin of the brick
-  int32_t pad;
+  int32_t pad[3];
 };
 
 struct DLevel {
@@ -77,7 +78,9 @@ struct RenderArgs {
   const DLeaf* leaves;
   const DPatch* patches;
   const void* pool;            // linear atlas base (element type of the storage)
+  const float4* gpool;         // linear atlas of gradient bricks (float4 per cell)
   cudaTextureObject_t atlas;   // 3D atlas texture
+  cudaTextureObject_t gatlas;  // 3D atlas of gradient bricks
   const float4* tf;            // transfer function [tf_n]
   int32_t tf_n;
   int32_t max_segments;

@@ -201,6 +201,35 @@ amr_status build_bricks(amr_ctx* c) {
   return AMR_OK;
 }
 
+// Gradient bricks: per cell (V, V(c+x) - V(c-x), V(c+y) - V(c-y), V(c+z) - V(c-z)).  A one-cell
+// shift commutes with trilinear interpolation, so interpolating these differences at beta
+// gives exactly the central difference S(beta + e_a) - S(beta - e_a) of the trilinear
+// field whenever both neighbours read this brick.  Outer-layer cells (no neighbour on one
+// side) hold zero differences; the kernels use the gradient brick only away from them.
+amr_status build_gradient_bricks(amr_ctx* c) {
+  const size_t P = c->patches.size();
+  c->gbricks.assign(P, {});
+  for (size_t p = 0; p < P; ++p) {
+    const int64_t d0 = c->patches[p].n[0] + 2, d1 = c->patches[p].n[1] + 2,
+                  d2 = c->patches[p].n[2] + 2;
+    const std::vector<float>& v = c->bricks[p];
+    std::vector<float4>& g = c->gbricks[p];
+    g.resize(v.size());
+    auto at = [&](int64_t i, int64_t j, int64_t k) { return v[(size_t)(i + d0 * (j + d1 * k))]; };
+    for (int64_t k = 0; k < d2; ++k)
+      for (int64_t j = 0; j < d1; ++j)
+        for (int64_t i = 0; i < d0; ++i) {
+          float4 q;
+          q.x = at(i, j, k);
+          q.y = (i > 0 && i < d0 - 1) ? at(i + 1, j, k) - at(i - 1, j, k) : 0.0f;
+          q.z = (j > 0 && j < d1 - 1) ? at(i, j + 1, k) - at(i, j - 1, k) : 0.0f;
+          q.w = (k > 0 && k < d2 - 1) ? at(i, j, k + 1) - at(i, j, k - 1) : 0.0f;
+          g[(size_t)(i + d0 * (j + d1 * k))] = q;
+        }
+  }
+  return AMR_OK;
+}
+
 // Next-fit decreasing height in 3D over square bases; returns the container height.
 static int64_t nfdh(const std::vector<std::array<int64_t, 3>>& ext, const std::vector<int>& order,
                     int64_t W, std::vector<int64_t>& org) {

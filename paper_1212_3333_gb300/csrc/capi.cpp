@@ -101,6 +101,7 @@ void amr_default_params(amr_render_params* p) {
   p->rows = 0;
   p->skip = 0;
   p->max_segments = 0;
+  p->schedule = 0;
 }
 
 amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double domain_lo[3],
@@ -188,9 +189,12 @@ amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double dom
   return AMR_OK;
 }
 
-amr_status amr_build_host(amr_ctx* c, amr_storage storage) {
+amr_status amr_build_host(amr_ctx* c, amr_storage storage_flags) {
   if (!c) return AMR_ERR_ARG;
-  if (storage < AMR_STORE_PTR || storage > AMR_STORE_ATLAS_TEX3D)
+  const int storage = (int)storage_flags & 0xff;
+  const bool gradient = ((int)storage_flags & AMR_STORE_GRADIENT) != 0;
+  if (storage < AMR_STORE_PTR || storage > AMR_STORE_ATLAS_TEX3D ||
+      ((int)storage_flags & ~(0xff | AMR_STORE_GRADIENT)))
     return fail(c, AMR_ERR_ARG, "unknown storage");
   auto t0 = std::chrono::steady_clock::now();
   try {
@@ -208,11 +212,17 @@ amr_status amr_build_host(amr_ctx* c, amr_storage storage) {
       amr_status s = pack_atlas(c);
       if (s != AMR_OK) return s;
     }
+    if (gradient && c->gbricks.empty()) {
+      amr_status s = build_gradient_bricks(c);
+      if (s != AMR_OK) return s;
+    }
   } catch (const std::bad_alloc&) {
     return fail(c, AMR_ERR_OOM, "out of host memory during the build");
   }
-  if (c->storage != (int)storage && c->device_built) release_device(c);
-  c->storage = (int)storage;
+  if ((c->storage != storage || c->want_gradient != gradient) && c->device_built)
+    release_device(c);
+  c->storage = storage;
+  c->want_gradient = gradient;
   c->build_seconds +=
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   c->err.clear();
@@ -244,6 +254,7 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   if (!(p->kappa >= 0.0)) return fail(c, AMR_ERR_ARG, "kappa must be non-negative");
   if (p->interp != 0 && p->interp != 1) return fail(c, AMR_ERR_ARG, "unknown interp");
   if (p->shade != 0 && p->shade != 1) return fail(c, AMR_ERR_ARG, "unknown shade");
+  if (p->schedule != 0 && p->schedule != 1) return fail(c, AMR_ERR_ARG, "unknown schedule");
   if (p->row0 < 0 || p->row0 >= cam->height) return fail(c, AMR_ERR_ARG, "row0 out of range");
   int rows = p->rows <= 0 ? cam->height - p->row0 : std::min(p->rows, cam->height - p->row0);
   std::memset(a, 0, sizeof *a);
@@ -253,7 +264,9 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->leaves = c->dev.leaves;
   a->patches = c->dev.patches;
   a->pool = c->dev.pool;
+  a->gpool = (const float4*)c->dev.gpool;
   a->atlas = c->dev.atlas_tex;
+  a->gatlas = c->dev.gatlas_tex;
   a->tf_n = tf_n;
   int64_t ms = p->max_segments > 0 ? p->max_segments : 4 * (int64_t)c->tree.axis.size() + 64;
   a->max_segments = (int32_t)std::min<int64_t>(ms, INT32_MAX);
@@ -269,6 +282,13 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->gfloor_num = (float)(p->gamma * (p->vmax - p->vmin));
   a->counters = c->dev.counters;
   return AMR_OK;
+}
+
+// shading variant: 2 = Phong reading the gradient bricks (trilinear only), when built
+static int kernel_shade(const amr_ctx* c, const amr_render_params* p) {
+  if (p->shade && p->interp == AMR_INTERP_TRILINEAR && c->want_gradient && c->dev.gpool_bytes)
+    return 2;
+  return p->shade;
 }
 
 static amr_status finish_render(amr_ctx* c, cudaStream_t st, uint64_t* samples_out) {
@@ -296,7 +316,8 @@ amr_status amr_render(amr_ctx* c, const amr_camera* cam, const float* tf_rgba_de
   a.out = reinterpret_cast<float4*>(out_rgba_dev);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   CK(cudaMemsetAsync(c->dev.counters, 0, 2 * sizeof(unsigned long long), st));
-  s = launch_render(c, a, c->storage, params->interp, params->shade, cuda_stream);
+  s = launch_render(c, a, c->storage, params->interp, kernel_shade(c, params), params->schedule,
+                    cuda_stream);
   if (s != AMR_OK) return s;
   return finish_render(c, st, samples_out);
 }
@@ -330,7 +351,8 @@ amr_status amr_render_host(amr_ctx* c, const amr_camera* cam, const float* tf_rg
   a.tf = d.tf_scratch;
   a.out = d.img_scratch;
   CK(cudaMemsetAsync(d.counters, 0, 2 * sizeof(unsigned long long), st));
-  s = launch_render(c, a, c->storage, params->interp, params->shade, cuda_stream);
+  s = launch_render(c, a, c->storage, params->interp, kernel_shade(c, params), params->schedule,
+                    cuda_stream);
   if (s != AMR_OK) return s;
   CK(cudaMemcpyAsync(out_rgba_host, d.img_scratch, img_bytes, cudaMemcpyDeviceToHost, st));
   if (samples_out) return finish_render(c, st, samples_out);

@@ -38,6 +38,12 @@ struct DeviceState {
   DPatch* patches = nullptr;
   void* pool = nullptr;  // brick pool (pointer table) or linear atlas
   size_t pool_bytes = 0;
+  void* gpool = nullptr; // gradient bricks, same layout, float4 per cell
+  size_t gpool_bytes = 0;
+  std::vector<void*> garrays;                    // gradient cudaArray_t per patch
+  std::vector<cudaTextureObject_t> gtexobjs;
+  void* gatlas_array = nullptr;
+  cudaTextureObject_t gatlas_tex = 0;
   std::vector<void*> arrays;                     // cudaArray_t per patch (texture table)
   std::vector<cudaTextureObject_t> texobjs;
   void* atlas_array = nullptr;                   // cudaArray_t of the 3D atlas
@@ -62,6 +68,8 @@ struct amr_ctx {
   int64_t root[6] = {0, 0, 0, 0, 0, 0};
   amr::Tree tree;
   std::vector<std::vector<float>> bricks;  // per patch, with halo
+  bool want_gradient = false;              // build gradient bricks too
+  std::vector<std::vector<float4>> gbricks; // per patch: value and central differences
   std::vector<float> leaf_vmin, leaf_vmax;
   amr::Packing packing;
   int storage = -1;
@@ -79,13 +87,14 @@ amr_status validate_hierarchy(amr_ctx* c);
 amr_status build_tree(amr_ctx* c);
 // bricks.cpp
 amr_status build_bricks(amr_ctx* c);
+amr_status build_gradient_bricks(amr_ctx* c);
 amr_status pack_atlas(amr_ctx* c);
 // device.cpp
 amr_status upload(amr_ctx* c, void* stream);
 void release_device(amr_ctx* c);
 // kernels (march.cu)
 amr_status launch_render(amr_ctx* c, const RenderArgs& a, int storage, int interp, int shade,
-                         void* stream);
+                         int schedule, void* stream);
 amr_status launch_trace(amr_ctx* c, const TraceArgs& a, void* stream);
 void fill_levels(const amr_ctx* c, DLevel* lv, double step_factor);
 void fill_ray(const amr_ctx* c, const amr_camera* cam, int row0, int rows, RayArgs* ra);

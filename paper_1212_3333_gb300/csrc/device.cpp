@@ -44,17 +44,141 @@ std::vector<DNode> layout_nodes(const Tree& t) {
   return out;
 }
 
+// Bricks of element type T (float values, or float4 value + central differences) in the
+// layout of the context's storage strategy; fills base (or gbase) of every patch record.
+template <typename T>
+amr_status upload_bricks(amr_ctx* c, const std::vector<std::vector<T>>& bricks,
+                         std::vector<DPatch>& pt, bool gradient, cudaStream_t stream) {
+  DeviceState& d = c->dev;
+  const size_t P = c->patches.size();
+  const int storage = c->storage;
+  void*& pool = gradient ? d.gpool : d.pool;
+  size_t& pool_bytes = gradient ? d.gpool_bytes : d.pool_bytes;
+  auto set_base = [&](size_t p, long long v) { (gradient ? pt[p].gbase : pt[p].base) = v; };
+  const cudaChannelFormatDesc ch = cudaCreateChannelDesc<T>();
+  cudaTextureDesc td;
+  std::memset(&td, 0, sizeof td);
+  td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+  td.filterMode = cudaFilterModePoint;
+  td.readMode = cudaReadModeElementType;
+  td.normalizedCoords = 0;
+  if (storage == AMR_STORE_PTR) {
+    // one pool, each brick 128-byte aligned; the table holds the device addresses
+    std::vector<size_t> off(P);
+    size_t elems = 0;
+    const size_t align = 128 / sizeof(T);
+    for (size_t p = 0; p < P; ++p) {
+      off[p] = elems;
+      elems += (bricks[p].size() + align - 1) / align * align;
+    }
+    pool_bytes = elems * sizeof(T);
+    CK(cudaMalloc(&pool, pool_bytes));
+    for (size_t p = 0; p < P; ++p) {
+      T* dst = (T*)pool + off[p];
+      CK(cudaMemcpyAsync(dst, bricks[p].data(), bricks[p].size() * sizeof(T),
+                         cudaMemcpyHostToDevice, stream));
+      set_base(p, (long long)(uintptr_t)dst);
+      pt[p].sy = pt[p].dim[0];
+      pt[p].sz = pt[p].dim[0] * pt[p].dim[1];
+    }
+  } else if (storage == AMR_STORE_TEXOBJ) {
+    std::vector<void*>& arrays = gradient ? d.garrays : d.arrays;
+    std::vector<cudaTextureObject_t>& tex = gradient ? d.gtexobjs : d.texobjs;
+    arrays.assign(P, nullptr);
+    tex.assign(P, 0);
+    pool_bytes = 0;
+    for (size_t p = 0; p < P; ++p) {
+      cudaExtent ext = make_cudaExtent(pt[p].dim[0], pt[p].dim[1], pt[p].dim[2]);
+      cudaArray_t arr = nullptr;
+      CK(cudaMalloc3DArray(&arr, &ch, ext));
+      arrays[p] = arr;
+      cudaMemcpy3DParms cp;
+      std::memset(&cp, 0, sizeof cp);
+      cp.srcPtr = make_cudaPitchedPtr((void*)bricks[p].data(), pt[p].dim[0] * sizeof(T),
+                                      pt[p].dim[0], pt[p].dim[1]);
+      cp.dstArray = arr;
+      cp.extent = ext;
+      cp.kind = cudaMemcpyHostToDevice;
+      CK(cudaMemcpy3DAsync(&cp, stream));
+      cudaResourceDesc rd;
+      std::memset(&rd, 0, sizeof rd);
+      rd.resType = cudaResourceTypeArray;
+      rd.res.array.array = arr;
+      cudaTextureObject_t t = 0;
+      CK(cudaCreateTextureObject(&t, &rd, &td, nullptr));
+      tex[p] = t;
+      set_base(p, (long long)t);
+      pool_bytes += bricks[p].size() * sizeof(T);
+    }
+    CK(cudaStreamSynchronize(stream));
+  } else {
+    // packed atlas (NFDH), linear memory or one 3D array
+    const int64_t AX = c->packing.dims[0], AY = c->packing.dims[1], AZ = c->packing.dims[2];
+    const size_t total = (size_t)(AX * AY * AZ);
+    std::vector<T> img(total);
+    std::memset((void*)img.data(), 0, total * sizeof(T));
+    for (size_t p = 0; p < P; ++p) {
+      const int64_t* o = &c->packing.org[3 * p];
+      const int64_t d0 = pt[p].dim[0], d1 = pt[p].dim[1], d2 = pt[p].dim[2];
+      for (int64_t k = 0; k < d2; ++k)
+        for (int64_t j = 0; j < d1; ++j)
+          std::memcpy((void*)&img[(size_t)(o[0] + AX * ((o[1] + j) + AY * (o[2] + k)))],
+                      &bricks[p][(size_t)(d0 * (j + d1 * k))], sizeof(T) * (size_t)d0);
+      for (int a = 0; a < 3; ++a) pt[p].org[a] = (int32_t)o[a];
+      set_base(p, (long long)(o[0] + AX * (o[1] + AY * o[2])));
+      pt[p].sy = (int32_t)AX;
+      pt[p].sz = (int32_t)(AX * AY);
+    }
+    pool_bytes = total * sizeof(T);
+    if (storage == AMR_STORE_ATLAS_LINEAR) {
+      CK(cudaMalloc(&pool, pool_bytes));
+      CK(cudaMemcpyAsync(pool, img.data(), pool_bytes, cudaMemcpyHostToDevice, stream));
+      CK(cudaStreamSynchronize(stream));
+    } else {
+      cudaDeviceProp prop;
+      CK(cudaGetDeviceProperties(&prop, d.device));
+      if (AX > prop.maxTexture3D[0] || AY > prop.maxTexture3D[1] || AZ > prop.maxTexture3D[2])
+        return fail(c, AMR_ERR_CAPACITY, "atlas exceeds the 3D texture extent limit");
+      cudaExtent ext = make_cudaExtent(AX, AY, AZ);
+      cudaArray_t arr = nullptr;
+      CK(cudaMalloc3DArray(&arr, &ch, ext));
+      (gradient ? d.gatlas_array : d.atlas_array) = arr;
+      cudaMemcpy3DParms cp;
+      std::memset(&cp, 0, sizeof cp);
+      cp.srcPtr = make_cudaPitchedPtr(img.data(), AX * sizeof(T), AX, AY);
+      cp.dstArray = arr;
+      cp.extent = ext;
+      cp.kind = cudaMemcpyHostToDevice;
+      CK(cudaMemcpy3DAsync(&cp, stream));
+      cudaResourceDesc rd;
+      std::memset(&rd, 0, sizeof rd);
+      rd.resType = cudaResourceTypeArray;
+      rd.res.array.array = arr;
+      CK(cudaCreateTextureObject(gradient ? &d.gatlas_tex : &d.atlas_tex, &rd, &td, nullptr));
+      CK(cudaStreamSynchronize(stream));
+    }
+  }
+  return AMR_OK;
+}
+
 }  // namespace
 
 void release_device(amr_ctx* c) {
   DeviceState& d = c->dev;
   if (d.device >= 0) cudaSetDevice(d.device);
   if (d.atlas_tex) cudaDestroyTextureObject(d.atlas_tex);
+  if (d.gatlas_tex) cudaDestroyTextureObject(d.gatlas_tex);
   for (auto t : d.texobjs)
+    if (t) cudaDestroyTextureObject(t);
+  for (auto t : d.gtexobjs)
     if (t) cudaDestroyTextureObject(t);
   for (void* a : d.arrays)
     if (a) cudaFreeArray((cudaArray_t)a);
+  for (void* a : d.garrays)
+    if (a) cudaFreeArray((cudaArray_t)a);
   if (d.atlas_array) cudaFreeArray((cudaArray_t)d.atlas_array);
+  if (d.gatlas_array) cudaFreeArray((cudaArray_t)d.gatlas_array);
+  cudaFree(d.gpool);
   cudaFree(d.nodes);
   cudaFree(d.leaves);
   cudaFree(d.patches);
@@ -101,111 +225,11 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   CK(cudaMalloc(&d.counters, 4 * sizeof(unsigned long long)));
   CK(cudaMemsetAsync(d.counters, 0, 4 * sizeof(unsigned long long), stream));
 
-  size_t brick_elems = 0;
-  const int storage = c->storage;
-  if (storage == AMR_STORE_PTR) {
-    // one pool, each brick 128-byte aligned; the table holds the device addresses
-    std::vector<size_t> off(P);
-    for (size_t p = 0; p < P; ++p) {
-      off[p] = brick_elems;
-      brick_elems += (c->bricks[p].size() + 31) & ~(size_t)31;
-    }
-    d.pool_bytes = brick_elems * sizeof(float);
-    CK(cudaMalloc(&d.pool, d.pool_bytes));
-    for (size_t p = 0; p < P; ++p) {
-      float* dst = (float*)d.pool + off[p];
-      CK(cudaMemcpyAsync(dst, c->bricks[p].data(), c->bricks[p].size() * sizeof(float),
-                         cudaMemcpyHostToDevice, stream));
-      pt[p].base = (long long)(uintptr_t)dst;
-      pt[p].sy = pt[p].dim[0];
-      pt[p].sz = pt[p].dim[0] * pt[p].dim[1];
-    }
-  } else if (storage == AMR_STORE_TEXOBJ) {
-    d.arrays.assign(P, nullptr);
-    d.texobjs.assign(P, 0);
-    cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
-    for (size_t p = 0; p < P; ++p) {
-      cudaExtent ext = make_cudaExtent(pt[p].dim[0], pt[p].dim[1], pt[p].dim[2]);
-      cudaArray_t arr = nullptr;
-      CK(cudaMalloc3DArray(&arr, &ch, ext));
-      d.arrays[p] = arr;
-      cudaMemcpy3DParms cp;
-      std::memset(&cp, 0, sizeof cp);
-      cp.srcPtr = make_cudaPitchedPtr(c->bricks[p].data(), pt[p].dim[0] * sizeof(float),
-                                      pt[p].dim[0], pt[p].dim[1]);
-      cp.dstArray = arr;
-      cp.extent = ext;
-      cp.kind = cudaMemcpyHostToDevice;
-      CK(cudaMemcpy3DAsync(&cp, stream));
-      cudaResourceDesc rd;
-      std::memset(&rd, 0, sizeof rd);
-      rd.resType = cudaResourceTypeArray;
-      rd.res.array.array = arr;
-      cudaTextureDesc td;
-      std::memset(&td, 0, sizeof td);
-      td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
-      td.filterMode = cudaFilterModePoint;
-      td.readMode = cudaReadModeElementType;
-      td.normalizedCoords = 0;
-      cudaTextureObject_t tex = 0;
-      CK(cudaCreateTextureObject(&tex, &rd, &td, nullptr));
-      d.texobjs[p] = tex;
-      pt[p].base = (long long)tex;
-      brick_elems += c->bricks[p].size();
-    }
-  } else {
-    // packed atlas (NFDH), linear memory or one 3D array
-    const int64_t AX = c->packing.dims[0], AY = c->packing.dims[1], AZ = c->packing.dims[2];
-    const size_t total = (size_t)(AX * AY * AZ);
-    std::vector<float> img(total, 0.0f);
-    for (size_t p = 0; p < P; ++p) {
-      const int64_t* o = &c->packing.org[3 * p];
-      const int64_t d0 = pt[p].dim[0], d1 = pt[p].dim[1], d2 = pt[p].dim[2];
-      for (int64_t k = 0; k < d2; ++k)
-        for (int64_t j = 0; j < d1; ++j)
-          std::memcpy(&img[(size_t)(o[0] + AX * ((o[1] + j) + AY * (o[2] + k)))],
-                      &c->bricks[p][(size_t)(d0 * (j + d1 * k))], sizeof(float) * (size_t)d0);
-      for (int a = 0; a < 3; ++a) pt[p].org[a] = (int32_t)o[a];
-      pt[p].base = (long long)(o[0] + AX * (o[1] + AY * o[2]));
-      pt[p].sy = (int32_t)AX;
-      pt[p].sz = (int32_t)(AX * AY);
-    }
-    brick_elems = total;
-    if (storage == AMR_STORE_ATLAS_LINEAR) {
-      d.pool_bytes = total * sizeof(float);
-      CK(cudaMalloc(&d.pool, d.pool_bytes));
-      CK(cudaMemcpyAsync(d.pool, img.data(), d.pool_bytes, cudaMemcpyHostToDevice, stream));
-      CK(cudaStreamSynchronize(stream));
-    } else {
-      cudaDeviceProp prop;
-      CK(cudaGetDeviceProperties(&prop, d.device));
-      if (AX > prop.maxTexture3D[0] || AY > prop.maxTexture3D[1] || AZ > prop.maxTexture3D[2])
-        return fail(c, AMR_ERR_CAPACITY, "atlas exceeds the 3D texture extent limit");
-      cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
-      cudaExtent ext = make_cudaExtent(AX, AY, AZ);
-      cudaArray_t arr = nullptr;
-      CK(cudaMalloc3DArray(&arr, &ch, ext));
-      d.atlas_array = arr;
-      cudaMemcpy3DParms cp;
-      std::memset(&cp, 0, sizeof cp);
-      cp.srcPtr = make_cudaPitchedPtr(img.data(), AX * sizeof(float), AX, AY);
-      cp.dstArray = arr;
-      cp.extent = ext;
-      cp.kind = cudaMemcpyHostToDevice;
-      CK(cudaMemcpy3DAsync(&cp, stream));
-      cudaResourceDesc rd;
-      std::memset(&rd, 0, sizeof rd);
-      rd.resType = cudaResourceTypeArray;
-      rd.res.array.array = arr;
-      cudaTextureDesc td;
-      std::memset(&td, 0, sizeof td);
-      td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
-      td.filterMode = cudaFilterModePoint;
-      td.readMode = cudaReadModeElementType;
-      td.normalizedCoords = 0;
-      CK(cudaCreateTextureObject(&d.atlas_tex, &rd, &td, nullptr));
-      CK(cudaStreamSynchronize(stream));
-    }
+  amr_status st = upload_bricks<float>(c, c->bricks, pt, false, stream);
+  if (st != AMR_OK) return st;
+  if (c->want_gradient) {
+    st = upload_bricks<float4>(c, c->gbricks, pt, true, stream);
+    if (st != AMR_OK) return st;
   }
   CK(cudaMemcpyAsync(d.nodes, nodes.data(), nodes.size() * sizeof(DNode), cudaMemcpyHostToDevice,
                      stream));
@@ -214,7 +238,6 @@ amr_status upload(amr_ctx* c, void* stream_v) {
                        stream));
   CK(cudaMemcpyAsync(d.patches, pt.data(), P * sizeof(DPatch), cudaMemcpyHostToDevice, stream));
   CK(cudaStreamSynchronize(stream));
-  d.pool_bytes = brick_elems * sizeof(float);
   c->device_built = true;
   return AMR_OK;
 }

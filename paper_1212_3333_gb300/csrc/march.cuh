@@ -95,7 +95,7 @@ __device__ __forceinline__ bool make_ray(const RayArgs& A, int i, int j, RayX& r
 }
 
 // Exact FP64 ray parameter of a plane id (the reference's t_s, t_in or t_out).
-static __device__ __noinline__ double exact_t(const RayArgs& A, const RayX& r, int pid) {
+__device__ __forceinline__ double exact_t(const RayArgs& A, const RayX& r, int pid) {
   if (pid == kPidIn) return r.t_in;
   if (pid == kPidOut) return r.t_out;
   const int ax = pid & 3;
@@ -105,6 +105,50 @@ static __device__ __noinline__ double exact_t(const RayArgs& A, const RayX& r, i
   const double sw = __dadd_rn(sel3(ax, A.dlo[0], A.dlo[1], A.dlo[2]),
                               __dmul_rn((double)s, sel3(ax, A.hf[0], A.hf[1], A.hf[2])));
   return __dmul_rn(__dsub_rn(sw, o), __ddiv_rn(1.0, d));
+}
+
+// The rare exact paths rebuild the FP64 ray of their pixel (make_ray is deterministic)
+// instead of keeping it live, so the hot loops hold FP32 state only.
+
+// Exact descent decision for plane `pid` against (t0, t1) = (pid0, pid1):
+// 0 near only, 1 far only, 2 near with t1 = t_s.
+static __device__ __noinline__ int exact_decide(const RayArgs& A, int px, int py, int pid,
+                                                int pid0, int pid1) {
+  RayX r;
+  make_ray(A, px, py, r);
+  const double t = exact_t(A, r, pid);
+  if (t >= exact_t(A, r, pid1)) return 0;
+  if (t <= exact_t(A, r, pid0)) return 1;
+  return 2;
+}
+
+// Exact sample count n = max(1, ceil(len / step)) of the segment (pid0, pid1).
+static __device__ __noinline__ int exact_count(const RayArgs& A, int px, int py, int pid0,
+                                               int pid1, double step) {
+  RayX r;
+  make_ray(A, px, py, r);
+  const double t0 = exact_t(A, r, pid0), t1 = exact_t(A, r, pid1);
+  const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(r.d[0], r.d[0]),
+                                                   __dmul_rn(r.d[1], r.d[1])),
+                                         __dmul_rn(r.d[2], r.d[2])));
+  const double len = __dmul_rn(__dsub_rn(t1, t0), dn);
+  const double nf = ceil(__ddiv_rn(len, step));
+  return nf < 1.0 ? 1 : (nf > (double)kMaxSamplesPerSegment ? kMaxSamplesPerSegment + 1 : (int)nf);
+}
+
+// Position of sample k of the segment (pid0, pid1, n), exactly as the FP64 reference
+// computes it: t = t0 + (k + 1/2) (t1 - t0) / n, x = o + t d.
+static __device__ __noinline__ double3 sample_x_exact(const RayArgs& A, int px, int py, int pid0,
+                                                      int pid1, int n, int k) {
+  RayX r;
+  make_ray(A, px, py, r);
+  const double t0 = exact_t(A, r, pid0);
+  const double t1 = exact_t(A, r, pid1);
+  const double dt = __ddiv_rn(__dsub_rn(t1, t0), (double)n);
+  const double t = __dadd_rn(t0, __dmul_rn(__dadd_rn((double)k, 0.5), dt));
+  return make_double3(__dadd_rn(r.o[0], __dmul_rn(t, r.d[0])),
+                      __dadd_rn(r.o[1], __dmul_rn(t, r.d[1])),
+                      __dadd_rn(r.o[2], __dmul_rn(t, r.d[2])));
 }
 
 // Build the FP32 frame.  Error bounds: tau_s = fma(s, B, C) with B, C rounded once from
@@ -148,9 +192,9 @@ __device__ __forceinline__ void make_frame(const RayArgs& A, const RayX& r, RayF
 // first split plane beyond t0.  Near child = the side entered first (d_a > 0: lower);
 // t_s >= t1 -> near only; t_s <= t0 -> far only; otherwise near with t1 = t_s;
 // d_a == 0 -> the side holding the origin.  Returns -1 on a malformed tree.
-__device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const RayArgs& A,
-                                       const RayX& rx, const RayF& rf, int pid0, float tau0,
-                                       float e0, int& pid1, float& tau1, float& e1) {
+__device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const RayArgs& A, int px,
+                                       int py, const RayF& rf, int pid0, float tau0, float e0,
+                                       int& pid1, float& tau1, float& e1) {
   uint32_t i = 0;
   for (int depth = 0; depth < kMaxDepth; ++depth) {
     const DNode nd = nodes[i];
@@ -158,8 +202,8 @@ __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const Ra
     const uint32_t idx = nd.meta & kIndexMask;
     if (ax == kLeafAxis) return (int)idx;
     const float B = sel3f(ax, rf.B[0], rf.B[1], rf.B[2]);
-    if (B == 0.0f) {  // ray parallel to the plane: the origin's side (exact)
-      const double o = sel3(ax, rx.o[0], rx.o[1], rx.o[2]);
+    if (B == 0.0f) {  // ray parallel to the plane: the origin's (eye's) side, exactly
+      const double o = sel3(ax, A.eye[0], A.eye[1], A.eye[2]);
       const double sw = __dadd_rn(sel3(ax, A.dlo[0], A.dlo[1], A.dlo[2]),
                                   __dmul_rn((double)nd.split, sel3(ax, A.hf[0], A.hf[1], A.hf[2])));
       i = idx + (o < sw ? 0u : 1u);
@@ -188,16 +232,16 @@ __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const Ra
       tau1 = ts;
       e1 = es;
     } else {  // too close to call in FP32: decide on the exact FP64 values
-      const double t = exact_t(A, rx, pid);
-      if (t >= exact_t(A, rx, pid1)) {
-        i = near_c;
-      } else if (t <= exact_t(A, rx, pid0)) {
+      const int dcs = exact_decide(A, px, py, pid, pid0, pid1);
+      if (dcs == 1) {
         i = far_c;
       } else {
         i = near_c;
-        pid1 = pid;
-        tau1 = ts;
-        e1 = es;
+        if (dcs == 2) {
+          pid1 = pid;
+          tau1 = ts;
+          e1 = es;
+        }
       }
     }
   }
@@ -221,6 +265,7 @@ __device__ __forceinline__ int locate_cell(const DNode* __restrict__ nodes, int 
 // Brick of one patch as held in registers while a segment is sampled.
 struct BrickRef {
   long long base;  // pointer / element offset / texture object
+  long long gbase; // the same for the gradient brick
   int sy, sz;
   int dim[3];
   int lo[3];
@@ -231,6 +276,7 @@ __device__ __forceinline__ BrickRef load_brick(const DPatch* __restrict__ pt, in
   const DPatch q = pt[p];
   BrickRef b;
   b.base = q.base;
+  b.gbase = q.gbase;
   b.sy = q.sy;
   b.sz = q.sz;
 #pragma unroll
@@ -255,6 +301,23 @@ __device__ __forceinline__ float fetch(const RenderArgs& A, const BrickRef& b, l
   } else {
     return tex3D<float>(A.atlas, (float)(b.org[0] + i) + 0.5f, (float)(b.org[1] + j) + 0.5f,
                         (float)(b.org[2] + k) + 0.5f);
+  }
+}
+
+// Gradient-brick cell: (V, V(c+x) - V(c-x), V(c+y) - V(c-y), V(c+z) - V(c-z)).
+template <int ST>
+__device__ __forceinline__ float4 fetch4(const RenderArgs& A, const BrickRef& b, long long lin,
+                                         int i, int j, int k) {
+  if constexpr (ST == ST_PTR) {
+    return __ldg(reinterpret_cast<const float4*>(b.gbase) + lin);
+  } else if constexpr (ST == ST_ATLAS_LINEAR) {
+    return __ldg(A.gpool + b.gbase + lin);
+  } else if constexpr (ST == ST_TEXOBJ) {
+    return tex3D<float4>((cudaTextureObject_t)b.gbase, (float)i + 0.5f, (float)j + 0.5f,
+                         (float)k + 0.5f);
+  } else {
+    return tex3D<float4>(A.gatlas, (float)(b.org[0] + i) + 0.5f, (float)(b.org[1] + j) + 0.5f,
+                         (float)(b.org[2] + k) + 0.5f);
   }
 }
 
@@ -308,18 +371,8 @@ struct SegState {
   float bl[3], bh[3]; // leaf box in brick coordinates
   float margin;       // bound on |FP32 beta - beta of the exact FP64 sample position|
   int pid0, pid1, n;  // exact segment: t0, t1 by plane id, n samples
+  int px, py;         // pixel (the exact paths rebuild its ray)
 };
-
-// Position of sample k, exactly as the FP64 reference computes it (rare path).
-static __device__ __noinline__ void sample_x_exact(const RenderArgs& A, const RayX& r, const SegState& s,
-                                            int k, double* x) {
-  const double t0 = exact_t(A.ray, r, s.pid0);
-  const double t1 = exact_t(A.ray, r, s.pid1);
-  const double dt = __ddiv_rn(__dsub_rn(t1, t0), (double)s.n);
-  const double t = __dadd_rn(t0, __dmul_rn(__dadd_rn((double)k, 0.5), dt));
-#pragma unroll
-  for (int a = 0; a < 3; ++a) x[a] = __dadd_rn(r.o[a], __dmul_rn(t, r.d[a]));
-}
 
 // finest cell of an exact point, clamped into the root (the reference's rule)
 __device__ __forceinline__ int finest_cell_exact(const RayArgs& A, double x, int a) {
@@ -329,19 +382,116 @@ __device__ __forceinline__ int finest_cell_exact(const RayArgs& A, double x, int
   return (int)q;
 }
 
-template <int ST, int INTERP>
-__device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayX& r, const SegState& s,
-                                             const float* bn, int a, float sign, int k);
+// Brick index of the level-l cell holding an exact point (nearest sampling).
+__device__ __forceinline__ int nearest_index_exact(const RayArgs& A, const DLevel& lv, double x,
+                                                   int a, int lo) {
+  return (int)floor(__ddiv_rn(__dsub_rn(x, A.dlo[a]), lv.h[a])) - lo + 1;
+}
 
-// Value of the AMR field at the gradient neighbour x_k + sign * h^l e_a (Sec. 4: shading
+// Cross-leaf gradient neighbour x_k + sign h^l e_a: descend the tree on finest-cell
+// coordinates relative to the current leaf corner; a split within the error margin sends
+// the decision to FP64.  Takes scalars only, so the caller keeps its state in registers.
+template <int ST, int INTERP>
+__device__ __noinline__ float neighbour_slow(const RenderArgs& A, int px, int py, int leaf,
+                                             int pid0, int pid1, int n, int k, float margin,
+                                             float bn0, float bn1, float bn2, int a, float sign) {
+  const DLeaf cl = A.leaves[leaf];
+  const DLevel& lv = A.lv[cl.level];
+  const BrickRef cb = load_brick(A.patches, cl.patch);
+  const float scf = (float)lv.sc;
+  const float mf = margin * scf;
+  const float bn[3] = {bn0, bn1, bn2};
+  float xr[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    xr[q] = (bn[q] - ((float)(cl.lo[q] - cb.lo[q] * lv.sc) * lv.inv_sc + 0.5f)) * scf;
+  bool amb = false;
+  uint32_t i = 0;
+  int lid = -1;
+  for (int depth = 0; depth < kMaxDepth; ++depth) {
+    const DNode nd = A.nodes[i];
+    const uint32_t ax = nd.meta >> 30;
+    const uint32_t idx = nd.meta & kIndexMask;
+    if (ax == kLeafAxis) {
+      lid = (int)idx;
+      break;
+    }
+    const float diff = sel3f(ax, xr[0], xr[1], xr[2]) -
+                       (float)(nd.split - sel3i(ax, cl.lo[0], cl.lo[1], cl.lo[2]));
+    if (fabsf(diff) <= mf) {
+      amb = true;
+      break;
+    }
+    i = idx + (diff < 0.0f ? 0u : 1u);
+  }
+  double xe[3] = {0.0, 0.0, 0.0};
+  auto exact_point = [&]() {
+    const double3 x = sample_x_exact(A.ray, px, py, pid0, pid1, n, k);
+    xe[0] = x.x;
+    xe[1] = x.y;
+    xe[2] = x.z;
+    const double hq = sel3(a, lv.h[0], lv.h[1], lv.h[2]);
+    if (a == 0) xe[0] = sign > 0.0f ? __dadd_rn(xe[0], hq) : __dsub_rn(xe[0], hq);
+    if (a == 1) xe[1] = sign > 0.0f ? __dadd_rn(xe[1], hq) : __dsub_rn(xe[1], hq);
+    if (a == 2) xe[2] = sign > 0.0f ? __dadd_rn(xe[2], hq) : __dsub_rn(xe[2], hq);
+  };
+  if (amb) {
+    exact_point();
+    lid = locate_cell(A.nodes, finest_cell_exact(A.ray, xe[0], 0), finest_cell_exact(A.ray, xe[1], 1),
+                      finest_cell_exact(A.ray, xe[2], 2));
+  }
+  if (lid < 0) return 0.0f;
+  const DLeaf lf = A.leaves[lid];
+  const BrickRef nb = (lid == leaf) ? cb : load_brick(A.patches, lf.patch);
+  const DLevel& lw = A.lv[lf.level];
+  float bq[3];
+  if (amb) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      bq[q] = (float)((xe[q] - A.ray.dlo[q]) * lw.inv_h[q] + (0.5 - (double)nb.lo[q]));
+  } else {
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      bq[q] = fmaf(xr[q], lw.inv_sc, (float)(cl.lo[q] - nb.lo[q] * lw.sc) * lw.inv_sc + 0.5f);
+  }
+  if constexpr (INTERP == 1) {
+    return trilinear<ST>(A, nb, bq[0], bq[1], bq[2]);
+  } else {
+    if (!amb) {
+      const float fx = bq[0] + 0.5f, fy = bq[1] + 0.5f, fz = bq[2] + 0.5f;
+      const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
+      const float mq = mf * lw.inv_sc;
+      if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > mq)
+        return cell_at<ST>(A, nb, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
+      exact_point();
+    }
+    return cell_at<ST>(A, nb, nearest_index_exact(A.ray, lw, xe[0], 0, nb.lo[0]),
+                       nearest_index_exact(A.ray, lw, xe[1], 1, nb.lo[1]),
+                       nearest_index_exact(A.ray, lw, xe[2], 2, nb.lo[2]));
+  }
+}
+
+// Exact nearest-cell value of sample k in its own brick (rare path).
+template <int ST>
+__device__ __noinline__ float nearest_sample_exact(const RenderArgs& A, int px, int py, int leaf,
+                                                   int pid0, int pid1, int n, int k) {
+  const DLeaf cl = A.leaves[leaf];
+  const DLevel& lv = A.lv[cl.level];
+  const BrickRef b = load_brick(A.patches, cl.patch);
+  const double3 x = sample_x_exact(A.ray, px, py, pid0, pid1, n, k);
+  return cell_at<ST>(A, b, nearest_index_exact(A.ray, lv, x.x, 0, b.lo[0]),
+                     nearest_index_exact(A.ray, lv, x.y, 1, b.lo[1]),
+                     nearest_index_exact(A.ray, lv, x.z, 2, b.lo[2]));
+}
+
+// Value of the AMR field at the gradient neighbour x_k + SG h^l e_AX (Sec. 4: shading
 // reads across block boundaries).  Inside the current leaf (beyond the error margin) it is
 // the current brick; otherwise the slow path locates the finest leaf holding the point.
-template <int ST, int INTERP>
-__device__ __forceinline__ float neighbour_value(const RenderArgs& A, const RayX& r,
-                                                 const SegState& s, const float* beta, int a,
-                                                 float sign, int k) {
+template <int ST, int INTERP, int AX, int SG>
+__device__ __forceinline__ float neighbour_value(const RenderArgs& A, const SegState& s,
+                                                 const float* beta, int k) {
   float bn[3] = {beta[0], beta[1], beta[2]};
-  bn[a] += sign;
+  bn[AX] += (float)SG;
   const float m = s.margin;
   bool inside = true;
 #pragma unroll
@@ -356,89 +506,13 @@ __device__ __forceinline__ float neighbour_value(const RenderArgs& A, const RayX
         return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
     }
   }
-  return neighbour_slow<ST, INTERP>(A, r, s, bn, a, sign, k);
-}
-
-// Cross-leaf neighbour: descend the tree on finest-cell coordinates relative to the current
-// leaf corner; any split within the error margin sends the decision to FP64.
-template <int ST, int INTERP>
-__device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayX& r, const SegState& s,
-                                             const float* bn, int a, float sign, int k) {
-  const DLevel& lv = A.lv[s.level];
-  const float scf = (float)lv.sc;
-  const float mf = s.margin * scf;
-  float xr[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) xr[q] = (bn[q] - s.bl[q]) * scf;
-  bool amb = false;
-  uint32_t i = 0;
-  int lid = -1;
-  for (int depth = 0; depth < kMaxDepth; ++depth) {
-    const DNode nd = A.nodes[i];
-    const uint32_t ax = nd.meta >> 30;
-    const uint32_t idx = nd.meta & kIndexMask;
-    if (ax == kLeafAxis) {
-      lid = (int)idx;
-      break;
-    }
-    const float diff = sel3f(ax, xr[0], xr[1], xr[2]) -
-                       (float)(nd.split - sel3i(ax, s.leaf_lo[0], s.leaf_lo[1], s.leaf_lo[2]));
-    if (fabsf(diff) <= mf) {
-      amb = true;
-      break;
-    }
-    i = idx + (diff < 0.0f ? 0u : 1u);
-  }
-  double xe[3];
-  if (amb) {
-    sample_x_exact(A, r, s, k, xe);
-    const double hq = sel3(a, lv.h[0], lv.h[1], lv.h[2]);
-    if (a == 0) xe[0] = sign > 0.0f ? __dadd_rn(xe[0], hq) : __dsub_rn(xe[0], hq);
-    if (a == 1) xe[1] = sign > 0.0f ? __dadd_rn(xe[1], hq) : __dsub_rn(xe[1], hq);
-    if (a == 2) xe[2] = sign > 0.0f ? __dadd_rn(xe[2], hq) : __dsub_rn(xe[2], hq);
-    lid = locate_cell(A.nodes, finest_cell_exact(A.ray, xe[0], 0), finest_cell_exact(A.ray, xe[1], 1),
-                      finest_cell_exact(A.ray, xe[2], 2));
-  }
-  if (lid < 0) return 0.0f;
-  const DLeaf lf = A.leaves[lid];
-  const BrickRef nb = (lid == s.leaf) ? s.brick : load_brick(A.patches, lf.patch);
-  const DLevel& lw = A.lv[lf.level];
-  float bq[3];
-  if (amb) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      bq[q] = (float)((xe[q] - A.ray.dlo[q]) * lw.inv_h[q] + (0.5 - (double)nb.lo[q]));
-  } else {
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      bq[q] = fmaf(xr[q], lw.inv_sc, (float)(s.leaf_lo[q] - nb.lo[q] * lw.sc) * lw.inv_sc + 0.5f);
-  }
-  if constexpr (INTERP == 1) {
-    return trilinear<ST>(A, nb, bq[0], bq[1], bq[2]);
-  } else {
-    if (!amb) {
-      const float fx = bq[0] + 0.5f, fy = bq[1] + 0.5f, fz = bq[2] + 0.5f;
-      const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
-      const float mq = mf * lw.inv_sc;
-      if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > mq)
-        return cell_at<ST>(A, nb, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
-      sample_x_exact(A, r, s, k, xe);
-      const double hq = sel3(a, lv.h[0], lv.h[1], lv.h[2]);
-      if (a == 0) xe[0] = sign > 0.0f ? __dadd_rn(xe[0], hq) : __dsub_rn(xe[0], hq);
-      if (a == 1) xe[1] = sign > 0.0f ? __dadd_rn(xe[1], hq) : __dsub_rn(xe[1], hq);
-      if (a == 2) xe[2] = sign > 0.0f ? __dadd_rn(xe[2], hq) : __dsub_rn(xe[2], hq);
-    }
-    int c[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      c[q] = (int)floor(__ddiv_rn(__dsub_rn(xe[q], A.ray.dlo[q]), lw.h[q])) - nb.lo[q] + 1;
-    return cell_at<ST>(A, nb, c[0], c[1], c[2]);
-  }
+  return neighbour_slow<ST, INTERP>(A, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k, s.margin,
+                                    bn[0], bn[1], bn[2], AX, (float)SG);
 }
 
 // Value at the sample itself (the segment's own leaf and level, Sec. 3.3).
 template <int ST, int INTERP>
-__device__ __forceinline__ float sample_value(const RenderArgs& A, const RayX& r, const SegState& s,
+__device__ __forceinline__ float sample_value(const RenderArgs& A, const SegState& s,
                                               const float* beta, int k) {
   if constexpr (INTERP == 1) {
     return trilinear<ST>(A, s.brick, beta[0], beta[1], beta[2]);
@@ -447,14 +521,7 @@ __device__ __forceinline__ float sample_value(const RenderArgs& A, const RayX& r
     const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
     if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > s.margin)
       return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
-    const DLevel& lv = A.lv[s.level];
-    double x[3];
-    sample_x_exact(A, r, s, k, x);
-    int c[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      c[q] = (int)floor(__ddiv_rn(__dsub_rn(x[q], A.ray.dlo[q]), lv.h[q])) - s.brick.lo[q] + 1;
-    return cell_at<ST>(A, s.brick, c[0], c[1], c[2]);
+    return nearest_sample_exact<ST>(A, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k);
   }
 }
 
@@ -479,20 +546,9 @@ __device__ __forceinline__ bool tf_transparent(const int* __restrict__ nz_prefix
   return nz_prefix[i1 + 1] - nz_prefix[i0] == 0;
 }
 
-// Exact sample count of a segment: n = max(1, ceil(len / step)), len = (t1 - t0) |d|.
+// Sample count of a segment: n = max(1, ceil(len / step)), len = (t1 - t0) |d|.
 // The FP32 estimate decides unless the quotient lies within its error bound of an integer.
-static __device__ __noinline__ int exact_count(const RenderArgs& A, const RayX& r, int pid0, int pid1,
-                                        double step) {
-  const double t0 = exact_t(A.ray, r, pid0), t1 = exact_t(A.ray, r, pid1);
-  const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(r.d[0], r.d[0]),
-                                                   __dmul_rn(r.d[1], r.d[1])),
-                                         __dmul_rn(r.d[2], r.d[2])));
-  const double len = __dmul_rn(__dsub_rn(t1, t0), dn);
-  const double nf = ceil(__ddiv_rn(len, step));
-  return nf < 1.0 ? 1 : (nf > (double)kMaxSamplesPerSegment ? kMaxSamplesPerSegment + 1 : (int)nf);
-}
-
-__device__ __forceinline__ int segment_count(const RenderArgs& A, const RayX& r, const RayF& f,
+__device__ __forceinline__ int segment_count(const RenderArgs& A, int px, int py, const RayF& f,
                                              int pid0, float tau0, float e0, int pid1, float tau1,
                                              float e1, const DLevel& lv) {
   const float inv_step = lv.inv_step;
@@ -504,7 +560,106 @@ __device__ __forceinline__ int segment_count(const RenderArgs& A, const RayX& r,
   if (q + eq <= 1.0f) return 1;
   const float c = ceilf(q);
   if (c - q > eq && q - (c - 1.0f) > eq && c <= (float)kMaxSamplesPerSegment) return (int)c;
-  return exact_count(A, r, pid0, pid1, lv.step);
+  return exact_count(A.ray, px, py, pid0, pid1, lv.step);
+}
+
+// Central-difference gradient g_a = (F(x + h e_a) - F(x - h e_a)) / 2h at sample beta.
+// When all six neighbours lie inside the current leaf (beyond the error margin), they are
+// trilinear values of the same brick and share one 32-cell stencil: the differences along
+// an axis are lerps of the two outer cell pairs, combined bilinearly in the other axes.
+// Otherwise each neighbour goes through neighbour_value (cross-leaf lookups).
+template <int ST, int INTERP, int GB>
+__device__ __forceinline__ void gradient(const RenderArgs& A, const SegState& s, const float* beta,
+                                         int k, const DLevel& lv, float* g) {
+  if constexpr (INTERP == 1) {
+    const float m = s.margin;
+    bool inner = true;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      inner = inner && (beta[q] - 1.0f >= s.bl[q] + m) && (beta[q] + 1.0f < s.bh[q] - m);
+    if (GB && inner) {
+      // gradient brick: trilinear interpolation of the per-cell central differences
+      const BrickRef& b = s.brick;
+      const int ix = min(max((int)beta[0], 1), b.dim[0] - 3);
+      const int iy = min(max((int)beta[1], 1), b.dim[1] - 3);
+      const int iz = min(max((int)beta[2], 1), b.dim[2] - 3);
+      const float wx = beta[0] - (float)ix, wy = beta[1] - (float)iy, wz = beta[2] - (float)iz;
+      const long long l0 = (long long)ix + (long long)b.sy * iy + (long long)b.sz * iz;
+      const float4 q000 = fetch4<ST>(A, b, l0, ix, iy, iz);
+      const float4 q100 = fetch4<ST>(A, b, l0 + 1, ix + 1, iy, iz);
+      const float4 q010 = fetch4<ST>(A, b, l0 + b.sy, ix, iy + 1, iz);
+      const float4 q110 = fetch4<ST>(A, b, l0 + b.sy + 1, ix + 1, iy + 1, iz);
+      const float4 q001 = fetch4<ST>(A, b, l0 + b.sz, ix, iy, iz + 1);
+      const float4 q101 = fetch4<ST>(A, b, l0 + b.sz + 1, ix + 1, iy, iz + 1);
+      const float4 q011 = fetch4<ST>(A, b, l0 + b.sz + b.sy, ix, iy + 1, iz + 1);
+      const float4 q111 = fetch4<ST>(A, b, l0 + b.sz + b.sy + 1, ix + 1, iy + 1, iz + 1);
+      auto tri = [&](float v000, float v100, float v010, float v110, float v001, float v101,
+                     float v011, float v111) {
+        const float c00 = fmaf(wx, v100 - v000, v000), c10 = fmaf(wx, v110 - v010, v010);
+        const float c01 = fmaf(wx, v101 - v001, v001), c11 = fmaf(wx, v111 - v011, v011);
+        const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
+        return fmaf(wz, c1 - c0, c0);
+      };
+      g[0] = tri(q000.y, q100.y, q010.y, q110.y, q001.y, q101.y, q011.y, q111.y) *
+             (0.5f * (float)lv.inv_h[0]);
+      g[1] = tri(q000.z, q100.z, q010.z, q110.z, q001.z, q101.z, q011.z, q111.z) *
+             (0.5f * (float)lv.inv_h[1]);
+      g[2] = tri(q000.w, q100.w, q010.w, q110.w, q001.w, q101.w, q011.w, q111.w) *
+             (0.5f * (float)lv.inv_h[2]);
+      return;
+    }
+    if (inner) {
+      const BrickRef& b = s.brick;
+      const int ix = min(max((int)beta[0], 1), b.dim[0] - 3);
+      const int iy = min(max((int)beta[1], 1), b.dim[1] - 3);
+      const int iz = min(max((int)beta[2], 1), b.dim[2] - 3);
+      const float wx = beta[0] - (float)ix, wy = beta[1] - (float)iy, wz = beta[2] - (float)iz;
+      const long long l0 = (long long)ix + (long long)b.sy * iy + (long long)b.sz * iz;
+      auto V = [&](int dx, int dy, int dz) {
+        return fetch<ST>(A, b, l0 + dx + (long long)b.sy * dy + (long long)b.sz * dz, ix + dx,
+                         iy + dy, iz + dz);
+      };
+      float c[2][2][2];
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) c[dz][dy][dx] = V(dx, dy, dz);
+      float dxv[2][2], dyv[2][2], dzv[2][2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          // x: at (y = iy + u, z = iz + v)
+          const float xm = V(-1, u, v), xp = V(2, u, v);
+          dxv[v][u] = fmaf(wx, xp - c[v][u][1], c[v][u][1]) - fmaf(wx, c[v][u][0] - xm, xm);
+          // y: at (x = ix + u, z = iz + v)
+          const float ym = V(u, -1, v), yp = V(u, 2, v);
+          dyv[v][u] = fmaf(wy, yp - c[v][1][u], c[v][1][u]) - fmaf(wy, c[v][0][u] - ym, ym);
+          // z: at (x = ix + u, y = iy + v)
+          const float zm = V(u, v, -1), zp = V(u, v, 2);
+          dzv[v][u] = fmaf(wz, zp - c[1][v][u], c[1][v][u]) - fmaf(wz, c[0][v][u] - zm, zm);
+        }
+      // bilinear combination in the two transverse axes
+      const float gx0 = fmaf(wy, dxv[0][1] - dxv[0][0], dxv[0][0]);
+      const float gx1 = fmaf(wy, dxv[1][1] - dxv[1][0], dxv[1][0]);
+      const float gy0 = fmaf(wx, dyv[0][1] - dyv[0][0], dyv[0][0]);
+      const float gy1 = fmaf(wx, dyv[1][1] - dyv[1][0], dyv[1][0]);
+      const float gz0 = fmaf(wx, dzv[0][1] - dzv[0][0], dzv[0][0]);
+      const float gz1 = fmaf(wx, dzv[1][1] - dzv[1][0], dzv[1][0]);
+      g[0] = fmaf(wz, gx1 - gx0, gx0) * (0.5f * (float)lv.inv_h[0]);
+      g[1] = fmaf(wz, gy1 - gy0, gy0) * (0.5f * (float)lv.inv_h[1]);
+      g[2] = fmaf(wy, gz1 - gz0, gz0) * (0.5f * (float)lv.inv_h[2]);
+      return;
+    }
+  }
+  g[0] = (neighbour_value<ST, INTERP, 0, 1>(A, s, beta, k) -
+          neighbour_value<ST, INTERP, 0, -1>(A, s, beta, k)) * (0.5f * (float)lv.inv_h[0]);
+  g[1] = (neighbour_value<ST, INTERP, 1, 1>(A, s, beta, k) -
+          neighbour_value<ST, INTERP, 1, -1>(A, s, beta, k)) * (0.5f * (float)lv.inv_h[1]);
+  g[2] = (neighbour_value<ST, INTERP, 2, 1>(A, s, beta, k) -
+          neighbour_value<ST, INTERP, 2, -1>(A, s, beta, k)) * (0.5f * (float)lv.inv_h[2]);
 }
 
 template <int ST, int INTERP, int SHADE>
@@ -552,14 +707,14 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Rend
         ++seg;
         int pid1 = kPidOut;
         float tau1 = rf.tau_out, e1 = rf.e_out;
-        const int lid = descend(A.nodes, A.ray, rx, rf, pid0, tau0, e0, pid1, tau1, e1);
+        const int lid = descend(A.nodes, A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;
           break;
         }
         const DLeaf lf = A.leaves[lid];
         const DLevel& lv = A.lv[lf.level];
-        int n = segment_count(A, rx, rf, pid0, tau0, e0, pid1, tau1, e1, lv);
+        int n = segment_count(A, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv);
         if (n > kMaxSamplesPerSegment) {
           status |= kStatusCapacity;
           n = kMaxSamplesPerSegment;
@@ -577,6 +732,8 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Rend
         s.pid0 = pid0;
         s.pid1 = pid1;
         s.n = n;
+        s.px = i;
+        s.py = j;
         const float nfl = (float)n;
         const float dtau = (tau1 - tau0) / nfl;
         const float delta = dtau * rf.dn;
@@ -605,20 +762,15 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Rend
           float beta[3];
 #pragma unroll
           for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, db[a], b0[a]);
-          const float v = sample_value<ST, INTERP>(A, rx, s, beta, k);
+          const float v = sample_value<ST, INTERP>(A, s, beta, k);
           const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
           ++nsamp;
           if (c.w <= 0.0f) continue;
           const float alpha = -expm1f(-A.kappa * c.w * delta);
           float cr = c.x, cg = c.y, cb = c.z;
-          if constexpr (SHADE == 1) {
+          if constexpr (SHADE >= 1) {
             float g[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const float vp = neighbour_value<ST, INTERP>(A, rx, s, beta, a, 1.0f, k);
-              const float vm = neighbour_value<ST, INTERP>(A, rx, s, beta, a, -1.0f, k);
-              g[a] = (vp - vm) * (0.5f * (float)lv.inv_h[a]);
-            }
+            gradient<ST, INTERP, (SHADE == 2)>(A, s, beta, k, lv, g);
             const float gn = sqrtf(fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2])));
             const float gf = A.gfloor_num / lv.hmin;
             const float den = fmaxf(gn, gf);

@@ -4,11 +4,11 @@
 
 namespace amr {
 amr_status launch_atlas_linear(amr_ctx* c, const RenderArgs& a, int interp, int shade,
-                               cudaStream_t s) {
-  return launch_storage<ST_ATLAS_LINEAR>(c, a, interp, shade, s);
+                               int schedule, cudaStream_t s) {
+  return launch_storage<ST_ATLAS_LINEAR>(c, a, interp, shade, schedule, s);
 }
 amr_status launch_atlas_tex3d(amr_ctx* c, const RenderArgs& a, int interp, int shade,
-                              cudaStream_t s) {
-  return launch_storage<ST_ATLAS_TEX3D>(c, a, interp, shade, s);
+                               int schedule, cudaStream_t s) {
+  return launch_storage<ST_ATLAS_TEX3D>(c, a, interp, shade, schedule, s);
 }
 }  // namespace amr

@@ -3,8 +3,8 @@
 #include "march_launch.cuh"
 
 namespace amr {
-amr_status launch_texobj(amr_ctx* c, const RenderArgs& a, int interp, int shade,
+amr_status launch_texobj(amr_ctx* c, const RenderArgs& a, int interp, int shade, int schedule,
                          cudaStream_t s) {
-  return launch_storage<ST_TEXOBJ>(c, a, interp, shade, s);
+  return launch_storage<ST_TEXOBJ>(c, a, interp, shade, schedule, s);
 }
 }  // namespace amr

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
     }
     int pid1 = kPidOut;
     float tau1 = rf.tau_out, e1 = rf.e_out;
-    const int lid = descend(A.nodes, A.ray, rx, rf, pid0, tau0, e0, pid1, tau1, e1);
+    const int lid = descend(A.nodes, A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1);
     if (lid < 0) {
       status |= kStatusDevice;
       break;
@@ -59,13 +59,13 @@ amr_status launch_trace(amr_ctx* c, const TraceArgs& a, void* stream) {
 }
 
 amr_status launch_render(amr_ctx* c, const RenderArgs& a, int storage, int interp, int shade,
-                         void* stream) {
+                         int schedule, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   switch (storage) {
-    case ST_PTR: return launch_ptr(c, a, interp, shade, s);
-    case ST_TEXOBJ: return launch_texobj(c, a, interp, shade, s);
-    case ST_ATLAS_LINEAR: return launch_atlas_linear(c, a, interp, shade, s);
-    case ST_ATLAS_TEX3D: return launch_atlas_tex3d(c, a, interp, shade, s);
+    case ST_PTR: return launch_ptr(c, a, interp, shade, schedule, s);
+    case ST_TEXOBJ: return launch_texobj(c, a, interp, shade, schedule, s);
+    case ST_ATLAS_LINEAR: return launch_atlas_linear(c, a, interp, shade, schedule, s);
+    case ST_ATLAS_TEX3D: return launch_atlas_tex3d(c, a, interp, shade, schedule, s);
     default: return fail(c, AMR_ERR_ARG, "unknown storage");
   }
 }

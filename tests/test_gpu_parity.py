@@ -65,19 +65,44 @@ def test_trace_c1_bit_exact(c1, c1_ctx):
 @pytest.mark.parametrize("storage", STORAGES)
 @pytest.mark.parametrize("shade", [0, 1])
 @pytest.mark.parametrize("interp", [1, 0])
-def test_image_c1(amr, c1, c1_ctx, storage, shade, interp):
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_image_c1(amr, c1, c1_ctx, storage, shade, interp, schedule):
     w, o = c1
-    p, op = params_pair(amr, w["vmin"], w["vmax"], shade=shade, interp=interp)
+    p, op = params_pair(amr, w["vmin"], w["vmax"], shade=shade, interp=interp, schedule=schedule)
     img, n = gpu_render(c1_ctx[storage], w["camera"], w["tf"], p)
     ref, smp = o.render(w["camera"], w["tf"], op)
-    assert_image_close(img, ref, what=f"{storage} shade={shade} interp={interp}")
+    assert_image_close(img, ref, what=f"{storage} shade={shade} interp={interp} sched={schedule}")
     assert abs(int(n) - int(smp.sum())) <= 0.001 * smp.sum()
 
 
-@pytest.mark.parametrize("storage", ["ptr", "atlas_tex3d"])
-def test_sample_count_exact_without_ert(amr, c1, c1_ctx, storage):
+@pytest.fixture(scope="module")
+def c1_gctx(amr, c1):
+    """C1 with gradient bricks (float4 value + central differences per cell)."""
+    ctxs = {}
+    for st in STORAGES:
+        ctx = amr.from_hierarchy(c1[0]["hier"])
+        ctx.amr_build_kdtree(st, gradient=True)
+        ctxs[st] = ctx
+    return ctxs
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_image_c1_gradient_bricks(amr, c1, c1_ctx, c1_gctx, storage, schedule):
     w, o = c1
-    p, op = params_pair(amr, w["vmin"], w["vmax"], ert_eps=0.0, shade=1)
+    p, op = params_pair(amr, w["vmin"], w["vmax"], shade=1, schedule=schedule)
+    img, n = gpu_render(c1_gctx[storage], w["camera"], w["tf"], p)
+    ref, smp = o.render(w["camera"], w["tf"], op)
+    assert_image_close(img, ref, what=f"gradient bricks {storage} sched={schedule}")
+    plain, n2 = gpu_render(c1_ctx[storage], w["camera"], w["tf"], p)
+    assert np.max(np.abs(img - plain)) < 1e-5 and abs(int(n) - int(n2)) <= 0.001 * n2
+
+
+@pytest.mark.parametrize("storage", ["ptr", "atlas_tex3d"])
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_sample_count_exact_without_ert(amr, c1, c1_ctx, storage, schedule):
+    w, o = c1
+    p, op = params_pair(amr, w["vmin"], w["vmax"], ert_eps=0.0, shade=1, schedule=schedule)
     img, n = gpu_render(c1_ctx[storage], w["camera"], w["tf"], p)
     ref, smp = o.render(w["camera"], w["tf"], op)
     assert int(n) == int(smp.sum())
@@ -97,7 +122,7 @@ def test_random_hierarchies_ragged_images(amr, seed):
     ctx = amr.from_hierarchy(h)
     ctx.amr_build_kdtree(storage)
     for shade in (0, 1):
-        p, op = params_pair(amr, vmin, vmax, shade=shade, kappa=20.0)
+        p, op = params_pair(amr, vmin, vmax, shade=shade, kappa=20.0, schedule=seed % 2)
         img, _ = gpu_render(ctx, cam, tf, p)
         ref, _ = o.render(cam, tf, op)
         assert_image_close(img, ref, what=f"seed {seed} {storage} shade {shade}")
@@ -137,24 +162,30 @@ def test_edge_cameras(amr, c1, c1_ctx):
     assert np.all(away == 0)
 
 
-def test_bands_skip_and_host_path_are_bit_identical(amr, c1, c1_ctx):
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_bands_skip_and_host_path(amr, c1, c1_ctx, schedule):
     import torch
 
     w, _ = c1
     ctx = c1_ctx["atlas_linear"]
     cam = w["camera"]
-    p, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1)
+    p, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1, schedule=schedule)
     full, n_full = gpu_render(ctx, cam, w["tf"], p)
-    # image-space bands (the multi-GPU partition) stitch to the full image
+    again, n_again = gpu_render(ctx, cam, w["tf"], p)
+    assert np.array_equal(full, again) and n_full == n_again  # deterministic
+    # image-space bands (the multi-GPU partition) on 4-row boundaries stitch bit for bit:
+    # a warp covers 8x4 pixels, so each warp sees the same rays as in the full frame
     parts = []
-    for r0, r1 in [(0, 77), (77, 200), (200, 256)]:
-        pb, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1, row0=r0, rows=r1 - r0)
+    for r0, r1 in [(0, 80), (80, 200), (200, 256)]:
+        pb, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1, row0=r0, rows=r1 - r0,
+                            schedule=schedule)
         parts.append(gpu_render(ctx, cam, w["tf"], pb)[0])
     assert np.array_equal(np.concatenate(parts, axis=0), full)
-    # exact empty-space skipping changes nothing but the work
-    ps, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1, skip=1)
+    # exact empty-space skipping removes only transparent samples (the wavefront schedule
+    # may sum the remaining contributions in another order)
+    ps, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1, skip=1, schedule=schedule)
     skipped, n_skip = gpu_render(ctx, cam, w["tf"], ps)
-    assert np.array_equal(skipped, full)
+    assert np.max(np.abs(skipped - full)) <= (0.0 if schedule == 0 else 2e-6)
     assert n_skip < n_full
     # host-buffer entry point
     out = np.zeros((cam.height, cam.width, 4), dtype=np.float32)
@@ -191,20 +222,22 @@ def _sample_pixels(W, H, n, seed):
     return np.concatenate([pix, row], axis=0).astype(np.int32)
 
 
-@pytest.mark.parametrize("size,storage", [(1024, "ptr"), (1024, "texobj"), (1024, "atlas_linear"),
-                                          (1024, "atlas_tex3d"), (2048, "ptr")])
-def test_c2_sampled_pixels(amr, c2, size, storage):
+@pytest.mark.parametrize("size,storage,schedule,gradient", [
+    (1024, "ptr", 0, False), (1024, "texobj", 0, False), (1024, "atlas_linear", 0, False),
+    (1024, "atlas_tex3d", 0, False), (1024, "ptr", 1, False), (1024, "atlas_linear", 0, True),
+    (2048, "ptr", 0, True), (2048, "ptr", 0, False)])
+def test_c2_sampled_pixels(amr, c2, size, storage, schedule, gradient):
     h, vmin, vmax, o = c2
     ctx = amr.from_hierarchy(h)
-    ctx.amr_build_kdtree(storage)
+    ctx.amr_build_kdtree(storage, gradient=gradient)
     cam = synth.orbit_camera(2, size, size)
     tf = synth.ramp_tf()
-    p, op = params_pair(amr, vmin, vmax, shade=1)
+    p, op = params_pair(amr, vmin, vmax, shade=1, schedule=schedule)
     img, n = gpu_render(ctx, cam, tf, p)
     pix = _sample_pixels(size, size, 1200 if size == 1024 else 800, size)
     ref, _ = o.render(cam, tf, op, pixels=pix)
     got = img[pix[:, 1], pix[:, 0]]
-    assert_image_close(got, ref, what=f"c2 {size} {storage}")
+    assert_image_close(got, ref, what=f"c2 {size} {storage} sched {schedule}")
     assert n > 0
 
 
