@@ -271,6 +271,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     samples = ctx.amr_render(cam, tf, params, out, count_samples=True)  # also checks status
+    exact_paths = list(ctx.amr_get_stats().exact_paths)
     for _ in range(args.warmup):
         ctx.amr_render(cam, tf, params, out)
     torch.cuda.synchronize()
@@ -330,6 +331,8 @@ def main():
                       "<storage, trilinear, phong>",
             "kernel_ms": kern_ms}
     extra = {"frames_per_s": fps, "samples_per_frame": samples, "build_s": build_s,
+             "exact_fp64_paths_per_frame": {"descent": exact_paths[0], "count": exact_paths[1],
+                                            "position": exact_paths[2]},
              "tree": {"nodes": st.num_nodes, "leaves": st.num_leaves, "depth": st.max_depth,
                       "brick_mb": st.brick_bytes / 1e6}}
     if args.compare:

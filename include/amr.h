@@ -160,6 +160,8 @@ typedef struct {
   double build_seconds;     /* host build time (tree + bricks + packing) */
   int32_t max_depth;        /* deepest leaf (root = 0) */
   int32_t storage;          /* amr_storage in use, -1 before build */
+  int64_t exact_paths[3];   /* last render with samples_out: FP64 recomputations of descent
+                               decisions, sample counts, and sample / neighbour positions */
 } amr_stats;
 
 amr_status amr_get_stats(const amr_ctx* ctx, amr_stats* out);

@@ -46,7 +46,8 @@ class amr_stats(C.Structure):
                 ("brick_bytes", C.c_int64), ("tree_bytes", C.c_int64),
                 ("atlas_dims", C.c_int32 * 3), ("atlas_efficiency", C.c_double),
                 ("atlas_efficiency_halo", C.c_double), ("build_seconds", C.c_double),
-                ("max_depth", C.c_int32), ("storage", C.c_int32)]
+                ("max_depth", C.c_int32), ("storage", C.c_int32),
+                ("exact_paths", C.c_int64 * 3)]
 
 
 # every symbol include/amr.h declares, with its ctypes signature

@@ -22,6 +22,9 @@ constexpr uint32_t kIndexMask = 0x3fffffffu;
 constexpr int kMaxDepth = 256;          // descent bound (tree depth is checked at build)
 constexpr int kMaxSamplesPerSegment = 1 << 22;
 
+// device counters: [0] samples, [1] status bits, [2] exact descent decisions,
+// [3] exact sample counts, [4] exact neighbour / nearest positions
+constexpr int kNumCounters = 8;
 // status bits raised by kernels (OR-ed into counters[1])
 constexpr unsigned long long kStatusCapacity = 1ull;   // segment or sample bound hit
 constexpr unsigned long long kStatusDevice = 2ull;     // malformed tree reached
@@ -67,8 +70,10 @@ struct RayArgs {
   int32_t row0, rows;
   double dlo[3];        // domain origin
   double hf[3];         // finest spacing h^(L-1)
+  double inv_hf[3];     // 1 / hf
   double root_w[6];     // root box, world coordinates
   int32_t root_f[6];    // root box, finest cells
+  unsigned long long* counters;  // [0] samples, [1] status, [2..4] exact-path counts
 };
 
 struct RenderArgs {

@@ -48,6 +48,7 @@ void fill_ray(const amr_ctx* c, const amr_camera* cam, int row0, int rows, RayAr
     ra->up[a] = cam->up[a];
     ra->dlo[a] = c->dlo[a];
     ra->hf[a] = c->h0[a] / (double)c->R;
+    ra->inv_hf[a] = 1.0 / ra->hf[a];
     ra->root_w[a] = c->dlo[a] + (double)c->root[a] * ra->hf[a];
     ra->root_w[3 + a] = c->dlo[a] + (double)c->root[3 + a] * ra->hf[a];
     ra->root_f[a] = (int32_t)c->root[a];
@@ -281,6 +282,7 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->shininess = (float)p->shininess;
   a->gfloor_num = (float)(p->gamma * (p->vmax - p->vmin));
   a->counters = c->dev.counters;
+  a->ray.counters = c->dev.counters;
   return AMR_OK;
 }
 
@@ -293,9 +295,10 @@ static int kernel_shade(const amr_ctx* c, const amr_render_params* p) {
 
 static amr_status finish_render(amr_ctx* c, cudaStream_t st, uint64_t* samples_out) {
   if (!samples_out) return AMR_OK;
-  unsigned long long h[2] = {0, 0};
+  unsigned long long h[kNumCounters] = {0};
   CK(cudaMemcpyAsync(h, c->dev.counters, sizeof h, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  std::memcpy(c->last_counters, h, sizeof h);
   *samples_out = h[0];
   if (h[1] & kStatusDevice) return fail(c, AMR_ERR_DEVICE, "device reported a malformed tree");
   if (h[1] & kStatusCapacity)
@@ -315,7 +318,7 @@ amr_status amr_render(amr_ctx* c, const amr_camera* cam, const float* tf_rgba_de
   a.tf = reinterpret_cast<const float4*>(tf_rgba_dev);
   a.out = reinterpret_cast<float4*>(out_rgba_dev);
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  CK(cudaMemsetAsync(c->dev.counters, 0, 2 * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(c->dev.counters, 0, kNumCounters * sizeof(unsigned long long), st));
   s = launch_render(c, a, c->storage, params->interp, kernel_shade(c, params), params->schedule,
                     cuda_stream);
   if (s != AMR_OK) return s;
@@ -350,7 +353,7 @@ amr_status amr_render_host(amr_ctx* c, const amr_camera* cam, const float* tf_rg
                      cudaMemcpyHostToDevice, st));
   a.tf = d.tf_scratch;
   a.out = d.img_scratch;
-  CK(cudaMemsetAsync(d.counters, 0, 2 * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(d.counters, 0, kNumCounters * sizeof(unsigned long long), st));
   s = launch_render(c, a, c->storage, params->interp, kernel_shade(c, params), params->schedule,
                     cuda_stream);
   if (s != AMR_OK) return s;
@@ -378,6 +381,7 @@ amr_status amr_get_stats(const amr_ctx* c, amr_stats* out) {
   for (const Patch& p : c->patches) out->num_cells += p.n[0] * p.n[1] * p.n[2];
   out->storage = c->storage;
   out->build_seconds = c->build_seconds;
+  for (int k = 0; k < 3; ++k) out->exact_paths[k] = (int64_t)c->last_counters[2 + k];
   if (!c->host_built) return AMR_OK;
   out->num_nodes = (int64_t)c->tree.axis.size();
   out->num_leaves = (int64_t)c->tree.leaf_patch.size();
@@ -461,8 +465,9 @@ amr_status amr_trace(amr_ctx* c, const amr_camera* cam, int32_t* leaf_seq_dev, d
   a.max_len = max_len;
   a.max_segments = (int32_t)std::min<int64_t>(4 * (int64_t)c->tree.axis.size() + 64, INT32_MAX);
   a.counters = c->dev.counters;
+  a.ray.counters = c->dev.counters;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  CK(cudaMemsetAsync(c->dev.counters, 0, 2 * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(c->dev.counters, 0, kNumCounters * sizeof(unsigned long long), st));
   s = launch_trace(c, a, cuda_stream);
   if (s != AMR_OK) return s;
   unsigned long long h[2] = {0, 0};

@@ -73,6 +73,7 @@ struct amr_ctx {
   std::vector<float> leaf_vmin, leaf_vmax;
   amr::Packing packing;
   int storage = -1;
+  unsigned long long last_counters[amr::kNumCounters] = {0};  // of the last synchronous render
   bool host_built = false;
   bool device_built = false;
   double build_seconds = 0.0;

@@ -222,8 +222,8 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   CK(cudaMalloc(&d.nodes, nodes.size() * sizeof(DNode)));
   CK(cudaMalloc(&d.leaves, std::max<size_t>(1, M) * sizeof(DLeaf)));
   CK(cudaMalloc(&d.patches, P * sizeof(DPatch)));
-  CK(cudaMalloc(&d.counters, 4 * sizeof(unsigned long long)));
-  CK(cudaMemsetAsync(d.counters, 0, 4 * sizeof(unsigned long long), stream));
+  CK(cudaMalloc(&d.counters, kNumCounters * sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(d.counters, 0, kNumCounters * sizeof(unsigned long long), stream));
 
   amr_status st = upload_bricks<float>(c, c->bricks, pt, false, stream);
   if (st != AMR_OK) return st;

@@ -44,7 +44,7 @@ __device__ __forceinline__ int sel3i(int a, int x, int y, int z) {
 
 // Exact ray (FP64), used by the rare exact paths.
 struct RayX {
-  double o[3], d[3];
+  double o[3], d[3], inv[3];
   double t_in, t_out;
 };
 
@@ -52,10 +52,12 @@ struct RayX {
 // plane s on axis a within Ef[a]; X(tau) = Xe + tau * Dd approximates the position in
 // finest-cell units (x - dlo) / h_f.
 struct RayF {
-  float B[3], C[3], Ef[3];
+  float B[3], C[3];      // leading parts
+  float Bl[3], Cl[3];    // trailing parts (B = B + Bl, C = C + Cl to ~2^-48)
   float Xe[3], Dd[3];
   float tau_out, e_out;
   float dn;
+  int exact_axes;        // bit a set: planes on axis a are always decided in FP64
 };
 
 // Pixel (i, j) -> exact ray and root interval.  The operation order is part of the
@@ -76,8 +78,10 @@ __device__ __forceinline__ bool make_ray(const RayArgs& A, int i, int j, RayX& r
     r.o[a] = A.eye[a];
     r.d[a] = __dadd_rn(__dadd_rn(A.fwd[a], __dmul_rn(u, A.right[a])), __dmul_rn(v, A.up[a]));
     const double lo = A.root_w[a], hi = A.root_w[3 + a];
+    r.inv[a] = 0.0;
     if (r.d[a] != 0.0) {
       const double inv = __ddiv_rn(1.0, r.d[a]);
+      r.inv[a] = inv;
       const double ta = __dmul_rn(__dsub_rn(lo, r.o[a]), inv);
       const double tb = __dmul_rn(__dsub_rn(hi, r.o[a]), inv);
       const double tn = ta < tb ? ta : tb;
@@ -104,7 +108,8 @@ __device__ __forceinline__ double exact_t(const RayArgs& A, const RayX& r, int p
   const double d = sel3(ax, r.d[0], r.d[1], r.d[2]);
   const double sw = __dadd_rn(sel3(ax, A.dlo[0], A.dlo[1], A.dlo[2]),
                               __dmul_rn((double)s, sel3(ax, A.hf[0], A.hf[1], A.hf[2])));
-  return __dmul_rn(__dsub_rn(sw, o), __ddiv_rn(1.0, d));
+  (void)d;
+  return __dmul_rn(__dsub_rn(sw, o), sel3(ax, r.inv[0], r.inv[1], r.inv[2]));
 }
 
 // The rare exact paths rebuild the FP64 ray of their pixel (make_ray is deterministic)
@@ -114,6 +119,7 @@ __device__ __forceinline__ double exact_t(const RayArgs& A, const RayX& r, int p
 // 0 near only, 1 far only, 2 near with t1 = t_s.
 static __device__ __noinline__ int exact_decide(const RayArgs& A, int px, int py, int pid,
                                                 int pid0, int pid1) {
+  atomicAdd(A.counters + 2, 1ull);
   RayX r;
   make_ray(A, px, py, r);
   const double t = exact_t(A, r, pid);
@@ -125,6 +131,7 @@ static __device__ __noinline__ int exact_decide(const RayArgs& A, int px, int py
 // Exact sample count n = max(1, ceil(len / step)) of the segment (pid0, pid1).
 static __device__ __noinline__ int exact_count(const RayArgs& A, int px, int py, int pid0,
                                                int pid1, double step) {
+  atomicAdd(A.counters + 3, 1ull);
   RayX r;
   make_ray(A, px, py, r);
   const double t0 = exact_t(A, r, pid0), t1 = exact_t(A, r, pid1);
@@ -140,6 +147,7 @@ static __device__ __noinline__ int exact_count(const RayArgs& A, int px, int py,
 // computes it: t = t0 + (k + 1/2) (t1 - t0) / n, x = o + t d.
 static __device__ __noinline__ double3 sample_x_exact(const RayArgs& A, int px, int py, int pid0,
                                                       int pid1, int n, int k) {
+  atomicAdd(A.counters + 4, 1ull);
   RayX r;
   make_ray(A, px, py, r);
   const double t0 = exact_t(A, r, pid0);
@@ -151,51 +159,61 @@ static __device__ __noinline__ double3 sample_x_exact(const RayArgs& A, int px, 
                       __dadd_rn(r.o[2], __dmul_rn(t, r.d[2])));
 }
 
-// Build the FP32 frame.  Error bounds: tau_s = fma(s, B, C) with B, C rounded once from
-// FP64 is within u (|s B| + |C| + |tau_s|) of t_s - t_in (plus FP64 rounding, ~1e-15
-// relative); |tau_s| <= |s B| + |C|, so 4u (2 max|s B| + 2|C| + 1) bounds it with room.
+// Build the FP32 frame.  tau_s = (s h_f + dlo - o) / d - t_in = s B + C with
+// B = h_f / d and C = (dlo - e) / d, e = o + t_in d the root entry point.  B and C are
+// kept as two-float pairs, so fma(s, B, C) + fma(s, Bl, Cl) carries only the final
+// roundings: |error| <= 2u |tau_s| plus terms below 2^-45 (|s B| + |C|), all inside the
+// per-node bound 2^-22 (|tau_s| + 1) while |s B| + |C| < 2^20 (else: exact decisions).
 __device__ __forceinline__ void make_frame(const RayArgs& A, const RayX& r, RayF& f) {
   const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(r.d[0], r.d[0]),
                                                    __dmul_rn(r.d[1], r.d[1])),
                                          __dmul_rn(r.d[2], r.d[2])));
   f.dn = (float)dn;
+  f.exact_axes = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const double e = r.o[a] + r.t_in * r.d[a];  // entry point (accuracy only)
     const double smax = (double)max(abs(A.root_f[a]), abs(A.root_f[3 + a]));
     if (r.d[a] != 0.0) {
-      const double inv = 1.0 / r.d[a];
+      const double inv = r.inv[a];
       const double B = A.hf[a] * inv;
       const double C = (A.dlo[a] - e) * inv;
+      const float bh = (float)B, ch = (float)C;
       // B == 0 must mean d_a == 0: keep the sign of a B that would underflow
-      f.B[a] = (float)B != 0.0f ? (float)B : copysignf(1e-38f, (float)inv);
-      f.C[a] = (float)C;
-      const double ef = ldexp(2.0 * smax * fabs(B) + 2.0 * fabs(C) + 1.0, -22);
-      // an axis whose frame does not fit FP32 always takes the exact path
-      f.Ef[a] = (fabs(B) * smax < 1e30 && fabs(C) < 1e30 && fabs(B) > 1e-30) ? (float)ef
-                                                                           : __int_as_float(0x7f800000);
+      f.B[a] = bh != 0.0f ? bh : copysignf(1e-38f, (float)inv);
+      f.C[a] = ch;
+      f.Bl[a] = (float)(B - (double)bh);
+      f.Cl[a] = (float)(C - (double)ch);
+      const bool fits = fabs(B) * smax + fabs(C) < 1048576.0 && fabs(B) > 1e-30;
+      if (!fits) f.exact_axes |= 1 << a;
     } else {
-      f.B[a] = 0.0f;
-      f.C[a] = 0.0f;
-      f.Ef[a] = __int_as_float(0x7f800000);
+      f.B[a] = f.C[a] = f.Bl[a] = f.Cl[a] = 0.0f;
+      f.exact_axes |= 1 << a;
     }
-    f.Xe[a] = (float)((e - A.dlo[a]) / A.hf[a]);
-    f.Dd[a] = (float)(r.d[a] / A.hf[a]);
+    f.Xe[a] = (float)((e - A.dlo[a]) * A.inv_hf[a]);
+    f.Dd[a] = (float)(r.d[a] * A.inv_hf[a]);
   }
   const double tau_out = r.t_out - r.t_in;
   f.tau_out = (float)tau_out;
   f.e_out = ldexpf(f.tau_out + 1.0f, -22);
 }
 
-// kd-restart descent (Sec. 3.3) from the root for the segment starting at (pid0, tau0):
-// returns the leaf holding the ray just after t0 and narrows (pid1, tau1, e1) to the
-// first split plane beyond t0.  Near child = the side entered first (d_a > 0: lower);
-// t_s >= t1 -> near only; t_s <= t0 -> far only; otherwise near with t1 = t_s;
-// d_a == 0 -> the side holding the origin.  Returns -1 on a malformed tree.
+// kd-restart descent (Sec. 3.3) for the segment starting at (pid0, tau0): returns the leaf
+// holding the ray just after t0 and narrows (pid1, tau1, e1) to the first split plane
+// beyond t0.  Near child = the side entered first (d_a > 0: lower); t_s >= t1 -> near
+// only; t_s <= t0 -> far only; otherwise near with t1 = t_s; d_a == 0 -> the side holding
+// the origin.  Returns -1 on a malformed tree.
+//
+// Push-down (Horn et al.'s refinement of kd-restart): `start` is the deepest node reached
+// before any narrowing, i.e. a node whose box holds the whole remaining ray [t0, t_out].
+// Every later restart takes the same one-sided decisions above it (t0 only grows and t1
+// is t_out there), so restarting at `start` instead of the root yields the same leaves
+// and the same t1 bit for bit.
 __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const RayArgs& A, int px,
-                                       int py, const RayF& rf, int pid0, float tau0, float e0,
-                                       int& pid1, float& tau1, float& e1) {
-  uint32_t i = 0;
+                                       int py, const RayF& rf, uint32_t& start, int pid0,
+                                       float tau0, float e0, int& pid1, float& tau1, float& e1) {
+  uint32_t i = start;
+  bool pushing = true;  // no narrowing yet: the chosen child still holds all of [t0, t_out]
   for (int depth = 0; depth < kMaxDepth; ++depth) {
     const DNode nd = nodes[i];
     const uint32_t ax = nd.meta >> 30;
@@ -207,43 +225,44 @@ __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const Ra
       const double sw = __dadd_rn(sel3(ax, A.dlo[0], A.dlo[1], A.dlo[2]),
                                   __dmul_rn((double)nd.split, sel3(ax, A.hf[0], A.hf[1], A.hf[2])));
       i = idx + (o < sw ? 0u : 1u);
+      if (pushing) start = i;
       continue;
     }
     const int pid = nd.split * 4 + (int)ax;
     const uint32_t near_c = idx + (B > 0.0f ? 0u : 1u);
     const uint32_t far_c = idx + (B > 0.0f ? 1u : 0u);
+    bool narrow = false;
     if (pid == pid0) {  // the plane that produced t0: t_s == t0
       i = far_c;
-      continue;
-    }
-    if (pid == pid1) {  // the plane that produced t1: t_s == t1
+    } else if (pid == pid1) {  // the plane that produced t1: t_s == t1
       i = near_c;
-      continue;
-    }
-    const float ts = fmaf((float)nd.split, B, sel3f(ax, rf.C[0], rf.C[1], rf.C[2]));
-    const float es = sel3f(ax, rf.Ef[0], rf.Ef[1], rf.Ef[2]);
-    if (ts - tau1 > es + e1) {
-      i = near_c;
-    } else if (tau0 - ts > es + e0) {
-      i = far_c;
-    } else if (tau1 - ts > es + e1 && ts - tau0 > es + e0) {
-      i = near_c;
-      pid1 = pid;
-      tau1 = ts;
-      e1 = es;
-    } else {  // too close to call in FP32: decide on the exact FP64 values
-      const int dcs = exact_decide(A, px, py, pid, pid0, pid1);
-      if (dcs == 1) {
-        i = far_c;
-      } else {
+    } else {
+      const float sf = (float)nd.split;
+      const float ts = fmaf(sf, B, sel3f(ax, rf.C[0], rf.C[1], rf.C[2])) +
+                       fmaf(sf, sel3f(ax, rf.Bl[0], rf.Bl[1], rf.Bl[2]),
+                            sel3f(ax, rf.Cl[0], rf.Cl[1], rf.Cl[2]));
+      const float es = ((rf.exact_axes >> ax) & 1) ? __int_as_float(0x7f800000)
+                                                   : ldexpf(fabsf(ts) + 1.0f, -22);
+      if (ts - tau1 > es + e1) {
         i = near_c;
-        if (dcs == 2) {
-          pid1 = pid;
-          tau1 = ts;
-          e1 = es;
-        }
+      } else if (tau0 - ts > es + e0) {
+        i = far_c;
+      } else if (tau1 - ts > es + e1 && ts - tau0 > es + e0) {
+        i = near_c;
+        narrow = true;
+      } else {  // too close to call in FP32: decide on the exact FP64 values
+        const int dcs = exact_decide(A, px, py, pid, pid0, pid1);
+        i = dcs == 1 ? far_c : near_c;
+        narrow = dcs == 2;
+      }
+      if (narrow) {
+        pid1 = pid;
+        tau1 = ts;
+        e1 = es;
       }
     }
+    pushing = pushing && !narrow;
+    if (pushing) start = i;
   }
   return -1;
 }
@@ -554,9 +573,8 @@ __device__ __forceinline__ int segment_count(const RenderArgs& A, int px, int py
   const float inv_step = lv.inv_step;
   const float lenf = (tau1 - tau0) * f.dn;
   const float q = lenf * inv_step;
-  // |q - exact| <= ((e0 + e1) |d| + 2^-21 (tau0 + tau1 + 1) |d|) / step + 2^-21 q
-  const float eq = ((e0 + e1) * f.dn + ldexpf((tau0 + tau1 + 1.0f) * f.dn, -21)) * inv_step +
-                   ldexpf(q + 1.0f, -21);
+  // |q - exact| <= (e0 + e1) |d| / step + 5u q (subtraction, |d|, product, 1/step roundings)
+  const float eq = (e0 + e1) * f.dn * inv_step + ldexpf(q + 1.0f, -21);
   if (q + eq <= 1.0f) return 1;
   const float c = ceilf(q);
   if (c - q > eq && q - (c - 1.0f) > eq && c <= (float)kMaxSamplesPerSegment) return (int)c;
@@ -662,8 +680,14 @@ __device__ __forceinline__ void gradient(const RenderArgs& A, const SegState& s,
           neighbour_value<ST, INTERP, 2, -1>(A, s, beta, k)) * (0.5f * (float)lv.inv_h[2]);
 }
 
+// resident blocks per SM the compiler must allow for (register budget 65536 / (128 x this));
+// 4 (<= 128 registers) measured fastest for the shaded kernels on C2 at 2048^2
+#ifndef AMR_MIN_BLOCKS
+#define AMR_MIN_BLOCKS 4
+#endif
+
 template <int ST, int INTERP, int SHADE>
-__global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ RenderArgs A) {
+__global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) march_kernel(const __grid_constant__ RenderArgs A) {
   extern __shared__ float4 smem[];
   float4* s_tf = smem;
   int* s_nz = reinterpret_cast<int*>(smem + A.tf_n);
@@ -698,6 +722,7 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Rend
       const float Lz = -rf.Dd[2] * (float)A.ray.hf[2] * inv_dn;
       int pid0 = kPidIn;
       float tau0 = 0.0f, e0 = 0.0f;
+      uint32_t start = 0;
       int seg = 0;
       while (pid0 != kPidOut) {
         if (seg >= A.max_segments) {
@@ -707,7 +732,7 @@ __global__ void __launch_bounds__(128) march_kernel(const __grid_constant__ Rend
         ++seg;
         int pid1 = kPidOut;
         float tau1 = rf.tau_out, e1 = rf.e_out;
-        const int lid = descend(A.nodes, A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1);
+        const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;
           break;

@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
   }
   int pid0 = kPidIn;
   float tau0 = 0.0f, e0 = 0.0f;
+  uint32_t start = 0;
   int nseg = 0;
   const float one_minus_eps = A.ert_thresh;  // include a sample while 1 - T < 1 - eps
 
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
         ++nseg;
         int pid1 = kPidOut;
         float tau1 = rf.tau_out, e1 = rf.e_out;
-        const int lid = descend(A.nodes, A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1);
+        const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;
           live = false;

@@ -17,6 +17,7 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
   make_frame(A.ray, rx, rf);
   int pid0 = kPidIn;
   float tau0 = 0.0f, e0 = 0.0f;
+  uint32_t start = 0;
   int n = 0;
   unsigned long long status = 0;
   while (pid0 != kPidOut) {
@@ -26,7 +27,7 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
     }
     int pid1 = kPidOut;
     float tau1 = rf.tau_out, e1 = rf.e_out;
-    const int lid = descend(A.nodes, A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1);
+    const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
     if (lid < 0) {
       status |= kStatusDevice;
       break;
