@@ -139,6 +139,24 @@ amr_status amr_render_host(amr_ctx* ctx, const amr_camera* cam, const float* tf_
                            int32_t tf_n, const amr_render_params* params, float* out_rgba_host,
                            void* cuda_stream, uint64_t* samples_out);
 
+/* amr_render_host for callers that must not allocate device memory during rendering (a
+ * host application whose device memory another allocator owns and caps, or a process
+ * whose device footprint must not grow after start-up).  The paper has no counterpart.
+ * It calls no cudaMalloc / cudaFree: counters, the transfer function and the image are
+ * staged in one fixed 4 MiB + 32 KiB + 64 B array that is part of the library (every GPU
+ * that loads the library holds it until the process exits).  The frame is rendered in
+ * 16-row bands that fit the array and copied band by band into out_rgba_host, so results
+ * equal amr_render_host's; limits: 2 <= tf_n <= 2048, image width <= 16384
+ * (AMR_ERR_ARG beyond them).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) for that device; make that first call before any stream
+ * capture.  Every call reuses the array (the counters are cleared per call); calls that
+ * overlap on the GPU race, so serialise them.  Synchronises the stream before returning;
+ * samples_out (nullable) receives the sample count. */
+amr_status amr_render_host_noalloc(amr_ctx* ctx, const amr_camera* cam,
+                                   const float* tf_rgba_host, int32_t tf_n,
+                                   const amr_render_params* params, float* out_rgba_host,
+                                   void* cuda_stream, uint64_t* samples_out);
+
 /* Release the context and every device allocation it owns (NULL-safe). */
 amr_status amr_destroy(amr_ctx* ctx);
 

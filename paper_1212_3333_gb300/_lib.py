@@ -63,6 +63,9 @@ _SIGS = {
                              C.POINTER(amr_render_params), _P, _P, C.POINTER(C.c_uint64)]),
     "amr_render_host": (C.c_int, [_P, C.POINTER(amr_camera), _P, C.c_int32,
                                   C.POINTER(amr_render_params), _P, _P, C.POINTER(C.c_uint64)]),
+    "amr_render_host_noalloc": (C.c_int, [_P, C.POINTER(amr_camera), _P, C.c_int32,
+                                          C.POINTER(amr_render_params), _P, _P,
+                                          C.POINTER(C.c_uint64)]),
     "amr_destroy": (C.c_int, [_P]),
     "amr_last_error": (C.c_char_p, [_P]),
     "amr_get_stats": (C.c_int, [_P, C.POINTER(amr_stats)]),

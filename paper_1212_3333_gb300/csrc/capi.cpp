@@ -306,6 +306,21 @@ static amr_status finish_render(amr_ctx* c, cudaStream_t st, uint64_t* samples_o
   return AMR_OK;
 }
 
+}  // extern "C"
+
+namespace amr {
+amr_status prepare_render_args(amr_ctx* c, const amr_camera* cam, int32_t tf_n,
+                               const amr_render_params* p, RenderArgs* a) {
+  return prepare_render(c, cam, tf_n, p, a);
+}
+amr_status launch_render_args(amr_ctx* c, const RenderArgs& a, const amr_render_params* p,
+                              void* stream) {
+  return launch_render(c, a, c->storage, p->interp, kernel_shade(c, p), p->schedule, stream);
+}
+}  // namespace amr
+
+extern "C" {
+
 amr_status amr_render(amr_ctx* c, const amr_camera* cam, const float* tf_rgba_dev, int32_t tf_n,
                       const amr_render_params* params, float* out_rgba_dev, void* cuda_stream,
                       uint64_t* samples_out) {

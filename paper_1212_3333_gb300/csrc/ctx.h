@@ -102,4 +102,10 @@ void fill_ray(const amr_ctx* c, const amr_camera* cam, int row0, int rows, RayAr
 
 amr_status fail(amr_ctx* c, amr_status s, const std::string& msg);
 
+// kernel argument block of one render call (capi.cpp), and its launch
+amr_status prepare_render_args(amr_ctx* c, const amr_camera* cam, int32_t tf_n,
+                               const amr_render_params* p, RenderArgs* a);
+amr_status launch_render_args(amr_ctx* c, const RenderArgs& a, const amr_render_params* p,
+                              void* stream);
+
 }  // namespace amr
