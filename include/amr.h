@@ -92,6 +92,10 @@ typedef struct {
                          warp's current segments spread over its lanes, shading on the
                          compacted opaque samples; pays off when rays diverge, e.g. small
                          views of a large volume) */
+  int32_t learned;    /* learned segment proposal (needs amr_set_proposal; trilinear; ptr or
+                         atlas_linear storage): 0 off; 1 skip segments whose predicted
+                         contribution is below tau; 2 sample them with a 4x coarser step */
+  double tau;         /* proposal threshold (default 1e-3) */
 } amr_render_params;
 
 /* Fills p with the defaults: step 0.5, kappa 8, ert_eps 1e-4, vmin 0, vmax 1, ka 0.3,
@@ -156,6 +160,58 @@ amr_status amr_render_host_noalloc(amr_ctx* ctx, const amr_camera* cam,
                                    const float* tf_rgba_host, int32_t tf_n,
                                    const amr_render_params* params, float* out_rgba_host,
                                    void* cuda_stream, uint64_t* samples_out);
+
+/* ---------------------------------------------------------------------------------- */
+/* learned segment proposal (not in the paper): a 12-64-64-64-1 MLP, ReLU hidden layers,  */
+/* sigmoid output, predicting a segment's opacity contribution A_out - A_in from 12       */
+/* features: entry xyz, exit xyz (root-box units), level / (L-1), leaf value min and max  */
+/* through the TF domain, accumulated opacity, octahedral ray direction.                  */
+/* ---------------------------------------------------------------------------------- */
+
+#define AMR_MLP_FEATURES 12
+#define AMR_MLP_PARAMS 9217      /* W1[64][12] b1[64] W2[64][64] b2[64] W3[64][64] b3[64]
+                                    W4[1][64] b4[1], FP32, W[out][in] row-major */
+#define AMR_MLP_PACKED_BYTES 23440 /* inference image: BF16 weights, padded rows, FP32 biases */
+
+/* Record training data: the plain march of one view (no early termination) writes, for each
+ * segment a seeded hash keeps with probability keep_prob, its 12 features to
+ * features_dev[k*12 ..] and its contribution A_out - A_in to targets_dev[k], where
+ * k = atomicAdd(count_dev, 1) (caller zeroes *count_dev; records with k >= capacity are
+ * dropped but still counted).  Storage must be ptr or atlas_linear.  Asynchronous. */
+amr_status amr_log_segments(amr_ctx* ctx, const amr_camera* cam, const float* tf_rgba_dev,
+                            int32_t tf_n, const amr_render_params* params, float* features_dev,
+                            float* targets_dev, int64_t capacity, unsigned long long* count_dev,
+                            float keep_prob, uint32_t seed, void* cuda_stream);
+
+/* FP32 parameters (AMR_MLP_PARAMS, device) -> packed inference image (AMR_MLP_PACKED_BYTES,
+ * device, 16-byte aligned): BF16 weights as the tensor-core kernels read them. */
+amr_status amr_mlp_pack(const float* params_dev, void* packed_dev, void* cuda_stream);
+
+/* Inference through the same mma.sync BF16 warp routine the learned march uses:
+ * y_dev[r] = sigmoid(MLP(x_dev[r*12 ..])) for r < n (FP32 accumulation, activations rounded
+ * to BF16 between layers).  Asynchronous.  Errors: amr_last_error(NULL). */
+amr_status amr_mlp_forward(const void* packed_dev, const float* x_dev, int64_t n, float* y_dev,
+                           void* cuda_stream);
+
+/* Mean binary cross-entropy of sigmoid(MLP(x)) against targets t in [0,1] over a batch of n
+ * rows and its gradient with respect to all AMR_MLP_PARAMS parameters.  Batch row r is
+ * dataset row (perm_a * (first + r) + perm_b) mod n_total of x_dev[n_total][12] and
+ * t_dev[n_total]; with perm_a coprime to n_total, consecutive batches walk a pseudo-random
+ * permutation (perm_a = 1, perm_b = 0: rows first .. first + n - 1).  The forward rounds
+ * weights and activations to BF16 as inference does; the backward is FP32.  Overwrites
+ * grad_dev and loss_dev[0].  Asynchronous.  Limits: n_total, perm_a < 2^31. */
+amr_status amr_mlp_loss_grad(const float* params_dev, const float* x_dev, const float* t_dev,
+                             int64_t n_total, int64_t first, int64_t n, int64_t perm_a,
+                             int64_t perm_b, float* grad_dev, float* loss_dev, void* cuda_stream);
+
+/* One Adam step (bias-corrected, step >= 1) on the AMR_MLP_PARAMS FP32 parameters. */
+amr_status amr_mlp_adam(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev,
+                        float lr, float beta1, float beta2, float eps, int32_t step,
+                        void* cuda_stream);
+
+/* Install packed proposal weights (device, AMR_MLP_PACKED_BYTES) in the context for renders
+ * with params->learned != 0.  Copies them; synchronises the stream. */
+amr_status amr_set_proposal(amr_ctx* ctx, const void* packed_dev, void* cuda_stream);
 
 /* Release the context and every device allocation it owns (NULL-safe). */
 amr_status amr_destroy(amr_ctx* ctx);

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "AMR_OK", 1: "AMR_ERR_ARG", 2: "AMR_ERR_OVERLAP", 3: "AMR_ERR
 AMR_F32, AMR_F16, AMR_BF16 = 0, 1, 2
 AMR_STORE_PTR, AMR_STORE_TEXOBJ, AMR_STORE_ATLAS_LINEAR, AMR_STORE_ATLAS_TEX3D = 0, 1, 2, 3
 AMR_STORE_GRADIENT = 0x100
+AMR_MLP_FEATURES, AMR_MLP_PARAMS, AMR_MLP_PACKED_BYTES = 12, 9217, 23440
 STORAGES = {"ptr": AMR_STORE_PTR, "texobj": AMR_STORE_TEXOBJ,
             "atlas_linear": AMR_STORE_ATLAS_LINEAR, "atlas_tex3d": AMR_STORE_ATLAS_TEX3D}
 
@@ -37,7 +38,8 @@ class amr_render_params(C.Structure):
                 ("kd", C.c_double), ("ks", C.c_double), ("shininess", C.c_double),
                 ("gamma", C.c_double), ("interp", C.c_int32), ("shade", C.c_int32),
                 ("row0", C.c_int32), ("rows", C.c_int32), ("skip", C.c_int32),
-                ("max_segments", C.c_int32), ("schedule", C.c_int32)]
+                ("max_segments", C.c_int32), ("schedule", C.c_int32),
+                ("learned", C.c_int32), ("tau", C.c_double)]
 
 
 class amr_stats(C.Structure):
@@ -66,6 +68,16 @@ _SIGS = {
     "amr_render_host_noalloc": (C.c_int, [_P, C.POINTER(amr_camera), _P, C.c_int32,
                                           C.POINTER(amr_render_params), _P, _P,
                                           C.POINTER(C.c_uint64)]),
+    "amr_log_segments": (C.c_int, [_P, C.POINTER(amr_camera), _P, C.c_int32,
+                                   C.POINTER(amr_render_params), _P, _P, C.c_int64, _P, C.c_float,
+                                   C.c_uint32, _P]),
+    "amr_mlp_pack": (C.c_int, [_P, _P, _P]),
+    "amr_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
+    "amr_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                    C.c_int64, _P, _P, _P]),
+    "amr_mlp_adam": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_float, C.c_float, C.c_float,
+                               C.c_int32, _P]),
+    "amr_set_proposal": (C.c_int, [_P, _P, _P]),
     "amr_destroy": (C.c_int, [_P]),
     "amr_last_error": (C.c_char_p, [_P]),
     "amr_get_stats": (C.c_int, [_P, C.POINTER(amr_stats)]),

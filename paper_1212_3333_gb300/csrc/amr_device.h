@@ -94,6 +94,10 @@ struct RenderArgs {
   float ka, kd, ks, shininess, gfloor_num;  // gfloor = gfloor_num / hmin_l
   float4* out;
   unsigned long long* counters;  // [0] samples, [1] status bits
+  const unsigned char* mlp;      // packed learned-proposal weights (inference image)
+  float tau;                     // proposal threshold on the predicted contribution
+  int32_t learned;               // 0 off, 1 skip, 2 coarse (4x step) below tau
+  float inv_levels;              // 1 / (L - 1), 0 for one level
 };
 
 struct TraceArgs {

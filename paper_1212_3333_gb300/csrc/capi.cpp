@@ -103,6 +103,8 @@ void amr_default_params(amr_render_params* p) {
   p->skip = 0;
   p->max_segments = 0;
   p->schedule = 0;
+  p->learned = 0;
+  p->tau = 1e-3;
 }
 
 amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double domain_lo[3],
@@ -283,6 +285,16 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->gfloor_num = (float)(p->gamma * (p->vmax - p->vmin));
   a->counters = c->dev.counters;
   a->ray.counters = c->dev.counters;
+  a->mlp = c->dev.proposal;
+  a->tau = (float)p->tau;
+  a->learned = p->learned;
+  a->inv_levels = c->L > 1 ? 1.0f / (float)(c->L - 1) : 0.0f;
+  if (p->learned != 0) {
+    if (p->learned != 1 && p->learned != 2) return fail(c, AMR_ERR_ARG, "unknown learned mode");
+    if (!c->dev.proposal) return fail(c, AMR_ERR_STATE, "learned render before amr_set_proposal");
+    if (p->interp != AMR_INTERP_TRILINEAR)
+      return fail(c, AMR_ERR_ARG, "the learned proposal renders with trilinear sampling");
+  }
   return AMR_OK;
 }
 
@@ -315,6 +327,7 @@ amr_status prepare_render_args(amr_ctx* c, const amr_camera* cam, int32_t tf_n,
 }
 amr_status launch_render_args(amr_ctx* c, const RenderArgs& a, const amr_render_params* p,
                               void* stream) {
+  if (p->learned) return launch_learned(c, a, c->storage, kernel_shade(c, p), stream);
   return launch_render(c, a, c->storage, p->interp, kernel_shade(c, p), p->schedule, stream);
 }
 }  // namespace amr
@@ -334,8 +347,7 @@ amr_status amr_render(amr_ctx* c, const amr_camera* cam, const float* tf_rgba_de
   a.out = reinterpret_cast<float4*>(out_rgba_dev);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   CK(cudaMemsetAsync(c->dev.counters, 0, kNumCounters * sizeof(unsigned long long), st));
-  s = launch_render(c, a, c->storage, params->interp, kernel_shade(c, params), params->schedule,
-                    cuda_stream);
+  s = launch_render_args(c, a, params, cuda_stream);
   if (s != AMR_OK) return s;
   return finish_render(c, st, samples_out);
 }
@@ -369,13 +381,44 @@ amr_status amr_render_host(amr_ctx* c, const amr_camera* cam, const float* tf_rg
   a.tf = d.tf_scratch;
   a.out = d.img_scratch;
   CK(cudaMemsetAsync(d.counters, 0, kNumCounters * sizeof(unsigned long long), st));
-  s = launch_render(c, a, c->storage, params->interp, kernel_shade(c, params), params->schedule,
-                    cuda_stream);
+  s = launch_render_args(c, a, params, cuda_stream);
   if (s != AMR_OK) return s;
   CK(cudaMemcpyAsync(out_rgba_host, d.img_scratch, img_bytes, cudaMemcpyDeviceToHost, st));
   if (samples_out) return finish_render(c, st, samples_out);
   CK(cudaStreamSynchronize(st));
   return AMR_OK;
+}
+
+amr_status amr_set_proposal(amr_ctx* c, const void* packed_dev, void* cuda_stream) {
+  if (!c) return AMR_ERR_ARG;
+  if (!c->device_built) return fail(c, AMR_ERR_STATE, "amr_set_proposal before amr_build_kdtree");
+  if (!packed_dev) return fail(c, AMR_ERR_ARG, "packed weights are NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!c->dev.proposal) CK(cudaMalloc(&c->dev.proposal, AMR_MLP_PACKED_BYTES));
+  CK(cudaMemcpyAsync(c->dev.proposal, packed_dev, AMR_MLP_PACKED_BYTES, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return AMR_OK;
+}
+
+amr_status amr_log_segments(amr_ctx* c, const amr_camera* cam, const float* tf_rgba_dev,
+                            int32_t tf_n, const amr_render_params* params, float* features_dev,
+                            float* targets_dev, int64_t capacity, unsigned long long* count_dev,
+                            float keep_prob, uint32_t seed, void* cuda_stream) {
+  if (!params) return fail(c, AMR_ERR_ARG, "params is NULL");
+  amr_render_params p = *params;
+  p.ert_eps = 0.0;  // log every segment of the ray
+  p.learned = 0;
+  p.interp = AMR_INTERP_TRILINEAR;
+  RenderArgs a;
+  amr_status s = prepare_render(c, cam, tf_n, &p, &a);
+  if (s != AMR_OK) return s;
+  if (!tf_rgba_dev || !features_dev || !targets_dev || !count_dev || capacity < 0)
+    return fail(c, AMR_ERR_ARG, "bad segment-log buffers");
+  if (!(keep_prob >= 0.0f && keep_prob <= 1.0f))
+    return fail(c, AMR_ERR_ARG, "keep_prob must be in [0, 1]");
+  a.tf = reinterpret_cast<const float4*>(tf_rgba_dev);
+  return launch_log(c, a, c->storage, features_dev, targets_dev, capacity, count_dev, keep_prob,
+                    seed, cuda_stream);
 }
 
 amr_status amr_destroy(amr_ctx* c) {
@@ -386,7 +429,8 @@ amr_status amr_destroy(amr_ctx* c) {
 }
 
 const char* amr_last_error(const amr_ctx* c) {
-  return c ? c->err.c_str() : g_create_error.c_str();
+  if (c) return c->err.c_str();
+  return g_create_error.empty() ? amr::mlp_last_error() : g_create_error.c_str();
 }
 
 amr_status amr_get_stats(const amr_ctx* c, amr_stats* out) {

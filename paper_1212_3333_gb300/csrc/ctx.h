@@ -52,6 +52,7 @@ struct DeviceState {
   float4* tf_scratch = nullptr;                  // staging for amr_render_host
   int tf_scratch_n = 0;
   float4* img_scratch = nullptr;
+  unsigned char* proposal = nullptr;             // packed MLP weights (amr_set_proposal)
   size_t img_scratch_bytes = 0;
   int device = -1;
 };
@@ -97,6 +98,11 @@ void release_device(amr_ctx* c);
 amr_status launch_render(amr_ctx* c, const RenderArgs& a, int storage, int interp, int shade,
                          int schedule, void* stream);
 amr_status launch_trace(amr_ctx* c, const TraceArgs& a, void* stream);
+amr_status launch_learned(amr_ctx* c, const RenderArgs& a, int storage, int shade, void* stream);
+amr_status launch_log(amr_ctx* c, const RenderArgs& a, int storage, float* features,
+                      float* targets, long long cap, unsigned long long* count, float keep_prob,
+                      uint32_t seed, void* stream);
+const char* mlp_last_error();
 void fill_levels(const amr_ctx* c, DLevel* lv, double step_factor);
 void fill_ray(const amr_ctx* c, const amr_camera* cam, int row0, int rows, RayArgs* ra);
 

@@ -185,6 +185,7 @@ void release_device(amr_ctx* c) {
   cudaFree(d.pool);
   cudaFree(d.counters);
   cudaFree(d.tf_scratch);
+  cudaFree(d.proposal);
   cudaFree(d.img_scratch);
   d = DeviceState();
   c->device_built = false;

@@ -680,6 +680,96 @@ __device__ __forceinline__ void gradient(const RenderArgs& A, const SegState& s,
           neighbour_value<ST, INTERP, 2, -1>(A, s, beta, k)) * (0.5f * (float)lv.inv_h[2]);
 }
 
+// A segment ready for sampling: its state, first sample position and step in brick
+// coordinates, and the world length of one sub-step.
+struct SegSetup {
+  SegState s;
+  float b0[3], db[3];
+  float delta;
+};
+
+// Sample parameters of segment (pid0, pid1) of leaf `lid` with n midpoint samples, and the
+// bound on their FP32 error: the tau ends within max(e0, e1), a few roundings of the tau
+// arithmetic, then the position and brick-space roundings.
+__device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& rf, const DLeaf& lf,
+                                              const DLevel& lv, int lid, int pid0, int pid1,
+                                              float tau0, float e0, float tau1, float e1, int n,
+                                              int px, int py, SegSetup& g) {
+  SegState& s = g.s;
+  s.brick = load_brick(A.patches, lf.patch);
+  s.level = lf.level;
+  s.leaf = lid;
+  s.pid0 = pid0;
+  s.pid1 = pid1;
+  s.n = n;
+  s.px = px;
+  s.py = py;
+  const float nfl = (float)n;
+  const float dtau = (tau1 - tau0) / nfl;
+  g.delta = dtau * rf.dn;
+  const float taum = fmaf(0.5f, dtau, tau0);
+  const float etau = fmaxf(e0, e1) + ldexpf(tau1 + 1.0f, -21);
+  float ex = 0.0f, bmax = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float xm = fmaf(taum, rf.Dd[a], rf.Xe[a]);  // finest units
+    const float lo05 = 0.5f - (float)s.brick.lo[a];
+    g.b0[a] = fmaf(xm, lv.inv_sc, lo05);
+    g.db[a] = dtau * rf.Dd[a] * lv.inv_sc;
+    s.leaf_lo[a] = lf.lo[a];
+    s.bl[a] = (float)(lf.lo[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
+    s.bh[a] = (float)(lf.hi[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
+    const float ea = fabsf(rf.Dd[a]) * etau +
+                     ldexpf(fabsf(rf.Xe[a]) + fabsf(xm) + nfl * fabsf(dtau * rf.Dd[a]) + 1.0f, -21);
+    ex = fmaxf(ex, ea);
+    bmax = fmaxf(bmax, fabsf(g.b0[a]) + nfl * fabsf(g.db[a]) + (float)s.brick.dim[a]);
+  }
+  s.margin = ex * lv.inv_sc + ldexpf(bmax + 2.0f, -21);
+}
+
+// March the samples of one segment front to back (Sec. 3: emission-absorption
+// compositing; Sec. 4: gradient shading).  Returns true when early termination stops the
+// ray inside the segment.
+template <int ST, int INTERP, int SHADE>
+__device__ __forceinline__ bool sample_segment(const RenderArgs& A, const float4* s_tf,
+                                               const SegSetup& g, const DLevel& lv, float Lx,
+                                               float Ly, float Lz, float& C0, float& C1, float& C2,
+                                               float& Acc, unsigned& nsamp) {
+  const SegState& s = g.s;
+  for (int k = 0; k < s.n; ++k) {
+    float beta[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
+    const float v = sample_value<ST, INTERP>(A, s, beta, k);
+    const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
+    ++nsamp;
+    if (c.w <= 0.0f) continue;
+    const float alpha = -expm1f(-A.kappa * c.w * g.delta);
+    float cr = c.x, cg = c.y, cb = c.z;
+    if constexpr (SHADE >= 1) {
+      float gr[3];
+      gradient<ST, INTERP, (SHADE == 2)>(A, s, beta, k, lv, gr);
+      const float gn = sqrtf(fmaf(gr[0], gr[0], fmaf(gr[1], gr[1], gr[2] * gr[2])));
+      const float gf = A.gfloor_num / lv.hmin;
+      const float den = fmaxf(gn, gf);
+      const float inv = den > 0.0f ? 1.0f / den : 0.0f;
+      const float ndl = fabsf((gr[0] * Lx + gr[1] * Ly + gr[2] * Lz) * inv);
+      const float spec = A.ks * __powf(ndl, A.shininess);
+      const float diff = fmaf(A.kd, ndl, A.ka);
+      cr = fminf(fmaxf(fmaf(cr, diff, spec), 0.0f), 1.0f);
+      cg = fminf(fmaxf(fmaf(cg, diff, spec), 0.0f), 1.0f);
+      cb = fminf(fmaxf(fmaf(cb, diff, spec), 0.0f), 1.0f);
+    }
+    const float w = (1.0f - Acc) * alpha;
+    C0 = fmaf(w, cr, C0);
+    C1 = fmaf(w, cg, C1);
+    C2 = fmaf(w, cb, C2);
+    Acc += w;
+    if (Acc >= A.ert_thresh) return true;
+  }
+  return false;
+}
+
 // resident blocks per SM the compiler must allow for (register budget 65536 / (128 x this));
 // 4 (<= 128 registers) measured fastest for the shaded kernels on C2 at 2048^2
 #ifndef AMR_MIN_BLOCKS
@@ -750,73 +840,10 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) march_kernel(const __grid
           e0 = e1;
           continue;
         }
-        SegState s;
-        s.brick = load_brick(A.patches, lf.patch);
-        s.level = lf.level;
-        s.leaf = lid;
-        s.pid0 = pid0;
-        s.pid1 = pid1;
-        s.n = n;
-        s.px = i;
-        s.py = j;
-        const float nfl = (float)n;
-        const float dtau = (tau1 - tau0) / nfl;
-        const float delta = dtau * rf.dn;
-        const float taum = fmaf(0.5f, dtau, tau0);
-        // error of the FP32 sample parameters: tau ends within max(e0, e1), a few
-        // roundings of the tau arithmetic, then the position and brick-space roundings
-        const float etau = fmaxf(e0, e1) + ldexpf(tau1 + 1.0f, -21);
-        float b0[3], db[3];
-        float ex = 0.0f, bmax = 0.0f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float xm = fmaf(taum, rf.Dd[a], rf.Xe[a]);  // finest units
-          const float lo05 = 0.5f - (float)s.brick.lo[a];
-          b0[a] = fmaf(xm, lv.inv_sc, lo05);
-          db[a] = dtau * rf.Dd[a] * lv.inv_sc;
-          s.leaf_lo[a] = lf.lo[a];
-          s.bl[a] = (float)(lf.lo[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
-          s.bh[a] = (float)(lf.hi[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
-          const float ea = fabsf(rf.Dd[a]) * etau +
-                           ldexpf(fabsf(rf.Xe[a]) + fabsf(xm) + nfl * fabsf(dtau * rf.Dd[a]) + 1.0f, -21);
-          ex = fmaxf(ex, ea);
-          bmax = fmaxf(bmax, fabsf(b0[a]) + nfl * fabsf(db[a]) + (float)s.brick.dim[a]);
-        }
-        s.margin = ex * lv.inv_sc + ldexpf(bmax + 2.0f, -21);
-        for (int k = 0; k < n; ++k) {
-          float beta[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, db[a], b0[a]);
-          const float v = sample_value<ST, INTERP>(A, s, beta, k);
-          const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
-          ++nsamp;
-          if (c.w <= 0.0f) continue;
-          const float alpha = -expm1f(-A.kappa * c.w * delta);
-          float cr = c.x, cg = c.y, cb = c.z;
-          if constexpr (SHADE >= 1) {
-            float g[3];
-            gradient<ST, INTERP, (SHADE == 2)>(A, s, beta, k, lv, g);
-            const float gn = sqrtf(fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2])));
-            const float gf = A.gfloor_num / lv.hmin;
-            const float den = fmaxf(gn, gf);
-            const float inv = den > 0.0f ? 1.0f / den : 0.0f;
-            const float ndl = fabsf((g[0] * Lx + g[1] * Ly + g[2] * Lz) * inv);
-            const float spec = A.ks * __powf(ndl, A.shininess);
-            const float diff = fmaf(A.kd, ndl, A.ka);
-            cr = fminf(fmaxf(fmaf(cr, diff, spec), 0.0f), 1.0f);
-            cg = fminf(fmaxf(fmaf(cg, diff, spec), 0.0f), 1.0f);
-            cb = fminf(fmaxf(fmaf(cb, diff, spec), 0.0f), 1.0f);
-          }
-          const float w = (1.0f - Acc) * alpha;
-          C0 = fmaf(w, cr, C0);
-          C1 = fmaf(w, cg, C1);
-          C2 = fmaf(w, cb, C2);
-          Acc += w;
-          if (Acc >= A.ert_thresh) {
-            pid1 = kPidOut;  // done
-            break;
-          }
-        }
+        SegSetup g;
+        setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
+        if (sample_segment<ST, INTERP, SHADE>(A, s_tf, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
+          pid1 = kPidOut;  // early ray termination
         pid0 = pid1;
         tau0 = tau1;
         e0 = e1;
