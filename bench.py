@@ -181,6 +181,75 @@ def cpu_baseline(hier, cam, tf, vmin, vmax, shade, budget_s=15.0, seed=0):
                       f"({total_samples} samples, {total_s:.1f} s), FP64 oracle, {threads} threads"}
 
 
+def learned_eval(amr, ctx, hier, vmin, vmax, tf, args, taus=(1e-4, 3e-4, 1e-3, 3e-3, 1e-2)):
+    """Learned segment proposal on the same hierarchy: log segments from 256 seeded poses
+    (seeds 1000-1255), train the MLP with the library's kernels, then time held-out views
+    (seeds 2000-2007) at the bench size: plain march, exact min/max skipping, and min/max +
+    learned skipping (and 4x coarse sampling) for each tau, PSNR against the plain march."""
+    import torch
+
+    import synth
+    from paper_1212_3333_gb300 import proposal
+
+    t0 = time.perf_counter()
+    p_log = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=0)
+    poses = [synth.orbit_camera(1000 + s, args.log_size, args.log_size) for s in range(256)]
+    feats, tgts, seen = proposal.log_segments(ctx, poses, tf, p_log, capacity=args.log_cap,
+                                              keep_prob=args.log_keep, seed=1)
+    t_log = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    prop = proposal.Proposal(seed=0)
+    losses = prop.train(feats, tgts, epochs=args.epochs, batch=16384, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    prop.install(ctx)
+    size = args.size
+    out = torch.empty((size, size, 4), dtype=torch.float32, device="cuda")
+    ref = torch.empty_like(out)
+    stream = torch.cuda.current_stream()
+
+    def timed(cam, params, reps=2):
+        ctx.amr_render(cam, tf, params, out)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            ctx.amr_render(cam, tf, params, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    base = dict(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
+    configs = {"plain": {}, "minmax": {"skip": 1}}
+    for tau in taus:
+        configs[f"skip@{tau:g}"] = {"skip": 1, "learned": 1, "tau": tau}
+        configs[f"coarse@{tau:g}"] = {"skip": 1, "learned": 2, "tau": tau}
+    res = {k: {"ms": 0.0, "psnr_min": float("inf"), "samples": 0} for k in configs}
+    views = [synth.orbit_camera(2000 + s, size, size) for s in range(args.heldout)]
+    for cam in views:
+        ctx.amr_render(cam, tf, amr.amr_default_params(**base), ref)
+        for name, extra_p in configs.items():
+            prm = amr.amr_default_params(**base, **extra_p)
+            n = ctx.amr_render(cam, tf, prm, out, count_samples=True)
+            res[name]["samples"] += n
+            res[name]["psnr_min"] = min(res[name]["psnr_min"], proposal.psnr(out, ref))
+            res[name]["ms"] += timed(cam, prm)
+    t_plain, t_minmax = res["plain"]["ms"], res["minmax"]["ms"]
+    best = None
+    for name in configs:
+        r = res[name]
+        r["speedup_vs_plain"] = t_plain / r["ms"]
+        r["speedup_vs_minmax"] = t_minmax / r["ms"]
+        if name.startswith(("skip@", "coarse@")) and r["psnr_min"] >= 45.0:
+            if best is None or r["ms"] < res[best]["ms"]:
+                best = name
+    return {"train": {"poses": 256, "log_size": args.log_size, "segments_seen": seen,
+                      "records": int(feats.shape[0]), "epochs": args.epochs,
+                      "loss_per_epoch": losses, "log_s": t_log, "train_s": t_train},
+            "heldout_views": len(views), "results": res, "best_at_psnr45": best,
+            "learned_speedup_vs_plain": res[best]["speedup_vs_plain"] if best else None,
+            "learned_speedup_vs_minmax": res[best]["speedup_vs_minmax"] if best else None,
+            "minmax_speedup_vs_plain": t_plain / t_minmax}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -237,6 +306,12 @@ def main():
     ap.add_argument("--size", type=int, default=SIZE, help="image side (the metric is at 2048)")
     ap.add_argument("--schedule", type=int, default=0, help="0 per-ray loop, 1 warp wavefront")
     ap.add_argument("--gradient", type=int, default=1, help="build gradient bricks")
+    ap.add_argument("--learned", type=int, default=1, help="evaluate the learned proposal")
+    ap.add_argument("--log-size", type=int, default=96)
+    ap.add_argument("--log-cap", type=int, default=10_000_000)
+    ap.add_argument("--log-keep", type=float, default=0.3)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--heldout", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -366,6 +441,8 @@ def main():
                                   "efficiency_with_halo": s2.atlas_efficiency_halo}
             c2.amr_destroy()
         extra["storages"] = comp
+    if args.learned and world == 1:
+        extra["learned"] = learned_eval(amr, ctx, hier, vmin, vmax, tf, args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
