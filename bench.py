@@ -31,7 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "Gsamples/s and frames/s at 2048² (fraction of HBM roofline); learned-skip speedup at PSNR≥45 dB"
 UNIT = "Gsamples/s"
 SIZE = 2048
-BYTES_PER_SAMPLE = {0: 32, 1: 224}  # trilinear stencil, x7 with the six gradient stencils
+BYTES_PER_SAMPLE = {0: 32, 1: 224}  # FP32 trilinear stencil, x7 with the six gradient stencils
+CELL_BYTES = {"f32": 4, "f16": 2, "bf16": 2}
 
 
 def _peaks():
@@ -51,7 +52,11 @@ def _march_sha() -> str:
     return h.hexdigest()[:12]
 
 
-def _profiled_traffic(shade: int, storage: str, size: int):
+def _variant(storage: str, gradient: bool, dtype: str) -> str:
+    return f"{storage}{'+grad' if gradient else ''}/{dtype}"
+
+
+def _profiled_traffic(shade: int, variant: str, size: int):
     """dram bytes per launch from the committed ncu summary, if it was taken on the
     current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "march_c2_traffic.md")
@@ -61,7 +66,7 @@ def _profiled_traffic(shade: int, storage: str, size: int):
     for line in open(path):
         parts = line.strip().split("|")
         parts = [p.strip() for p in parts if p.strip()]
-        if (len(parts) >= 5 and parts[0] == sha and parts[1] == storage and parts[2] == str(shade)
+        if (len(parts) >= 5 and parts[0] == sha and parts[1] == variant and parts[2] == str(shade)
                 and parts[3] == str(size)):
             try:
                 return float(parts[4])
@@ -250,6 +255,48 @@ def learned_eval(amr, ctx, hier, vmin, vmax, tf, args, taus=(1e-4, 3e-4, 1e-3, 3
             "minmax_speedup_vs_plain": t_plain / t_minmax}
 
 
+def precision_eval(amr, hier, vmin, vmax, cam, tf, out, args, peak):
+    """Cell storage precision: FP32 / FP16 / BF16 bricks (pointer table, gradient bricks),
+    each timed plain and Phong, with PSNR and max-abs of its Phong image against the
+    FP32-storage image of the same view."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    res = {}
+    ref = None
+    for dtype, e in (("f32", 4), ("f16", 2), ("bf16", 2)):
+        ctx = amr.from_hierarchy(hier, dtype)
+        ctx.amr_build_kdtree("ptr", gradient=True)
+        r = {"brick_mb": ctx.amr_get_stats().brick_bytes / 1e6}
+        for shade in (0, 1):
+            p = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=shade, ert_eps=args.ert)
+            n = ctx.amr_render(cam, tf, p, out, count_samples=True)
+            for _ in range(2):
+                ctx.amr_render(cam, tf, p, out)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(5):
+                ctx.amr_render(cam, tf, p, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 5
+            bps = 8 * e * (7 if shade else 1)
+            key = "phong" if shade else "plain"
+            r[key] = {"gsamples_s": n / ms / 1e6, "ms": ms, "bytes_per_sample": bps,
+                      "frac_hbm": n * bps / (ms * 1e-3) / 1e9 / peak}
+        img = out.double().clone()  # the Phong image
+        if ref is None:
+            ref = img
+        else:
+            d = (img - ref).abs()
+            mse = float((d ** 2).mean())
+            r["psnr_vs_f32_storage_db"] = float("inf") if mse == 0 else 10 * math.log10(1 / mse)
+            r["max_abs_vs_f32_storage"] = float(d.max())
+        res[dtype] = r
+        ctx.amr_destroy()
+    return res
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -286,6 +333,7 @@ def _config(hier, args, storage, size=SIZE):
                          f"{'Phong' if args.shade else 'unshaded'} trilinear; step 0.5 h^l; "
                          f"ERT eps {args.ert}"),
             "storage": storage + ("+gradient bricks" if getattr(args, "gradient", 0) else ""),
+            "cells": getattr(args, "dtype", "f32"),
             "image": [size, size], "shade": args.shade,
             "l2": "inputs larger than L2: 602 MB of bricks vs 129 MB L2, no flush"}
 
@@ -306,7 +354,10 @@ def main():
     ap.add_argument("--size", type=int, default=SIZE, help="image side (the metric is at 2048)")
     ap.add_argument("--schedule", type=int, default=0, help="0 per-ray loop, 1 warp wavefront")
     ap.add_argument("--gradient", type=int, default=1, help="build gradient bricks")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"],
+                    help="brick cell storage type (interpolation and compositing stay FP32)")
     ap.add_argument("--learned", type=int, default=1, help="evaluate the learned proposal")
+    ap.add_argument("--precision", type=int, default=1, help="time FP16 / BF16 cell storage")
     ap.add_argument("--log-size", type=int, default=96)
     ap.add_argument("--log-cap", type=int, default=10_000_000)
     ap.add_argument("--log-keep", type=float, default=0.3)
@@ -335,7 +386,7 @@ def main():
     cam = synth.orbit_camera(2 + rank, size, size)   # each rank its own view
     tf_h = synth.ramp_tf()
     tf = torch.as_tensor(tf_h, device="cuda")
-    ctx = amr.from_hierarchy(hier)
+    ctx = amr.from_hierarchy(hier, args.dtype)
     t0 = time.perf_counter()
     ctx.amr_build_kdtree(args.storage, gradient=bool(args.gradient))
     build_s = time.perf_counter() - t0
@@ -397,13 +448,14 @@ def main():
     if rank != 0:
         return
     peak, peak_kind = _peaks()
-    bps = BYTES_PER_SAMPLE[args.shade]
+    bps = BYTES_PER_SAMPLE[args.shade] * CELL_BYTES[args.dtype] // 4
+    variant = _variant(args.storage, bool(args.gradient), args.dtype)
     achieved = samples * bps / (kern_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": _profiled_traffic(args.shade, args.storage, size),
+            "frac": achieved / peak, "traffic": _profiled_traffic(args.shade, variant, size),
             "peak_kind": peak_kind, "bytes_per_sample": bps,
             "kernel": ("march_kernel" if args.schedule == 0 else "wave_kernel") +
-                      "<storage, trilinear, phong>",
+                      f"<{variant}, trilinear, {'phong' if args.shade else 'plain'}>",
             "kernel_ms": kern_ms}
     extra = {"frames_per_s": fps, "samples_per_frame": samples, "build_s": build_s,
              "exact_fp64_paths_per_frame": {"descent": exact_paths[0], "count": exact_paths[1],
@@ -441,11 +493,13 @@ def main():
                                   "efficiency_with_halo": s2.atlas_efficiency_halo}
             c2.amr_destroy()
         extra["storages"] = comp
+    if args.precision and world == 1:
+        extra["precision"] = precision_eval(amr, hier, vmin, vmax, cam, tf, out, args, peak)
     if args.learned and world == 1:
         extra["learned"] = learned_eval(amr, ctx, hier, vmin, vmax, tf, args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": _config(hier, args, args.storage, size), "gpu_launches": args.steps,
             "e2e": e2e, "roofline": roof, "clocks": clk, "extra": extra}
     if args.cpu_baseline and world == 1:

@@ -47,6 +47,11 @@ typedef enum {
   AMR_ERR_DEVICE = 8      /* the device reported an inconsistent structure */
 } amr_status;
 
+/* Device storage type of the brick cells.  AMR_F16 (IEEE binary16) and AMR_BF16 (bfloat16)
+ * halve the brick bytes; cells are rounded to nearest-even once at upload and widened to
+ * FP32 before interpolation, so gradients, transfer function and compositing stay FP32,
+ * and ray/leaf entry and exit stay FP64-exact.  The paper stores FP32 cells; the 16-bit
+ * forms trade accuracy for bandwidth on its bandwidth-bound march (Sec. 5). */
 typedef enum { AMR_F32 = 0, AMR_F16 = 1, AMR_BF16 = 2 } amr_dtype;
 
 /* Brick storage strategies (Sec. 4).  The paper's GL designs are a packed memory-pool
@@ -93,7 +98,7 @@ typedef struct {
                          compacted opaque samples; pays off when rays diverge, e.g. small
                          views of a large volume) */
   int32_t learned;    /* learned segment proposal (needs amr_set_proposal; trilinear; ptr or
-                         atlas_linear storage): 0 off; 1 skip segments whose predicted
+                         atlas_linear storage, FP32 cells): 0 off; 1 skip segments whose predicted
                          contribution is below tau; 2 sample them with a 4x coarser step */
   double tau;         /* proposal threshold (default 1e-3) */
 } amr_render_params;
@@ -108,7 +113,7 @@ void amr_default_params(amr_render_params* p);
  *   domain_lo[3]  world position of level-0 cell index 0;  h0[3] level-0 spacing
  *   num_patches   P >= 1;  patch_level[P] in [0, L);  patch_box[6P] as above
  *   cell_data[P]  host pointers, float32, x fastest; copied (the caller keeps ownership)
- *   dtype         device storage type of the bricks (AMR_F32; F16/BF16 halve the bytes)
+ *   dtype         device storage type of the brick cells (amr_dtype; input is always FP32)
  * Returns AMR_ERR_ARG for malformed input; tiling and overlaps are checked at build. */
 amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double domain_lo[3],
                       const double h0[3], int32_t num_patches, const int32_t* patch_level,
@@ -119,7 +124,12 @@ amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double dom
  * refinement), the per-patch bricks with a one-cell halo (Sec. 4: one brick per subgrid),
  * the chosen storage (Sec. 4.1 packing / 4.2 handle table) and upload everything on
  * `cuda_stream`.  `storage` is an amr_storage strategy, optionally OR AMR_STORE_GRADIENT.
- * The call returns after the uploads complete. */
+ * The call returns after the uploads complete.  With AMR_F16 / AMR_BF16 cells: only
+ * AMR_STORE_PTR and AMR_STORE_ATLAS_LINEAR (else AMR_ERR_ARG); gradient bricks hold the
+ * value and the FP32 central differences, each rounded to the 16-bit type; AMR_F16 returns
+ * AMR_ERR_ARG if a finite cell value (or, with gradient bricks, a central difference)
+ * would round to infinity (|x| >= 65520).  Device leaf min/max ranges are those of the
+ * rounded cells, so exact skipping stays exact. */
 amr_status amr_build_kdtree(amr_ctx* ctx, amr_storage storage, void* cuda_stream);
 
 /* Host-only part of amr_build_kdtree (tree, bricks, packing), for inspecting the tree
@@ -131,7 +141,8 @@ amr_status amr_build_host(amr_ctx* ctx, amr_storage storage);
  * tf_rgba_dev: device float32 [tf_n][4] (2 <= tf_n <= 2048), linear between entries over
  * [vmin, vmax].  Both device buffers must be 16-byte aligned.  Asynchronous on cuda_stream.  samples_out (nullable, host): when given,
  * the call synchronises the stream, checks the device status word and stores the exact
- * number of samples taken (sum over segments of the per-segment sample count). */
+ * number of samples taken (sum over segments of the per-segment sample count).
+ * 16-bit cells render trilinear with the per-ray schedule (else AMR_ERR_ARG). */
 amr_status amr_render(amr_ctx* ctx, const amr_camera* cam, const float* tf_rgba_dev,
                       int32_t tf_n, const amr_render_params* params, float* out_rgba_dev,
                       void* cuda_stream, uint64_t* samples_out);
@@ -177,7 +188,8 @@ amr_status amr_render_host_noalloc(amr_ctx* ctx, const amr_camera* cam,
  * segment a seeded hash keeps with probability keep_prob, its 12 features to
  * features_dev[k*12 ..] and its contribution A_out - A_in to targets_dev[k], where
  * k = atomicAdd(count_dev, 1) (caller zeroes *count_dev; records with k >= capacity are
- * dropped but still counted).  Storage must be ptr or atlas_linear.  Asynchronous. */
+ * dropped but still counted).  Storage must be ptr or atlas_linear with FP32 cells.
+ * Asynchronous. */
 amr_status amr_log_segments(amr_ctx* ctx, const amr_camera* cam, const float* tf_rgba_dev,
                             int32_t tf_n, const amr_render_params* params, float* features_dev,
                             float* targets_dev, int64_t capacity, unsigned long long* count_dev,
@@ -252,7 +264,8 @@ amr_status amr_get_nodes(const amr_ctx* ctx, int32_t* axis, int32_t* split, int3
                          int32_t* right, int32_t* leaf, int64_t cap, int64_t* n);
 
 /* The host brick of patch p with its one-cell halo: float32 [(nz+2)][(ny+2)][(nx+2)],
- * brick index b = level cell c - lo + 1.  cap in floats; *n receives the brick size. */
+ * brick index b = level cell c - lo + 1.  cap in floats; *n receives the brick size.
+ * With 16-bit cells the values are the rounded ones the device holds. */
 amr_status amr_get_brick(const amr_ctx* ctx, int32_t patch, float* out, int64_t cap,
                          int64_t* n);
 

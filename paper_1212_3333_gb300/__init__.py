@@ -13,9 +13,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import (AMR_STORE_ATLAS_LINEAR, AMR_STORE_ATLAS_TEX3D, AMR_STORE_GRADIENT,  # noqa: F401
-                   AMR_STORE_PTR, AMR_STORE_TEXOBJ, STORAGES, amr_camera, amr_render_params,
-                   amr_stats)
+from ._lib import (AMR_BF16, AMR_F16, AMR_F32, AMR_STORE_ATLAS_LINEAR,  # noqa: F401
+                   AMR_STORE_ATLAS_TEX3D, AMR_STORE_GRADIENT, AMR_STORE_PTR, AMR_STORE_TEXOBJ,
+                   DTYPES, STORAGES, amr_camera, amr_render_params, amr_stats)
 
 
 class AmrError(RuntimeError):
@@ -171,8 +171,10 @@ class AmrContext:
 
 
 def amr_create(num_levels: int, refine_ratio: int, domain_lo: Sequence[float],
-               h0: Sequence[float], patch_level, patch_box, cell_data, dtype: int = 0) -> AmrContext:
+               h0: Sequence[float], patch_level, patch_box, cell_data, dtype=AMR_F32) -> AmrContext:
+    """dtype: device cell type, an amr_dtype code or "f32" / "f16" / "bf16"."""
     lib = _lib.load()
+    dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
     lvl = np.ascontiguousarray(patch_level, dtype=np.int32)
     box = np.ascontiguousarray(patch_box, dtype=np.int64).reshape(-1, 6)
     data = [np.ascontiguousarray(d, dtype=np.float32) for d in cell_data]
@@ -188,7 +190,7 @@ def amr_create(num_levels: int, refine_ratio: int, domain_lo: Sequence[float],
     return AmrContext(h.value)
 
 
-def from_hierarchy(hier, dtype: int = 0) -> AmrContext:
+def from_hierarchy(hier, dtype=AMR_F32) -> AmrContext:
     """amr_create from an object with num_levels, ratio, domain_lo, h0, patch_level,
     patch_box and data (list of float32 [nz, ny, nx] arrays)."""
     return amr_create(hier.num_levels, hier.ratio, hier.domain_lo, hier.h0, hier.patch_level,

@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "AMR_OK", 1: "AMR_ERR_ARG", 2: "AMR_ERR_OVERLAP", 3: "AMR_ERR
                 8: "AMR_ERR_DEVICE"}
 
 AMR_F32, AMR_F16, AMR_BF16 = 0, 1, 2
+DTYPES = {"f32": AMR_F32, "f16": AMR_F16, "bf16": AMR_BF16}
 AMR_STORE_PTR, AMR_STORE_TEXOBJ, AMR_STORE_ATLAS_LINEAR, AMR_STORE_ATLAS_TEX3D = 0, 1, 2, 3
 AMR_STORE_GRADIENT = 0x100
 AMR_MLP_FEATURES, AMR_MLP_PARAMS, AMR_MLP_PACKED_BYTES = 12, 9217, 23440

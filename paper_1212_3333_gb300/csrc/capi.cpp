@@ -7,6 +7,7 @@
 #include <new>
 
 #include "ctx.h"
+#include "storage16.h"
 
 using namespace amr;
 
@@ -122,7 +123,7 @@ amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double dom
   if (refine_ratio < 2 || refine_ratio > 64) return bad("refine_ratio out of range");
   if (!domain_lo || !h0 || !patch_level || !patch_box || !cell_data) return bad("NULL array");
   if (num_patches < 1) return bad("num_patches must be positive");
-  if (dtype != AMR_F32) return bad("only AMR_F32 storage is available");
+  if (dtype != AMR_F32 && dtype != AMR_F16 && dtype != AMR_BF16) return bad("unknown dtype");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(domain_lo[a]) || !std::isfinite(h0[a]) || !(h0[a] > 0.0))
       return bad("domain_lo / h0 must be finite, h0 positive");
@@ -199,6 +200,8 @@ amr_status amr_build_host(amr_ctx* c, amr_storage storage_flags) {
   if (storage < AMR_STORE_PTR || storage > AMR_STORE_ATLAS_TEX3D ||
       ((int)storage_flags & ~(0xff | AMR_STORE_GRADIENT)))
     return fail(c, AMR_ERR_ARG, "unknown storage");
+  if (c->dtype != AMR_F32 && storage != AMR_STORE_PTR && storage != AMR_STORE_ATLAS_LINEAR)
+    return fail(c, AMR_ERR_ARG, "16-bit cells need the ptr or atlas_linear storage");
   auto t0 = std::chrono::steady_clock::now();
   try {
     if (!c->host_built) {
@@ -218,6 +221,18 @@ amr_status amr_build_host(amr_ctx* c, amr_storage storage_flags) {
     if (gradient && c->gbricks.empty()) {
       amr_status s = build_gradient_bricks(c);
       if (s != AMR_OK) return s;
+    }
+    if (c->dtype == AMR_F16) {
+      // binary16 tops out at 65504: refuse data that would be stored as infinity
+      auto over = [](float v) { return std::isfinite(v) && std::isinf(storage_round(AMR_F16, v)); };
+      for (const auto& b : c->bricks)
+        for (float v : b)
+          if (over(v)) return fail(c, AMR_ERR_ARG, "a cell value exceeds the FP16 range");
+      if (gradient)
+        for (const auto& g : c->gbricks)
+          for (const float4& q : g)
+            if (over(q.y) || over(q.z) || over(q.w))
+              return fail(c, AMR_ERR_ARG, "a central difference exceeds the FP16 range");
     }
   } catch (const std::bad_alloc&) {
     return fail(c, AMR_ERR_OOM, "out of host memory during the build");
@@ -289,13 +304,22 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->tau = (float)p->tau;
   a->learned = p->learned;
   a->inv_levels = c->L > 1 ? 1.0f / (float)(c->L - 1) : 0.0f;
+  if (c->dtype != AMR_F32 && (p->interp != AMR_INTERP_TRILINEAR || p->schedule != 0))
+    return fail(c, AMR_ERR_ARG, "16-bit cells render trilinear with the per-ray schedule");
   if (p->learned != 0) {
     if (p->learned != 1 && p->learned != 2) return fail(c, AMR_ERR_ARG, "unknown learned mode");
+    if (c->dtype != AMR_F32) return fail(c, AMR_ERR_ARG, "the learned proposal needs FP32 cells");
     if (!c->dev.proposal) return fail(c, AMR_ERR_STATE, "learned render before amr_set_proposal");
     if (p->interp != AMR_INTERP_TRILINEAR)
       return fail(c, AMR_ERR_ARG, "the learned proposal renders with trilinear sampling");
   }
   return AMR_OK;
+}
+
+// kernel storage id: the strategy, or its 16-bit-cell variant (ids 4..7)
+static int kernel_storage(const amr_ctx* c) {
+  if (c->dtype == AMR_F32) return c->storage;
+  return c->storage + (c->dtype == AMR_F16 ? 4 : 5);
 }
 
 // shading variant: 2 = Phong reading the gradient bricks (trilinear only), when built
@@ -328,7 +352,7 @@ amr_status prepare_render_args(amr_ctx* c, const amr_camera* cam, int32_t tf_n,
 amr_status launch_render_args(amr_ctx* c, const RenderArgs& a, const amr_render_params* p,
                               void* stream) {
   if (p->learned) return launch_learned(c, a, c->storage, kernel_shade(c, p), stream);
-  return launch_render(c, a, c->storage, p->interp, kernel_shade(c, p), p->schedule, stream);
+  return launch_render(c, a, kernel_storage(c), p->interp, kernel_shade(c, p), p->schedule, stream);
 }
 }  // namespace amr
 
@@ -405,6 +429,7 @@ amr_status amr_log_segments(amr_ctx* c, const amr_camera* cam, const float* tf_r
                             float* targets_dev, int64_t capacity, unsigned long long* count_dev,
                             float keep_prob, uint32_t seed, void* cuda_stream) {
   if (!params) return fail(c, AMR_ERR_ARG, "params is NULL");
+  if (c && c->dtype != AMR_F32) return fail(c, AMR_ERR_ARG, "segment logging needs FP32 cells");
   amr_render_params p = *params;
   p.ert_eps = 0.0;  // log every segment of the ray
   p.learned = 0;
@@ -502,7 +527,7 @@ amr_status amr_get_brick(const amr_ctx* c, int32_t patch, float* out, int64_t ca
   *n = (int64_t)b.size();
   if (cap < *n) return AMR_ERR_CAPACITY;
   if (!out) return AMR_ERR_ARG;
-  std::memcpy(out, b.data(), sizeof(float) * b.size());
+  for (size_t i = 0; i < b.size(); ++i) out[i] = storage_round(c->dtype, b[i]);
   return AMR_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <deque>
 
 #include "ctx.h"
+#include "storage16.h"
 
 namespace amr {
 
@@ -209,8 +210,10 @@ amr_status upload(amr_ctx* c, void* stream_v) {
     for (int k = 0; k < 6; ++k) (k < 3 ? l.lo[k] : l.hi[k - 3]) = t.leaf_box[6 * m + k];
     l.patch = t.leaf_patch[m];
     l.level = t.leaf_level[m];
-    l.vmin = c->leaf_vmin[m];
-    l.vmax = c->leaf_vmax[m];
+    // the range of the cells as stored; rounding is monotone, so the rounded extremes
+    // bound every rounded cell and empty-space skipping stays exact
+    l.vmin = storage_round(c->dtype, c->leaf_vmin[m]);
+    l.vmax = storage_round(c->dtype, c->leaf_vmax[m]);
   }
   std::vector<DPatch> pt(P);
   for (size_t p = 0; p < P; ++p) {
@@ -226,11 +229,38 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   CK(cudaMalloc(&d.counters, kNumCounters * sizeof(unsigned long long)));
   CK(cudaMemsetAsync(d.counters, 0, kNumCounters * sizeof(unsigned long long), stream));
 
-  amr_status st = upload_bricks<float>(c, c->bricks, pt, false, stream);
-  if (st != AMR_OK) return st;
-  if (c->want_gradient) {
-    st = upload_bricks<float4>(c, c->gbricks, pt, true, stream);
+  amr_status st;
+  if (c->dtype == AMR_F32) {
+    st = upload_bricks<float>(c, c->bricks, pt, false, stream);
     if (st != AMR_OK) return st;
+    if (c->want_gradient) {
+      st = upload_bricks<float4>(c, c->gbricks, pt, true, stream);
+      if (st != AMR_OK) return st;
+    }
+  } else {
+    // 16-bit cells (and 4 x 16-bit value + central differences)
+    {
+      std::vector<std::vector<uint16_t>> b16(P);
+      for (size_t p = 0; p < P; ++p) {
+        const std::vector<float>& b = c->bricks[p];
+        b16[p].resize(b.size());
+        for (size_t i = 0; i < b.size(); ++i) b16[p][i] = storage_bits(c->dtype, b[i]);
+      }
+      st = upload_bricks<uint16_t>(c, b16, pt, false, stream);
+      if (st != AMR_OK) return st;
+    }
+    if (c->want_gradient) {
+      std::vector<std::vector<ushort4>> g16(P);
+      for (size_t p = 0; p < P; ++p) {
+        const std::vector<float4>& g = c->gbricks[p];
+        g16[p].resize(g.size());
+        for (size_t i = 0; i < g.size(); ++i)
+          g16[p][i] = make_ushort4(storage_bits(c->dtype, g[i].x), storage_bits(c->dtype, g[i].y),
+                                   storage_bits(c->dtype, g[i].z), storage_bits(c->dtype, g[i].w));
+      }
+      st = upload_bricks<ushort4>(c, g16, pt, true, stream);
+      if (st != AMR_OK) return st;
+    }
   }
   CK(cudaMemcpyAsync(d.nodes, nodes.data(), nodes.size() * sizeof(DNode), cudaMemcpyHostToDevice,
                      stream));

@@ -19,6 +19,8 @@
 //
 // Every device loop is bounded; exceeding a bound sets a status bit, never traps.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,7 +28,11 @@
 
 namespace amr {
 
-enum { ST_PTR = 0, ST_TEXOBJ = 1, ST_ATLAS_LINEAR = 2, ST_ATLAS_TEX3D = 3 };
+// storage strategies; ids 4..7 are the 16-bit-cell variants of the two linear storages
+enum {
+  ST_PTR = 0, ST_TEXOBJ = 1, ST_ATLAS_LINEAR = 2, ST_ATLAS_TEX3D = 3,
+  ST_PTR_F16 = 4, ST_PTR_BF16 = 5, ST_ATLAS_LINEAR_F16 = 6, ST_ATLAS_LINEAR_BF16 = 7
+};
 
 // plane ids: split * 4 + axis; the two ray ends use axis field 3
 constexpr int kPidIn = 3;
@@ -314,6 +320,14 @@ __device__ __forceinline__ float fetch(const RenderArgs& A, const BrickRef& b, l
     return __ldg(reinterpret_cast<const float*>(b.base) + lin);
   } else if constexpr (ST == ST_ATLAS_LINEAR) {
     return __ldg(reinterpret_cast<const float*>(A.pool) + b.base + lin);
+  } else if constexpr (ST == ST_PTR_F16) {
+    return __half2float(__ldg(reinterpret_cast<const __half*>(b.base) + lin));
+  } else if constexpr (ST == ST_PTR_BF16) {
+    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(b.base) + lin));
+  } else if constexpr (ST == ST_ATLAS_LINEAR_F16) {
+    return __half2float(__ldg(reinterpret_cast<const __half*>(A.pool) + b.base + lin));
+  } else if constexpr (ST == ST_ATLAS_LINEAR_BF16) {
+    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(A.pool) + b.base + lin));
   } else if constexpr (ST == ST_TEXOBJ) {
     return tex3D<float>((cudaTextureObject_t)b.base, (float)i + 0.5f, (float)j + 0.5f,
                         (float)k + 0.5f);
@@ -324,6 +338,17 @@ __device__ __forceinline__ float fetch(const RenderArgs& A, const BrickRef& b, l
 }
 
 // Gradient-brick cell: (V, V(c+x) - V(c-x), V(c+y) - V(c-y), V(c+z) - V(c-z)).
+__device__ __forceinline__ float4 unpack_half4(uint2 u) {
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 unpack_bf164(uint2 u) {
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
 template <int ST>
 __device__ __forceinline__ float4 fetch4(const RenderArgs& A, const BrickRef& b, long long lin,
                                          int i, int j, int k) {
@@ -331,6 +356,14 @@ __device__ __forceinline__ float4 fetch4(const RenderArgs& A, const BrickRef& b,
     return __ldg(reinterpret_cast<const float4*>(b.gbase) + lin);
   } else if constexpr (ST == ST_ATLAS_LINEAR) {
     return __ldg(A.gpool + b.gbase + lin);
+  } else if constexpr (ST == ST_PTR_F16) {
+    return unpack_half4(__ldg(reinterpret_cast<const uint2*>(b.gbase) + lin));
+  } else if constexpr (ST == ST_PTR_BF16) {
+    return unpack_bf164(__ldg(reinterpret_cast<const uint2*>(b.gbase) + lin));
+  } else if constexpr (ST == ST_ATLAS_LINEAR_F16) {
+    return unpack_half4(__ldg(reinterpret_cast<const uint2*>(A.gpool) + b.gbase + lin));
+  } else if constexpr (ST == ST_ATLAS_LINEAR_BF16) {
+    return unpack_bf164(__ldg(reinterpret_cast<const uint2*>(A.gpool) + b.gbase + lin));
   } else if constexpr (ST == ST_TEXOBJ) {
     return tex3D<float4>((cudaTextureObject_t)b.gbase, (float)i + 0.5f, (float)j + 0.5f,
                          (float)k + 0.5f);

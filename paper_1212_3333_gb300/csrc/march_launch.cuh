@@ -26,7 +26,15 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
   const size_t tf_bytes = (size_t)a.tf_n * sizeof(float4) + (size_t)(a.tf_n + 1) * sizeof(int);
   if (grid.x == 0 || grid.y == 0) return AMR_OK;
   cudaError_t e;
-  if (schedule == 0) {
+  if constexpr (ST >= ST_PTR_F16) {
+    // 16-bit cells: trilinear, per-ray schedule
+    if (interp != 1 || schedule != 0)
+      return fail(c, AMR_ERR_ARG, "16-bit storage renders trilinear with the per-ray schedule");
+    const size_t smem = tf_bytes;
+    if (shade == 0) e = launch_one(march_kernel<ST, 1, 0>, grid, block, smem, s, a);
+    else if (shade == 1) e = launch_one(march_kernel<ST, 1, 1>, grid, block, smem, s, a);
+    else e = launch_one(march_kernel<ST, 1, 2>, grid, block, smem, s, a);
+  } else if (schedule == 0) {
     const size_t smem = tf_bytes;
     if (interp == 1 && shade == 0) e = launch_one(march_kernel<ST, 1, 0>, grid, block, smem, s, a);
     else if (interp == 1 && shade == 1) e = launch_one(march_kernel<ST, 1, 1>, grid, block, smem, s, a);
@@ -54,5 +62,7 @@ amr_status launch_atlas_linear(amr_ctx* c, const RenderArgs& a, int interp, int 
                                int schedule, cudaStream_t s);
 amr_status launch_atlas_tex3d(amr_ctx* c, const RenderArgs& a, int interp, int shade,
                               int schedule, cudaStream_t s);
+amr_status launch_16bit(amr_ctx* c, const RenderArgs& a, int storage, int interp, int shade,
+                        int schedule, cudaStream_t s);
 
 }  // namespace amr

@@ -67,6 +67,10 @@ amr_status launch_render(amr_ctx* c, const RenderArgs& a, int storage, int inter
     case ST_TEXOBJ: return launch_texobj(c, a, interp, shade, schedule, s);
     case ST_ATLAS_LINEAR: return launch_atlas_linear(c, a, interp, shade, schedule, s);
     case ST_ATLAS_TEX3D: return launch_atlas_tex3d(c, a, interp, shade, schedule, s);
+    case ST_PTR_F16:
+    case ST_PTR_BF16:
+    case ST_ATLAS_LINEAR_F16:
+    case ST_ATLAS_LINEAR_BF16: return launch_16bit(c, a, storage, interp, shade, schedule, s);
     default: return fail(c, AMR_ERR_ARG, "unknown storage");
   }
 }
