@@ -132,31 +132,21 @@ def _dist():
 
 def _barrier(world):
     if world > 1:
-        import torch.distributed as dist
+        from paper_1212_3333_gb300 import shard
 
-        dist.barrier()
+        shard.barrier()
 
 
 def _max_over_ranks(world, x: float) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
+    from paper_1212_3333_gb300 import shard
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return shard.all_max(x) if world > 1 else x
 
 
 def _sum_over_ranks(world, x: float) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
+    from paper_1212_3333_gb300 import shard
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return shard.all_sum(x) if world > 1 else x
 
 
 def cpu_baseline(hier, cam, tf, vmin, vmax, shade, budget_s=15.0, seed=0):
