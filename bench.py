@@ -287,6 +287,67 @@ def precision_eval(amr, hier, vmin, vmax, cam, tf, out, args, peak):
     return res
 
 
+def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5):
+    """Batched multi-view rendering: 64 seeded views with square sides uniform in
+    256..2048 and four 256-entry transfer functions, rendered (a) as 64 separate
+    amr_render launches, (b) as one persistent amr_render_batch launch with the autotuned
+    tile configuration, (c) as that launch replayed from a CUDA graph."""
+    import torch
+    import synth
+
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(256, 2049, size=n_views)
+    cams = [synth.orbit_camera(5000 + v, int(sd), int(sd)) for v, sd in enumerate(sides)]
+    tfi = [v % 4 for v in range(n_views)]
+    tfs = torch.as_tensor(np.stack(synth.tf_variants()), device="cuda")
+    p = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
+    views, offsets, total = amr.make_views(cams, tfi)
+    out = torch.zeros((total,), dtype=torch.float32, device="cuda")
+    ref = torch.zeros_like(out)
+    stream = torch.cuda.current_stream()
+
+    def separate(dst):
+        for cam, t, off in zip(cams, tfi, offsets):
+            ctx.amr_render(cam, tfs[t], p, dst[off:off + 4 * cam.width * cam.height])
+
+    def timed(fn, reps=3):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms_sep = timed(lambda: separate(ref))
+    t0 = time.perf_counter()
+    best, table = ctx.amr_batch_autotune(views, tfs, p, out, reps=1)
+    tune_s = time.perf_counter() - t0
+    samples = ctx.amr_render_batch(views, tfs, p, out, count_samples=True)
+    same = bool(torch.equal(out, ref))
+    ms_batch = timed(lambda: ctx.amr_render_batch(views, tfs, p, out))
+    s = torch.cuda.Stream()
+    s.wait_stream(stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        ctx.amr_render_batch(views, tfs, p, out, stream=s)
+    ms_graph = timed(g.replay)
+    same = same and bool(torch.equal(out, ref))
+    names = [f"{tw}x{th}/r{r}" for tw, th in ((8, 8), (16, 8), (16, 16)) for r in (1, 2, 4)]
+    bps = BYTES_PER_SAMPLE[args.shade]
+    return {"views": n_views, "pixels": int(sum(int(sd) ** 2 for sd in sides)),
+            "samples": samples, "identical_to_separate": same,
+            "separate": {"ms": ms_sep, "gsamples_s": samples / ms_sep / 1e6},
+            "batched": {"ms": ms_batch, "gsamples_s": samples / ms_batch / 1e6},
+            "batched_graph": {"ms": ms_graph, "gsamples_s": samples / ms_graph / 1e6,
+                              "frac_hbm": samples * bps / (ms_graph * 1e-3) / 1e9 / peak},
+            "speedup_vs_separate": ms_sep / ms_graph,
+            "autotune": {"best": f"{best.tile_w}x{best.tile_h}/r{best.rays_per_thread}",
+                         "ms": dict(zip(names, table)), "seconds": tune_s}}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -348,6 +409,7 @@ def main():
                     help="brick cell storage type (interpolation and compositing stay FP32)")
     ap.add_argument("--learned", type=int, default=1, help="evaluate the learned proposal")
     ap.add_argument("--precision", type=int, default=1, help="time FP16 / BF16 cell storage")
+    ap.add_argument("--batch", type=int, default=1, help="time 64-view batched rendering")
     ap.add_argument("--log-size", type=int, default=96)
     ap.add_argument("--log-cap", type=int, default=10_000_000)
     ap.add_argument("--log-keep", type=float, default=0.3)
@@ -485,6 +547,8 @@ def main():
         extra["storages"] = comp
     if args.precision and world == 1:
         extra["precision"] = precision_eval(amr, hier, vmin, vmax, cam, tf, out, args, peak)
+    if args.batch and world == 1 and args.storage == "ptr" and args.dtype == "f32":
+        extra["batch"] = batch_eval(amr, ctx, vmin, vmax, args, peak)
     if args.learned and world == 1:
         extra["learned"] = learned_eval(amr, ctx, hier, vmin, vmax, tf, args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

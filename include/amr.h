@@ -173,6 +173,62 @@ amr_status amr_render_host_noalloc(amr_ctx* ctx, const amr_camera* cam,
                                    void* cuda_stream, uint64_t* samples_out);
 
 /* ---------------------------------------------------------------------------------- */
+/* batched multi-view rendering (not in the paper, which renders one view per pass)      */
+/* ---------------------------------------------------------------------------------- */
+
+#define AMR_MAX_BATCH_VIEWS 128
+#define AMR_BATCH_CANDIDATES 9   /* tiles 8x8, 16x8, 16x16  x  rays per thread 1, 2, 4 */
+
+/* One view of a batch: its camera, which transfer function it uses, and where its image
+ * starts in the shared output buffer (in floats; a multiple of 4). */
+typedef struct {
+  amr_camera cam;
+  int32_t tf_index;
+  int32_t reserved;
+  int64_t out_offset;
+} amr_view;
+
+/* Work decomposition of a batched render: pixel tiles of tile_w x tile_h threads (8x8,
+ * 16x8 or 16x16), each thread marching rays_per_thread (1..8) pixels of a column of its
+ * tile, so a queue item covers tile_w x (tile_h * rays_per_thread) pixels; blocks_per_sm
+ * caps the persistent grid per SM (0: as many as fit). */
+typedef struct {
+  int32_t tile_w, tile_h, rays_per_thread, blocks_per_sm;
+} amr_batch_config;
+
+/* Render n_views (1..AMR_MAX_BATCH_VIEWS) views of the context's dataset in one persistent
+ * launch: the pixel tiles of all views form one work queue that resident blocks drain.
+ * Every view's image equals, bit for bit, amr_render of that view alone with the same
+ * params and its transfer function.
+ *   views          host array [n_views]; whole images (params->row0 = 0, rows <= 0)
+ *   tfs_rgba_dev   device float32 [n_tf][tf_n][4], 1 <= n_tf <= 8, n_tf * tf_n <= 2048
+ *   out_rgba_dev   device float32 [out_floats]; view v writes [H][W][4] at out_offset;
+ *                  images must not overlap; buffers 16-byte aligned
+ *   config         NULL: the context's last autotuned configuration (initially 16x8, 1)
+ * Needs the ptr storage with FP32 cells, trilinear sampling, the per-ray schedule and no
+ * learned proposal (else AMR_ERR_ARG).  Issues one cudaMemsetAsync and one kernel launch
+ * on cuda_stream and allocates nothing, so with samples_out NULL the call can be captured
+ * in a CUDA graph; samples_out (nullable, host) synchronises and returns the total sample
+ * count of all views (plus the device status check, as amr_render). */
+amr_status amr_render_batch(amr_ctx* ctx, const amr_view* views, int32_t n_views,
+                            const float* tfs_rgba_dev, int32_t n_tf, int32_t tf_n,
+                            const amr_render_params* params, float* out_rgba_dev,
+                            int64_t out_floats, const amr_batch_config* config,
+                            void* cuda_stream, uint64_t* samples_out);
+
+/* Time every candidate configuration (tile 8x8 / 16x8 / 16x16 x rays per thread 1 / 2 / 4,
+ * blocks_per_sm 0) on this batch: one warm-up and `reps` (1..1000) timed renders each,
+ * CUDA events on cuda_stream.  ms_out (nullable) receives the mean milliseconds of the
+ * AMR_BATCH_CANDIDATES candidates in that order (tile-major); best_out (nullable) the
+ * fastest, which the context also keeps for amr_render_batch calls without a config.
+ * Synchronises; arguments as amr_render_batch. */
+amr_status amr_batch_autotune(amr_ctx* ctx, const amr_view* views, int32_t n_views,
+                              const float* tfs_rgba_dev, int32_t n_tf, int32_t tf_n,
+                              const amr_render_params* params, float* out_rgba_dev,
+                              int64_t out_floats, int32_t reps, void* cuda_stream,
+                              amr_batch_config* best_out, float* ms_out);
+
+/* ---------------------------------------------------------------------------------- */
 /* learned segment proposal (not in the paper): a 12-64-64-64-1 MLP, ReLU hidden layers,  */
 /* sigmoid output, predicting a segment's opacity contribution A_out - A_in from 12       */
 /* features: entry xyz, exit xyz (root-box units), level / (L-1), leaf value min and max  */

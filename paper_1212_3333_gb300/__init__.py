@@ -125,6 +125,29 @@ class AmrContext:
                                          C.byref(smp) if count_samples else None), self._h)
         return int(smp.value) if count_samples else None
 
+    def amr_render_batch(self, views, tfs, params: amr_render_params, out, config=None,
+                         stream=None, count_samples: bool = False) -> Optional[int]:
+        """views: from make_views; tfs: CUDA float32 [n_tf, tf_n, 4]; out: CUDA float32 buffer
+        of at least the views' total size; config: amr_batch_config or None (autotuned)."""
+        smp = C.c_uint64(0)
+        _check(self._lib.amr_render_batch(
+            self._h, views, len(views), C.c_void_p(_dptr(tfs)), int(tfs.shape[0]),
+            int(tfs.shape[1]), C.byref(params), C.c_void_p(_dptr(out)), int(out.numel()),
+            C.byref(config) if config is not None else None, C.c_void_p(_stream_ptr(stream)),
+            C.byref(smp) if count_samples else None), self._h)
+        return int(smp.value) if count_samples else None
+
+    def amr_batch_autotune(self, views, tfs, params: amr_render_params, out, reps: int = 3,
+                           stream=None):
+        """Returns (best amr_batch_config, mean ms of every candidate)."""
+        best = _lib.amr_batch_config()
+        ms = (C.c_float * _lib.AMR_BATCH_CANDIDATES)()
+        _check(self._lib.amr_batch_autotune(
+            self._h, views, len(views), C.c_void_p(_dptr(tfs)), int(tfs.shape[0]),
+            int(tfs.shape[1]), C.byref(params), C.c_void_p(_dptr(out)), int(out.numel()),
+            int(reps), C.c_void_p(_stream_ptr(stream)), C.byref(best), ms), self._h)
+        return best, list(ms)
+
     def amr_trace(self, camera, leaf_seq, seq_len, max_len: int, t_seq=None, stream=None) -> None:
         cam = camera if isinstance(camera, amr_camera) else make_camera(camera)
         _check(self._lib.amr_trace(self._h, C.byref(cam), C.c_void_p(_dptr(leaf_seq)),
@@ -188,6 +211,27 @@ def amr_create(num_levels: int, refine_ratio: int, domain_lo: Sequence[float],
                         box.ctypes.data_as(C.POINTER(C.c_int64)), ptrs, int(dtype), C.byref(h))
     _check(st, None)
     return AmrContext(h.value)
+
+
+def make_views(cameras, tf_index):
+    """Batch view table with the images packed back to back in camera order:
+    returns (amr_view array, per-view float offsets, total floats)."""
+    n = len(cameras)
+    views = (_lib.amr_view * n)()
+    offsets = []
+    off = 0
+    for v, (cam, t) in enumerate(zip(cameras, tf_index)):
+        views[v].cam = cam if isinstance(cam, amr_camera) else make_camera(cam)
+        views[v].tf_index = int(t)
+        views[v].out_offset = off
+        offsets.append(off)
+        off += 4 * views[v].cam.width * views[v].cam.height
+    return views, offsets, off
+
+
+def batch_config(tile_w: int = 16, tile_h: int = 8, rays_per_thread: int = 1,
+                 blocks_per_sm: int = 0):
+    return _lib.amr_batch_config(tile_w, tile_h, rays_per_thread, blocks_per_sm)
 
 
 def from_hierarchy(hier, dtype=AMR_F32) -> AmrContext:

@@ -53,6 +53,20 @@ class amr_stats(C.Structure):
                 ("exact_paths", C.c_int64 * 3)]
 
 
+AMR_MAX_BATCH_VIEWS = 128
+AMR_BATCH_CANDIDATES = 9
+
+
+class amr_view(C.Structure):
+    _fields_ = [("cam", amr_camera), ("tf_index", C.c_int32), ("reserved", C.c_int32),
+                ("out_offset", C.c_int64)]
+
+
+class amr_batch_config(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("rays_per_thread", C.c_int32),
+                ("blocks_per_sm", C.c_int32)]
+
+
 # every symbol include/amr.h declares, with its ctypes signature
 _P = C.c_void_p
 _SIGS = {
@@ -69,6 +83,13 @@ _SIGS = {
     "amr_render_host_noalloc": (C.c_int, [_P, C.POINTER(amr_camera), _P, C.c_int32,
                                           C.POINTER(amr_render_params), _P, _P,
                                           C.POINTER(C.c_uint64)]),
+    "amr_render_batch": (C.c_int, [_P, C.POINTER(amr_view), C.c_int32, _P, C.c_int32, C.c_int32,
+                                   C.POINTER(amr_render_params), _P, C.c_int64,
+                                   C.POINTER(amr_batch_config), _P, C.POINTER(C.c_uint64)]),
+    "amr_batch_autotune": (C.c_int, [_P, C.POINTER(amr_view), C.c_int32, _P, C.c_int32,
+                                     C.c_int32, C.POINTER(amr_render_params), _P, C.c_int64,
+                                     C.c_int32, _P, C.POINTER(amr_batch_config),
+                                     C.POINTER(C.c_float)]),
     "amr_log_segments": (C.c_int, [_P, C.POINTER(amr_camera), _P, C.c_int32,
                                    C.POINTER(amr_render_params), _P, _P, C.c_int64, _P, C.c_float,
                                    C.c_uint32, _P]),

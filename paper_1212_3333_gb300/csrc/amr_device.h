@@ -25,6 +25,8 @@ constexpr int kMaxSamplesPerSegment = 1 << 22;
 // device counters: [0] samples, [1] status bits, [2] exact descent decisions,
 // [3] exact sample counts, [4] exact neighbour / nearest positions
 constexpr int kNumCounters = 8;
+constexpr int kQueueCounter = 5;       // counters[5]: head of the batched work queue
+constexpr int kMaxBatchViews = 128;
 // status bits raised by kernels (OR-ed into counters[1])
 constexpr unsigned long long kStatusCapacity = 1ull;   // segment or sample bound hit
 constexpr unsigned long long kStatusDevice = 2ull;     // malformed tree reached
@@ -109,6 +111,24 @@ struct TraceArgs {
   int32_t max_len;
   int32_t max_segments;
   unsigned long long* counters;
+};
+
+// One view of a batched render (kept compact: the batch travels in the parameter block).
+struct BatchView {
+  double eye[3], fwd[3], right[3], up[3];
+  double tan_half_fov_y;
+  int32_t width, height;
+  int32_t item0;    // first work item (pixel tile) of the view in the batch queue
+  int32_t tiles_x;  // tiles per row of the view
+  int32_t tf;       // transfer-function index
+  int32_t pad;
+  long long out;    // float4 offset of the view's [H][W] image in the output buffer
+};
+
+struct BatchArgs {
+  RenderArgs A;     // shared state; A.tf = n_tf tables of A.tf_n entries, A.ray = domain part
+  int32_t n_views, n_items, n_tf, rays_per_thread;
+  BatchView v[kMaxBatchViews];
 };
 
 }  // namespace amr

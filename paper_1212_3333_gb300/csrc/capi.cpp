@@ -4,12 +4,16 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
+#include <utility>
 
 #include "ctx.h"
 #include "storage16.h"
 
 using namespace amr;
+
+static_assert(kMaxBatchViews == AMR_MAX_BATCH_VIEWS, "batch view bound");
 
 namespace {
 
@@ -411,6 +415,158 @@ amr_status amr_render_host(amr_ctx* c, const amr_camera* cam, const float* tf_rg
   if (samples_out) return finish_render(c, st, samples_out);
   CK(cudaStreamSynchronize(st));
   return AMR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Kernel arguments of one batched render: the shared render state from the first view,
+// then the view table (tiles in view order) and its checks.
+amr_status prepare_batch(amr_ctx* c, const amr_view* views, int32_t n_views, const float* tfs_dev,
+                         int32_t n_tf, int32_t tf_n, const amr_render_params* p, float* out_dev,
+                         int64_t out_floats, const amr_batch_config& cfg, BatchArgs* b) {
+  if (!c) return AMR_ERR_ARG;
+  if (!views || n_views < 1 || n_views > kMaxBatchViews)
+    return fail(c, AMR_ERR_ARG, "n_views must be in [1, AMR_MAX_BATCH_VIEWS]");
+  if (!p) return fail(c, AMR_ERR_ARG, "params is NULL");
+  if (n_tf < 1 || n_tf > 8 || (int64_t)n_tf * tf_n > 2048)
+    return fail(c, AMR_ERR_ARG, "need 1 <= n_tf <= 8 and n_tf * tf_n <= 2048");
+  if (p->row0 != 0 || p->rows > 0)
+    return fail(c, AMR_ERR_ARG, "batched views render whole images (row0 = 0, rows <= 0)");
+  if (p->interp != AMR_INTERP_TRILINEAR || p->schedule != 0 || p->learned != 0)
+    return fail(c, AMR_ERR_ARG, "batched rendering is trilinear, per-ray, without the proposal");
+  if (cfg.rays_per_thread < 1 || cfg.rays_per_thread > 8 || cfg.blocks_per_sm < 0)
+    return fail(c, AMR_ERR_ARG, "batch config: rays_per_thread in [1, 8], blocks_per_sm >= 0");
+  if (!((cfg.tile_w == 8 && cfg.tile_h == 8) || (cfg.tile_w == 16 && cfg.tile_h == 8) ||
+        (cfg.tile_w == 16 && cfg.tile_h == 16)))
+    return fail(c, AMR_ERR_ARG, "batch tile must be 8x8, 16x8 or 16x16");
+  amr_status s = prepare_render(c, &views[0].cam, tf_n, p, &b->A);
+  if (s != AMR_OK) return s;
+  if (kernel_storage(c) != AMR_STORE_PTR)
+    return fail(c, AMR_ERR_ARG, "batched rendering needs the ptr storage with FP32 cells");
+  if (!tfs_dev || !out_dev) return fail(c, AMR_ERR_ARG, "NULL device buffer");
+  if (((uintptr_t)tfs_dev | (uintptr_t)out_dev) & 15)
+    return fail(c, AMR_ERR_ARG, "device buffers must be 16-byte aligned");
+  std::vector<std::pair<int64_t, int64_t>> ranges;
+  int64_t items = 0;
+  const int64_t tile_rows = (int64_t)cfg.tile_h * cfg.rays_per_thread;
+  for (int v = 0; v < n_views; ++v) {
+    const amr_view& in = views[v];
+    s = check_camera(c, &in.cam);
+    if (s != AMR_OK) return s;
+    if (in.tf_index < 0 || in.tf_index >= n_tf) return fail(c, AMR_ERR_ARG, "tf_index out of range");
+    const int64_t n = 4 * (int64_t)in.cam.width * in.cam.height;
+    if (in.out_offset < 0 || (in.out_offset & 3) || in.out_offset + n > out_floats)
+      return fail(c, AMR_ERR_ARG, "view image outside the output buffer or not 16-byte aligned");
+    ranges.push_back({in.out_offset, in.out_offset + n});
+    BatchView& bv = b->v[v];
+    std::memset(&bv, 0, sizeof bv);
+    for (int a = 0; a < 3; ++a) {
+      bv.eye[a] = in.cam.eye[a];
+      bv.fwd[a] = in.cam.fwd[a];
+      bv.right[a] = in.cam.right[a];
+      bv.up[a] = in.cam.up[a];
+    }
+    bv.tan_half_fov_y = in.cam.tan_half_fov_y;
+    bv.width = in.cam.width;
+    bv.height = in.cam.height;
+    bv.tiles_x = (int32_t)((in.cam.width + cfg.tile_w - 1) / cfg.tile_w);
+    bv.item0 = (int32_t)items;
+    bv.tf = in.tf_index;
+    bv.out = in.out_offset / 4;
+    items += (int64_t)bv.tiles_x * ((in.cam.height + tile_rows - 1) / tile_rows);
+    if (items >= ((int64_t)1 << 31)) return fail(c, AMR_ERR_ARG, "too many pixel tiles");
+  }
+  std::sort(ranges.begin(), ranges.end());
+  for (size_t k = 1; k < ranges.size(); ++k)
+    if (ranges[k].first < ranges[k - 1].second)
+      return fail(c, AMR_ERR_ARG, "view images overlap in the output buffer");
+  b->n_views = n_views;
+  b->n_items = (int32_t)items;
+  b->n_tf = n_tf;
+  b->rays_per_thread = cfg.rays_per_thread;
+  b->A.tf = reinterpret_cast<const float4*>(tfs_dev);
+  b->A.out = reinterpret_cast<float4*>(out_dev);
+  return AMR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+amr_status amr_render_batch(amr_ctx* c, const amr_view* views, int32_t n_views,
+                            const float* tfs_rgba_dev, int32_t n_tf, int32_t tf_n,
+                            const amr_render_params* params, float* out_rgba_dev,
+                            int64_t out_floats, const amr_batch_config* config, void* cuda_stream,
+                            uint64_t* samples_out) {
+  if (!c) return AMR_ERR_ARG;
+  const amr_batch_config cfg = config ? *config : c->batch_cfg;
+  std::unique_ptr<BatchArgs> b(new (std::nothrow) BatchArgs());
+  if (!b) return fail(c, AMR_ERR_OOM, "out of host memory");
+  amr_status s = prepare_batch(c, views, n_views, tfs_rgba_dev, n_tf, tf_n, params, out_rgba_dev,
+                               out_floats, cfg, b.get());
+  if (s != AMR_OK) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(cudaMemsetAsync(c->dev.counters, 0, kNumCounters * sizeof(unsigned long long), st));
+  s = launch_batch(c, *b, kernel_storage(c), kernel_shade(c, params), cfg, cuda_stream);
+  if (s != AMR_OK) return s;
+  return finish_render(c, st, samples_out);
+}
+
+amr_status amr_batch_autotune(amr_ctx* c, const amr_view* views, int32_t n_views,
+                              const float* tfs_rgba_dev, int32_t n_tf, int32_t tf_n,
+                              const amr_render_params* params, float* out_rgba_dev,
+                              int64_t out_floats, int32_t reps, void* cuda_stream,
+                              amr_batch_config* best_out, float* ms_out) {
+  if (!c) return AMR_ERR_ARG;
+  if (reps < 1 || reps > 1000) return fail(c, AMR_ERR_ARG, "reps must be in [1, 1000]");
+  static const int shapes[3][2] = {{8, 8}, {16, 8}, {16, 16}};
+  static const int rpts[3] = {1, 2, 4};
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::unique_ptr<BatchArgs> b(new (std::nothrow) BatchArgs());
+  if (!b) return fail(c, AMR_ERR_OOM, "out of host memory");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto done = [&](amr_status r) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return r;
+  };
+  float best_ms = -1.0f;
+  amr_batch_config best = c->batch_cfg;
+  for (int k = 0; k < AMR_BATCH_CANDIDATES; ++k) {
+    amr_batch_config cfg = {shapes[k / 3][0], shapes[k / 3][1], rpts[k % 3], 0};
+    amr_status s = prepare_batch(c, views, n_views, tfs_rgba_dev, n_tf, tf_n, params,
+                                 out_rgba_dev, out_floats, cfg, b.get());
+    if (s != AMR_OK) return done(s);
+    const int shade = kernel_shade(c, params);
+    float ms = 0.0f;
+    for (int r = -1; r < reps; ++r) {  // one untimed warm-up
+      if (r == 0 && cudaEventRecord(e0, st) != cudaSuccess) return done(fail(c, AMR_ERR_CUDA, "event"));
+      if (cudaMemsetAsync(c->dev.counters, 0, kNumCounters * sizeof(unsigned long long), st) !=
+          cudaSuccess)
+        return done(fail(c, AMR_ERR_CUDA, "cudaMemsetAsync"));
+      s = launch_batch(c, *b, kernel_storage(c), shade, cfg, cuda_stream);
+      if (s != AMR_OK) return done(s);
+    }
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return done(fail(c, AMR_ERR_CUDA, "batch autotune timing failed"));
+    uint64_t n = 0;
+    s = finish_render(c, st, &n);  // surfaces device status of the last run
+    if (s != AMR_OK) return done(s);
+    ms /= (float)reps;
+    if (ms_out) ms_out[k] = ms;
+    if (best_ms < 0.0f || ms < best_ms) {
+      best_ms = ms;
+      best = cfg;
+    }
+  }
+  c->batch_cfg = best;
+  if (best_out) *best_out = best;
+  return done(AMR_OK);
 }
 
 amr_status amr_set_proposal(amr_ctx* c, const void* packed_dev, void* cuda_stream) {

@@ -79,6 +79,7 @@ struct amr_ctx {
   bool device_built = false;
   double build_seconds = 0.0;
   amr::DeviceState dev;
+  amr_batch_config batch_cfg = {16, 8, 1, 0};  // used when a batch call passes no config
   std::string err;
 };
 
@@ -99,6 +100,8 @@ amr_status launch_render(amr_ctx* c, const RenderArgs& a, int storage, int inter
                          int schedule, void* stream);
 amr_status launch_trace(amr_ctx* c, const TraceArgs& a, void* stream);
 amr_status launch_learned(amr_ctx* c, const RenderArgs& a, int storage, int shade, void* stream);
+amr_status launch_batch(amr_ctx* c, const BatchArgs& b, int storage, int shade,
+                        const amr_batch_config& cfg, void* stream);
 amr_status launch_log(amr_ctx* c, const RenderArgs& a, int storage, float* features,
                       float* targets, long long cap, unsigned long long* count, float keep_prob,
                       uint32_t seed, void* stream);

@@ -81,14 +81,14 @@ __global__ void __launch_bounds__(128) log_kernel(const __grid_constant__ Render
     if (lid < 0) break;
     const DLeaf lf = A.leaves[lid];
     const DLevel& lv = A.lv[lf.level];
-    int n = min(segment_count(A, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv),
+    int n = min(segment_count(A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv),
                 kMaxSamplesPerSegment);
     float f[kMlpIn];
     segment_features(A, rf, tau0, tau1, lf, Acc, f);
     const float a_in = Acc;
     SegSetup g;
     setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
-    sample_segment<ST, 1, 0>(A, s_tf, g, lv, 0.f, 0.f, 0.f, C0, C1, C2, Acc, nsamp);
+    sample_segment<ST, 1, 0>(A, A.ray, s_tf, g, lv, 0.f, 0.f, 0.f, C0, C1, C2, Acc, nsamp);
     const uint32_t h = mix32((uint32_t)i * 0x9E3779B1u ^ mix32((uint32_t)j + L.seed * 0x85EBCA77u) ^
                              ((uint32_t)seg * 0xC2B2AE3Du));
     if ((float)(h >> 8) * (1.0f / 16777216.0f) < L.keep_prob) {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
           live = false;
         } else {
           lf = A.leaves[lid];
-          n = segment_count(A, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, A.lv[lf.level]);
+          n = segment_count(A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, A.lv[lf.level]);
           if (n > kMaxSamplesPerSegment) {
             status |= kStatusCapacity;
             n = kMaxSamplesPerSegment;
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
       const DLevel& lv = A.lv[lf.level];
       SegSetup g;
       setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
-      if (sample_segment<ST, 1, SHADE>(A, s_tf, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
+      if (sample_segment<ST, 1, SHADE>(A, A.ray, s_tf, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
         live = false;  // early ray termination
     }
     if (lid >= 0) {

@@ -444,7 +444,8 @@ __device__ __forceinline__ int nearest_index_exact(const RayArgs& A, const DLeve
 // coordinates relative to the current leaf corner; a split within the error margin sends
 // the decision to FP64.  Takes scalars only, so the caller keeps its state in registers.
 template <int ST, int INTERP>
-__device__ __noinline__ float neighbour_slow(const RenderArgs& A, int px, int py, int leaf,
+__device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs& R, int px, int py,
+                                             int leaf,
                                              int pid0, int pid1, int n, int k, float margin,
                                              float bn0, float bn1, float bn2, int a, float sign) {
   const DLeaf cl = A.leaves[leaf];
@@ -478,7 +479,7 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, int px, int py
   }
   double xe[3] = {0.0, 0.0, 0.0};
   auto exact_point = [&]() {
-    const double3 x = sample_x_exact(A.ray, px, py, pid0, pid1, n, k);
+    const double3 x = sample_x_exact(R, px, py, pid0, pid1, n, k);
     xe[0] = x.x;
     xe[1] = x.y;
     xe[2] = x.z;
@@ -489,8 +490,8 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, int px, int py
   };
   if (amb) {
     exact_point();
-    lid = locate_cell(A.nodes, finest_cell_exact(A.ray, xe[0], 0), finest_cell_exact(A.ray, xe[1], 1),
-                      finest_cell_exact(A.ray, xe[2], 2));
+    lid = locate_cell(A.nodes, finest_cell_exact(R, xe[0], 0), finest_cell_exact(R, xe[1], 1),
+                      finest_cell_exact(R, xe[2], 2));
   }
   if (lid < 0) return 0.0f;
   const DLeaf lf = A.leaves[lid];
@@ -500,7 +501,7 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, int px, int py
   if (amb) {
 #pragma unroll
     for (int q = 0; q < 3; ++q)
-      bq[q] = (float)((xe[q] - A.ray.dlo[q]) * lw.inv_h[q] + (0.5 - (double)nb.lo[q]));
+      bq[q] = (float)((xe[q] - R.dlo[q]) * lw.inv_h[q] + (0.5 - (double)nb.lo[q]));
   } else {
 #pragma unroll
     for (int q = 0; q < 3; ++q)
@@ -517,30 +518,32 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, int px, int py
         return cell_at<ST>(A, nb, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
       exact_point();
     }
-    return cell_at<ST>(A, nb, nearest_index_exact(A.ray, lw, xe[0], 0, nb.lo[0]),
-                       nearest_index_exact(A.ray, lw, xe[1], 1, nb.lo[1]),
-                       nearest_index_exact(A.ray, lw, xe[2], 2, nb.lo[2]));
+    return cell_at<ST>(A, nb, nearest_index_exact(R, lw, xe[0], 0, nb.lo[0]),
+                       nearest_index_exact(R, lw, xe[1], 1, nb.lo[1]),
+                       nearest_index_exact(R, lw, xe[2], 2, nb.lo[2]));
   }
 }
 
 // Exact nearest-cell value of sample k in its own brick (rare path).
 template <int ST>
-__device__ __noinline__ float nearest_sample_exact(const RenderArgs& A, int px, int py, int leaf,
+__device__ __noinline__ float nearest_sample_exact(const RenderArgs& A, const RayArgs& R, int px,
+                                                   int py, int leaf,
                                                    int pid0, int pid1, int n, int k) {
   const DLeaf cl = A.leaves[leaf];
   const DLevel& lv = A.lv[cl.level];
   const BrickRef b = load_brick(A.patches, cl.patch);
-  const double3 x = sample_x_exact(A.ray, px, py, pid0, pid1, n, k);
-  return cell_at<ST>(A, b, nearest_index_exact(A.ray, lv, x.x, 0, b.lo[0]),
-                     nearest_index_exact(A.ray, lv, x.y, 1, b.lo[1]),
-                     nearest_index_exact(A.ray, lv, x.z, 2, b.lo[2]));
+  const double3 x = sample_x_exact(R, px, py, pid0, pid1, n, k);
+  return cell_at<ST>(A, b, nearest_index_exact(R, lv, x.x, 0, b.lo[0]),
+                     nearest_index_exact(R, lv, x.y, 1, b.lo[1]),
+                     nearest_index_exact(R, lv, x.z, 2, b.lo[2]));
 }
 
 // Value of the AMR field at the gradient neighbour x_k + SG h^l e_AX (Sec. 4: shading
 // reads across block boundaries).  Inside the current leaf (beyond the error margin) it is
 // the current brick; otherwise the slow path locates the finest leaf holding the point.
 template <int ST, int INTERP, int AX, int SG>
-__device__ __forceinline__ float neighbour_value(const RenderArgs& A, const SegState& s,
+__device__ __forceinline__ float neighbour_value(const RenderArgs& A, const RayArgs& R,
+                                                 const SegState& s,
                                                  const float* beta, int k) {
   float bn[3] = {beta[0], beta[1], beta[2]};
   bn[AX] += (float)SG;
@@ -558,13 +561,14 @@ __device__ __forceinline__ float neighbour_value(const RenderArgs& A, const SegS
         return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
     }
   }
-  return neighbour_slow<ST, INTERP>(A, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k, s.margin,
+  return neighbour_slow<ST, INTERP>(A, R, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k, s.margin,
                                     bn[0], bn[1], bn[2], AX, (float)SG);
 }
 
 // Value at the sample itself (the segment's own leaf and level, Sec. 3.3).
 template <int ST, int INTERP>
-__device__ __forceinline__ float sample_value(const RenderArgs& A, const SegState& s,
+__device__ __forceinline__ float sample_value(const RenderArgs& A, const RayArgs& R,
+                                              const SegState& s,
                                               const float* beta, int k) {
   if constexpr (INTERP == 1) {
     return trilinear<ST>(A, s.brick, beta[0], beta[1], beta[2]);
@@ -573,7 +577,7 @@ __device__ __forceinline__ float sample_value(const RenderArgs& A, const SegStat
     const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
     if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > s.margin)
       return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
-    return nearest_sample_exact<ST>(A, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k);
+    return nearest_sample_exact<ST>(A, R, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k);
   }
 }
 
@@ -600,7 +604,7 @@ __device__ __forceinline__ bool tf_transparent(const int* __restrict__ nz_prefix
 
 // Sample count of a segment: n = max(1, ceil(len / step)), len = (t1 - t0) |d|.
 // The FP32 estimate decides unless the quotient lies within its error bound of an integer.
-__device__ __forceinline__ int segment_count(const RenderArgs& A, int px, int py, const RayF& f,
+__device__ __forceinline__ int segment_count(const RayArgs& R, int px, int py, const RayF& f,
                                              int pid0, float tau0, float e0, int pid1, float tau1,
                                              float e1, const DLevel& lv) {
   const float inv_step = lv.inv_step;
@@ -611,7 +615,7 @@ __device__ __forceinline__ int segment_count(const RenderArgs& A, int px, int py
   if (q + eq <= 1.0f) return 1;
   const float c = ceilf(q);
   if (c - q > eq && q - (c - 1.0f) > eq && c <= (float)kMaxSamplesPerSegment) return (int)c;
-  return exact_count(A.ray, px, py, pid0, pid1, lv.step);
+  return exact_count(R, px, py, pid0, pid1, lv.step);
 }
 
 // Central-difference gradient g_a = (F(x + h e_a) - F(x - h e_a)) / 2h at sample beta.
@@ -620,7 +624,8 @@ __device__ __forceinline__ int segment_count(const RenderArgs& A, int px, int py
 // an axis are lerps of the two outer cell pairs, combined bilinearly in the other axes.
 // Otherwise each neighbour goes through neighbour_value (cross-leaf lookups).
 template <int ST, int INTERP, int GB>
-__device__ __forceinline__ void gradient(const RenderArgs& A, const SegState& s, const float* beta,
+__device__ __forceinline__ void gradient(const RenderArgs& A, const RayArgs& R, const SegState& s,
+                                         const float* beta,
                                          int k, const DLevel& lv, float* g) {
   if constexpr (INTERP == 1) {
     const float m = s.margin;
@@ -705,12 +710,12 @@ __device__ __forceinline__ void gradient(const RenderArgs& A, const SegState& s,
       return;
     }
   }
-  g[0] = (neighbour_value<ST, INTERP, 0, 1>(A, s, beta, k) -
-          neighbour_value<ST, INTERP, 0, -1>(A, s, beta, k)) * (0.5f * (float)lv.inv_h[0]);
-  g[1] = (neighbour_value<ST, INTERP, 1, 1>(A, s, beta, k) -
-          neighbour_value<ST, INTERP, 1, -1>(A, s, beta, k)) * (0.5f * (float)lv.inv_h[1]);
-  g[2] = (neighbour_value<ST, INTERP, 2, 1>(A, s, beta, k) -
-          neighbour_value<ST, INTERP, 2, -1>(A, s, beta, k)) * (0.5f * (float)lv.inv_h[2]);
+  g[0] = (neighbour_value<ST, INTERP, 0, 1>(A, R, s, beta, k) -
+          neighbour_value<ST, INTERP, 0, -1>(A, R, s, beta, k)) * (0.5f * (float)lv.inv_h[0]);
+  g[1] = (neighbour_value<ST, INTERP, 1, 1>(A, R, s, beta, k) -
+          neighbour_value<ST, INTERP, 1, -1>(A, R, s, beta, k)) * (0.5f * (float)lv.inv_h[1]);
+  g[2] = (neighbour_value<ST, INTERP, 2, 1>(A, R, s, beta, k) -
+          neighbour_value<ST, INTERP, 2, -1>(A, R, s, beta, k)) * (0.5f * (float)lv.inv_h[2]);
 }
 
 // A segment ready for sampling: its state, first sample position and step in brick
@@ -764,7 +769,8 @@ __device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& r
 // compositing; Sec. 4: gradient shading).  Returns true when early termination stops the
 // ray inside the segment.
 template <int ST, int INTERP, int SHADE>
-__device__ __forceinline__ bool sample_segment(const RenderArgs& A, const float4* s_tf,
+__device__ __forceinline__ bool sample_segment(const RenderArgs& A, const RayArgs& R,
+                                               const float4* s_tf,
                                                const SegSetup& g, const DLevel& lv, float Lx,
                                                float Ly, float Lz, float& C0, float& C1, float& C2,
                                                float& Acc, unsigned& nsamp) {
@@ -773,7 +779,7 @@ __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const float4
     float beta[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
-    const float v = sample_value<ST, INTERP>(A, s, beta, k);
+    const float v = sample_value<ST, INTERP>(A, R, s, beta, k);
     const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
     ++nsamp;
     if (c.w <= 0.0f) continue;
@@ -781,7 +787,7 @@ __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const float4
     float cr = c.x, cg = c.y, cb = c.z;
     if constexpr (SHADE >= 1) {
       float gr[3];
-      gradient<ST, INTERP, (SHADE == 2)>(A, s, beta, k, lv, gr);
+      gradient<ST, INTERP, (SHADE == 2)>(A, R, s, beta, k, lv, gr);
       const float gn = sqrtf(fmaf(gr[0], gr[0], fmaf(gr[1], gr[1], gr[2] * gr[2])));
       const float gf = A.gfloor_num / lv.hmin;
       const float den = fmaxf(gn, gf);
@@ -809,81 +815,97 @@ __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const float4
 #define AMR_MIN_BLOCKS 4
 #endif
 
+// The whole march of pixel (i, j) of the view R: ray setup, kd-restart over the leaves,
+// sampling and compositing.  Returns premultiplied RGBA; adds to nsamp and status.
+template <int ST, int INTERP, int SHADE>
+__device__ __forceinline__ float4 march_ray(const RenderArgs& A, const RayArgs& R, int i, int j,
+                                            const float4* s_tf, const int* s_nz, unsigned& nsamp,
+                                            unsigned long long& status) {
+  float C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
+  RayX rx;
+  if (make_ray(R, i, j, rx)) {
+    RayF rf;
+    make_frame(R, rx, rf);
+    const float inv_dn = 1.0f / rf.dn;
+    const float Lx = -rf.Dd[0] * (float)R.hf[0] * inv_dn;
+    const float Ly = -rf.Dd[1] * (float)R.hf[1] * inv_dn;
+    const float Lz = -rf.Dd[2] * (float)R.hf[2] * inv_dn;
+    int pid0 = kPidIn;
+    float tau0 = 0.0f, e0 = 0.0f;
+    uint32_t start = 0;
+    int seg = 0;
+    while (pid0 != kPidOut) {
+      if (seg >= A.max_segments) {
+        status |= kStatusCapacity;
+        break;
+      }
+      ++seg;
+      int pid1 = kPidOut;
+      float tau1 = rf.tau_out, e1 = rf.e_out;
+      const int lid = descend(A.nodes, R, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
+      if (lid < 0) {
+        status |= kStatusDevice;
+        break;
+      }
+      const DLeaf lf = A.leaves[lid];
+      const DLevel& lv = A.lv[lf.level];
+      int n = segment_count(R, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv);
+      if (n > kMaxSamplesPerSegment) {
+        status |= kStatusCapacity;
+        n = kMaxSamplesPerSegment;
+      }
+      if (A.skip && tf_transparent(s_nz, A.tf_n, lf.vmin, lf.vmax, A.vmin, A.inv_range)) {
+        pid0 = pid1;
+        tau0 = tau1;
+        e0 = e1;
+        continue;
+      }
+      SegSetup g;
+      setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
+      if (sample_segment<ST, INTERP, SHADE>(A, R, s_tf, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
+        pid1 = kPidOut;  // early ray termination
+      pid0 = pid1;
+      tau0 = tau1;
+      e0 = e1;
+    }
+  }
+  return make_float4(C0, C1, C2, Acc);
+}
+
+// Stage a transfer function in shared memory with the prefix count of its non-transparent
+// entries (nz[k] = entries before k with alpha != 0), for exact empty-space skipping.
+__device__ __forceinline__ void stage_tf(const float4* __restrict__ tf, int n, float4* s_tf,
+                                         int* s_nz, int tid, int nthreads) {
+  for (int k = tid; k < n; k += nthreads) s_tf[k] = tf[k];
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    s_nz[0] = 0;
+    for (int k = 0; k < n; ++k) {
+      acc += s_tf[k].w != 0.0f ? 1 : 0;
+      s_nz[k + 1] = acc;
+    }
+  }
+  __syncthreads();
+}
+
 template <int ST, int INTERP, int SHADE>
 __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) march_kernel(const __grid_constant__ RenderArgs A) {
   extern __shared__ float4 smem[];
   float4* s_tf = smem;
   int* s_nz = reinterpret_cast<int*>(smem + A.tf_n);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  for (int k = tid; k < A.tf_n; k += blockDim.x * blockDim.y) s_tf[k] = A.tf[k];
-  __syncthreads();
-  if (tid == 0) {
-    int acc = 0;
-    s_nz[0] = 0;
-    for (int k = 0; k < A.tf_n; ++k) {
-      acc += s_tf[k].w != 0.0f ? 1 : 0;
-      s_nz[k + 1] = acc;
-    }
-  }
-  __syncthreads();
+  stage_tf(A.tf, A.tf_n, s_tf, s_nz, tid, blockDim.x * blockDim.y);
 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int jr = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = A.ray.row0 + jr;
   const bool active = i < A.ray.width && jr < A.ray.rows && j < A.ray.height;
-  float C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
   unsigned nsamp = 0;
   unsigned long long status = 0;
-  if (active) {
-    RayX rx;
-    if (make_ray(A.ray, i, j, rx)) {
-      RayF rf;
-      make_frame(A.ray, rx, rf);
-      const float inv_dn = 1.0f / rf.dn;
-      const float Lx = -rf.Dd[0] * (float)A.ray.hf[0] * inv_dn;
-      const float Ly = -rf.Dd[1] * (float)A.ray.hf[1] * inv_dn;
-      const float Lz = -rf.Dd[2] * (float)A.ray.hf[2] * inv_dn;
-      int pid0 = kPidIn;
-      float tau0 = 0.0f, e0 = 0.0f;
-      uint32_t start = 0;
-      int seg = 0;
-      while (pid0 != kPidOut) {
-        if (seg >= A.max_segments) {
-          status |= kStatusCapacity;
-          break;
-        }
-        ++seg;
-        int pid1 = kPidOut;
-        float tau1 = rf.tau_out, e1 = rf.e_out;
-        const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
-        if (lid < 0) {
-          status |= kStatusDevice;
-          break;
-        }
-        const DLeaf lf = A.leaves[lid];
-        const DLevel& lv = A.lv[lf.level];
-        int n = segment_count(A, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv);
-        if (n > kMaxSamplesPerSegment) {
-          status |= kStatusCapacity;
-          n = kMaxSamplesPerSegment;
-        }
-        if (A.skip && tf_transparent(s_nz, A.tf_n, lf.vmin, lf.vmax, A.vmin, A.inv_range)) {
-          pid0 = pid1;
-          tau0 = tau1;
-          e0 = e1;
-          continue;
-        }
-        SegSetup g;
-        setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
-        if (sample_segment<ST, INTERP, SHADE>(A, s_tf, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
-          pid1 = kPidOut;  // early ray termination
-        pid0 = pid1;
-        tau0 = tau1;
-        e0 = e1;
-      }
-    }
-    A.out[(size_t)jr * A.ray.width + i] = make_float4(C0, C1, C2, Acc);
-  }
+  if (active)
+    A.out[(size_t)jr * A.ray.width + i] =
+        march_ray<ST, INTERP, SHADE>(A, A.ray, i, j, s_tf, s_nz, nsamp, status);
   // exact sample count: one atomic per warp
   const unsigned total = __reduce_add_sync(0xffffffffu, nsamp);
   if ((tid & 31) == 0 && total) atomicAdd(A.counters, (unsigned long long)total);

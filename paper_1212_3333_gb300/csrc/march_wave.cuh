@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
         } else {
           const DLeaf lf = A.leaves[lid];
           const DLevel& lv = A.lv[lf.level];
-          n = segment_count(A, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv);
+          n = segment_count(A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv);
           if (n > kMaxSamplesPerSegment) {
             status |= kStatusCapacity;
             n = kMaxSamplesPerSegment;
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
           float beta[3];
 #pragma unroll
           for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, ws.db[a], ws.b0[a]);
-          const float v = sample_value<ST, INTERP>(A, ws.s, beta, k);
+          const float v = sample_value<ST, INTERP>(A, A.ray, ws.s, beta, k);
           const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
           const float alpha = c.w > 0.0f ? -expm1f(-A.kappa * c.w * ws.delta) : 0.0f;
           const int pq = pad_idx(q);
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
           for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, ws.db[a], ws.b0[a]);
           const DLevel& lv = A.lv[ws.s.level];
           float g[3];
-          gradient<ST, INTERP, (SHADE == 2)>(A, ws.s, beta, k, lv, g);
+          gradient<ST, INTERP, (SHADE == 2)>(A, A.ray, ws.s, beta, k, lv, g);
           const float gn = sqrtf(fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2])));
           const float gf = A.gfloor_num / lv.hmin;
           const float den = fmaxf(gn, gf);
