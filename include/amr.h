@@ -93,14 +93,17 @@ typedef struct {
   int32_t rows;       /* number of rows; <= 0: all rows from row0 */
   int32_t skip;       /* 0: none; 1: exact leaf min/max empty-space skipping */
   int32_t max_segments; /* per-ray segment bound; <= 0: 4 * nodes + 64 */
-  int32_t schedule;   /* 0: one loop per ray (default); 1: warp wavefront (the samples of a
-                         warp's current segments spread over its lanes, shading on the
-                         compacted opaque samples; pays off when rays diverge, e.g. small
-                         views of a large volume) */
+  int32_t schedule;   /* 0: one loop per ray; 1: warp wavefront (the samples of a warp's
+                         current segments spread over its lanes, shading on the compacted
+                         opaque samples); 2: persistent warps that refill finished lanes
+                         with new rays and fetch segments in batches (trilinear only).
+                         All three give the same image. */
   int32_t learned;    /* learned segment proposal (needs amr_set_proposal; trilinear; ptr or
                          atlas_linear storage, FP32 cells): 0 off; 1 skip segments whose predicted
                          contribution is below tau; 2 sample them with a 4x coarser step */
   double tau;         /* proposal threshold (default 1e-3) */
+  int32_t samples_per_iter; /* schedule 2: samples a lane takes between warp steps, 1..64
+                               (default 4) */
 } amr_render_params;
 
 /* Fills p with the defaults: step 0.5, kappa 8, ert_eps 1e-4, vmin 0, vmax 1, ka 0.3,

@@ -100,6 +100,7 @@ struct RenderArgs {
   float tau;                     // proposal threshold on the predicted contribution
   int32_t learned;               // 0 off, 1 skip, 2 coarse (4x step) below tau
   float inv_levels;              // 1 / (L - 1), 0 for one level
+  int32_t samples_per_iter;      // refill schedule: samples per lane between warp steps
 };
 
 struct TraceArgs {

@@ -110,6 +110,7 @@ void amr_default_params(amr_render_params* p) {
   p->schedule = 0;
   p->learned = 0;
   p->tau = 1e-3;
+  p->samples_per_iter = 4;
 }
 
 amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double domain_lo[3],
@@ -276,7 +277,11 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   if (!(p->kappa >= 0.0)) return fail(c, AMR_ERR_ARG, "kappa must be non-negative");
   if (p->interp != 0 && p->interp != 1) return fail(c, AMR_ERR_ARG, "unknown interp");
   if (p->shade != 0 && p->shade != 1) return fail(c, AMR_ERR_ARG, "unknown shade");
-  if (p->schedule != 0 && p->schedule != 1) return fail(c, AMR_ERR_ARG, "unknown schedule");
+  if (p->schedule < 0 || p->schedule > 2) return fail(c, AMR_ERR_ARG, "unknown schedule");
+  if (p->schedule == 2 && (p->samples_per_iter < 1 || p->samples_per_iter > 64))
+    return fail(c, AMR_ERR_ARG, "samples_per_iter must be in [1, 64]");
+  if (p->schedule == 2 && p->interp != AMR_INTERP_TRILINEAR)
+    return fail(c, AMR_ERR_ARG, "the refill schedule renders trilinear");
   if (p->row0 < 0 || p->row0 >= cam->height) return fail(c, AMR_ERR_ARG, "row0 out of range");
   int rows = p->rows <= 0 ? cam->height - p->row0 : std::min(p->rows, cam->height - p->row0);
   std::memset(a, 0, sizeof *a);
@@ -308,8 +313,9 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->tau = (float)p->tau;
   a->learned = p->learned;
   a->inv_levels = c->L > 1 ? 1.0f / (float)(c->L - 1) : 0.0f;
-  if (c->dtype != AMR_F32 && (p->interp != AMR_INTERP_TRILINEAR || p->schedule != 0))
-    return fail(c, AMR_ERR_ARG, "16-bit cells render trilinear with the per-ray schedule");
+  a->samples_per_iter = p->samples_per_iter;
+  if (c->dtype != AMR_F32 && (p->interp != AMR_INTERP_TRILINEAR || p->schedule == 1))
+    return fail(c, AMR_ERR_ARG, "16-bit cells render trilinear with schedule 0 or 2");
   if (p->learned != 0) {
     if (p->learned != 1 && p->learned != 2) return fail(c, AMR_ERR_ARG, "unknown learned mode");
     if (c->dtype != AMR_F32) return fail(c, AMR_ERR_ARG, "the learned proposal needs FP32 cells");

@@ -765,46 +765,57 @@ __device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& r
   s.margin = ex * lv.inv_sc + ldexpf(bmax + 2.0f, -21);
 }
 
-// March the samples of one segment front to back (Sec. 3: emission-absorption
-// compositing; Sec. 4: gradient shading).  Returns true when early termination stops the
-// ray inside the segment.
+// Sample k of a segment (Sec. 3: emission-absorption compositing; Sec. 4: gradient
+// shading), composited front to back into (C, Acc).  Returns true when early ray
+// termination stops the ray at this sample.
+template <int ST, int INTERP, int SHADE>
+__device__ __forceinline__ bool sample_one(const RenderArgs& A, const RayArgs& R,
+                                           const float4* s_tf, const SegSetup& g,
+                                           const DLevel& lv, int k, float Lx, float Ly, float Lz,
+                                           float& C0, float& C1, float& C2, float& Acc) {
+  const SegState& s = g.s;
+  float beta[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
+  const float v = sample_value<ST, INTERP>(A, R, s, beta, k);
+  const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
+  if (c.w <= 0.0f) return false;
+  const float alpha = -expm1f(-A.kappa * c.w * g.delta);
+  float cr = c.x, cg = c.y, cb = c.z;
+  if constexpr (SHADE >= 1) {
+    float gr[3];
+    gradient<ST, INTERP, (SHADE == 2)>(A, R, s, beta, k, lv, gr);
+    const float gn = sqrtf(fmaf(gr[0], gr[0], fmaf(gr[1], gr[1], gr[2] * gr[2])));
+    const float gf = A.gfloor_num / lv.hmin;
+    const float den = fmaxf(gn, gf);
+    const float inv = den > 0.0f ? 1.0f / den : 0.0f;
+    const float ndl = fabsf((gr[0] * Lx + gr[1] * Ly + gr[2] * Lz) * inv);
+    const float spec = A.ks * __powf(ndl, A.shininess);
+    const float diff = fmaf(A.kd, ndl, A.ka);
+    cr = fminf(fmaxf(fmaf(cr, diff, spec), 0.0f), 1.0f);
+    cg = fminf(fmaxf(fmaf(cg, diff, spec), 0.0f), 1.0f);
+    cb = fminf(fmaxf(fmaf(cb, diff, spec), 0.0f), 1.0f);
+  }
+  const float w = (1.0f - Acc) * alpha;
+  C0 = fmaf(w, cr, C0);
+  C1 = fmaf(w, cg, C1);
+  C2 = fmaf(w, cb, C2);
+  Acc += w;
+  return Acc >= A.ert_thresh;
+}
+
+// March the samples of one segment front to back.  Returns true when early ray
+// termination stops the ray inside the segment.
 template <int ST, int INTERP, int SHADE>
 __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const RayArgs& R,
                                                const float4* s_tf,
                                                const SegSetup& g, const DLevel& lv, float Lx,
                                                float Ly, float Lz, float& C0, float& C1, float& C2,
                                                float& Acc, unsigned& nsamp) {
-  const SegState& s = g.s;
-  for (int k = 0; k < s.n; ++k) {
-    float beta[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
-    const float v = sample_value<ST, INTERP>(A, R, s, beta, k);
-    const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
+  for (int k = 0; k < g.s.n; ++k) {
     ++nsamp;
-    if (c.w <= 0.0f) continue;
-    const float alpha = -expm1f(-A.kappa * c.w * g.delta);
-    float cr = c.x, cg = c.y, cb = c.z;
-    if constexpr (SHADE >= 1) {
-      float gr[3];
-      gradient<ST, INTERP, (SHADE == 2)>(A, R, s, beta, k, lv, gr);
-      const float gn = sqrtf(fmaf(gr[0], gr[0], fmaf(gr[1], gr[1], gr[2] * gr[2])));
-      const float gf = A.gfloor_num / lv.hmin;
-      const float den = fmaxf(gn, gf);
-      const float inv = den > 0.0f ? 1.0f / den : 0.0f;
-      const float ndl = fabsf((gr[0] * Lx + gr[1] * Ly + gr[2] * Lz) * inv);
-      const float spec = A.ks * __powf(ndl, A.shininess);
-      const float diff = fmaf(A.kd, ndl, A.ka);
-      cr = fminf(fmaxf(fmaf(cr, diff, spec), 0.0f), 1.0f);
-      cg = fminf(fmaxf(fmaf(cg, diff, spec), 0.0f), 1.0f);
-      cb = fminf(fmaxf(fmaf(cb, diff, spec), 0.0f), 1.0f);
-    }
-    const float w = (1.0f - Acc) * alpha;
-    C0 = fmaf(w, cr, C0);
-    C1 = fmaf(w, cg, C1);
-    C2 = fmaf(w, cb, C2);
-    Acc += w;
-    if (Acc >= A.ert_thresh) return true;
+    if (sample_one<ST, INTERP, SHADE>(A, R, s_tf, g, lv, k, Lx, Ly, Lz, C0, C1, C2, Acc))
+      return true;
   }
   return false;
 }

@@ -1,7 +1,10 @@
 // Template launcher shared by the per-storage translation units.
 #pragma once
+#include <algorithm>
+
 #include "ctx.h"
 #include "march.cuh"
+#include "march_persist.cuh"
 #include "march_wave.cuh"
 
 namespace amr {
@@ -18,6 +21,24 @@ cudaError_t launch_one(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_
   return cudaGetLastError();
 }
 
+// Persistent launch of the refill schedule: as many blocks as fit on the device, at most
+// one warp per 8x4 pixel tile.
+template <typename K>
+cudaError_t launch_persist(K kernel, size_t smem, cudaStream_t s, const RenderArgs& a) {
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 0, occ = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, smem);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (long long)((a.ray.width + 7) / 8) * ((a.ray.rows + 3) / 4);
+  const long long grid = std::max(1LL, std::min((long long)sms * std::max(occ, 1), (tiles + 3) / 4));
+  kernel<<<(unsigned)grid, dim3(8, 16), smem, s>>>(a, a.samples_per_iter);
+  return cudaGetLastError();
+}
+
 template <int ST>
 amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade, int schedule,
                           cudaStream_t s) {
@@ -26,10 +47,17 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
   const size_t tf_bytes = (size_t)a.tf_n * sizeof(float4) + (size_t)(a.tf_n + 1) * sizeof(int);
   if (grid.x == 0 || grid.y == 0) return AMR_OK;
   cudaError_t e;
-  if constexpr (ST >= ST_PTR_F16) {
+  if (schedule == 2) {
+    // persistent warps with ray refill (trilinear)
+    if (interp != 1) return fail(c, AMR_ERR_ARG, "the refill schedule renders trilinear");
+    const size_t smem = tf_bytes;
+    if (shade == 0) e = launch_persist(persist_kernel<ST, 1, 0>, smem, s, a);
+    else if (shade == 1) e = launch_persist(persist_kernel<ST, 1, 1>, smem, s, a);
+    else e = launch_persist(persist_kernel<ST, 1, 2>, smem, s, a);
+  } else if constexpr (ST >= ST_PTR_F16) {
     // 16-bit cells: trilinear, per-ray schedule
     if (interp != 1 || schedule != 0)
-      return fail(c, AMR_ERR_ARG, "16-bit storage renders trilinear with the per-ray schedule");
+      return fail(c, AMR_ERR_ARG, "16-bit storage renders trilinear with schedule 0 or 2");
     const size_t smem = tf_bytes;
     if (shade == 0) e = launch_one(march_kernel<ST, 1, 0>, grid, block, smem, s, a);
     else if (shade == 1) e = launch_one(march_kernel<ST, 1, 1>, grid, block, smem, s, a);
