@@ -13,6 +13,7 @@ from .amr import (  # noqa: F401
     make_uniform,
     orbit_camera,
     ramp_tf,
+    tf_variants,
     c1_workload,
     c2_workload,
 )
