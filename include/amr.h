@@ -100,10 +100,13 @@ typedef struct {
                          All three give the same image. */
   int32_t learned;    /* learned segment proposal (needs amr_set_proposal; trilinear; ptr or
                          atlas_linear storage, FP32 cells): 0 off; 1 skip segments whose predicted
-                         contribution is below tau; 2 sample them with a 4x coarser step */
+                         contribution is below tau; 2 sample them with a coarse_factor times
+                         coarser step */
   double tau;         /* proposal threshold (default 1e-3) */
   int32_t samples_per_iter; /* schedule 2: samples a lane takes between warp steps, 1..64
                                (default 4) */
+  int32_t coarse_factor;    /* learned mode 2: a segment predicted below tau takes
+                               ceil(n / coarse_factor) samples, 2..64 (default 4) */
 } amr_render_params;
 
 /* Fills p with the defaults: step 0.5, kappa 8, ert_eps 1e-4, vmin 0, vmax 1, ka 0.3,

@@ -40,7 +40,8 @@ class amr_render_params(C.Structure):
                 ("gamma", C.c_double), ("interp", C.c_int32), ("shade", C.c_int32),
                 ("row0", C.c_int32), ("rows", C.c_int32), ("skip", C.c_int32),
                 ("max_segments", C.c_int32), ("schedule", C.c_int32),
-                ("learned", C.c_int32), ("tau", C.c_double), ("samples_per_iter", C.c_int32)]
+                ("learned", C.c_int32), ("tau", C.c_double), ("samples_per_iter", C.c_int32),
+                ("coarse_factor", C.c_int32)]
 
 
 class amr_stats(C.Structure):

@@ -98,9 +98,10 @@ struct RenderArgs {
   unsigned long long* counters;  // [0] samples, [1] status bits
   const unsigned char* mlp;      // packed learned-proposal weights (inference image)
   float tau;                     // proposal threshold on the predicted contribution
-  int32_t learned;               // 0 off, 1 skip, 2 coarse (4x step) below tau
+  int32_t learned;               // 0 off, 1 skip, 2 coarse (coarse_factor x step) below tau
   float inv_levels;              // 1 / (L - 1), 0 for one level
   int32_t samples_per_iter;      // refill schedule: samples per lane between warp steps
+  int32_t coarse_factor;         // learned mode 2: step multiplier below tau
 };
 
 struct TraceArgs {

@@ -111,6 +111,7 @@ void amr_default_params(amr_render_params* p) {
   p->learned = 0;
   p->tau = 1e-3;
   p->samples_per_iter = 4;
+  p->coarse_factor = 4;
 }
 
 amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double domain_lo[3],
@@ -314,10 +315,13 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->learned = p->learned;
   a->inv_levels = c->L > 1 ? 1.0f / (float)(c->L - 1) : 0.0f;
   a->samples_per_iter = p->samples_per_iter;
+  a->coarse_factor = p->coarse_factor;
   if (c->dtype != AMR_F32 && (p->interp != AMR_INTERP_TRILINEAR || p->schedule == 1))
     return fail(c, AMR_ERR_ARG, "16-bit cells render trilinear with schedule 0 or 2");
   if (p->learned != 0) {
     if (p->learned != 1 && p->learned != 2) return fail(c, AMR_ERR_ARG, "unknown learned mode");
+    if (p->learned == 2 && (p->coarse_factor < 2 || p->coarse_factor > 64))
+      return fail(c, AMR_ERR_ARG, "coarse_factor must be in [2, 64]");
     if (c->dtype != AMR_F32) return fail(c, AMR_ERR_ARG, "the learned proposal needs FP32 cells");
     if (!c->dev.proposal) return fail(c, AMR_ERR_STATE, "learned render before amr_set_proposal");
     if (p->interp != AMR_INTERP_TRILINEAR)

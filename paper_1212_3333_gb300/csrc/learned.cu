@@ -5,7 +5,7 @@
 // live lane descends to its ray's next segment, drops it if exact min/max skipping proves
 // it transparent, and stages its 12 features; the warp evaluates the MLP for all 32 lanes
 // on the tensor cores (mlp_forward_warp); a segment whose predicted opacity contribution is
-// below tau is skipped (mode 1) or sampled with a 4x coarser step (mode 2); otherwise it is
+// below tau is skipped (mode 1) or sampled with a coarse_factor times coarser step (mode 2); otherwise it is
 // sampled exactly as the plain march samples it.
 //
 // log_kernel is the plain march (no early termination) that records, per segment kept by a
@@ -185,13 +185,17 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
         }
       }
     }
-    // stage the warp's features and evaluate the proposal on the tensor cores
+    // stage the warp's features and evaluate the proposal on the tensor cores (only when
+    // some lane has a segment to decide)
+    if (__any_sync(0xffffffffu, n > 0)) {
 #pragma unroll
-    for (int k = 0; k < kMlpInPad; ++k)
-      xs[lane * kStride1 + k] = __float2bfloat16_rn(k < kMlpIn ? f[k] : 0.0f);
-    __syncwarp();
-    const float predicted = mlp_forward_warp(wsm, xs, ys, lane);
-    if (n > 0 && predicted < A.tau) n = A.learned == 1 ? 0 : (n + 3) / 4;
+      for (int k = 0; k < kMlpInPad; ++k)
+        xs[lane * kStride1 + k] = __float2bfloat16_rn(k < kMlpIn ? f[k] : 0.0f);
+      __syncwarp();
+      const float predicted = mlp_forward_warp(wsm, xs, ys, lane);
+      if (n > 0 && predicted < A.tau)
+        n = A.learned == 1 ? 0 : (n + A.coarse_factor - 1) / A.coarse_factor;
+    }
     if (n > 0) {
       const DLevel& lv = A.lv[lf.level];
       SegSetup g;

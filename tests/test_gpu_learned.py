@@ -178,3 +178,28 @@ def test_learned_proposal_trains_and_keeps_psnr(mods, c1_learned):
     psnr = 10 * np.log10(1.0 / mse) if mse > 0 else np.inf
     assert psnr >= 45.0, psnr
     assert n <= n_minmax <= n_plain
+
+
+def test_coarse_factor_scales_the_sample_count(mods, c1_learned):
+    torch, amr, proposal = mods
+    from paper_1212_3333_gb300 import _lib
+
+    w, ctx = c1_learned
+    proposal.Proposal(seed=7).install(ctx)
+    p, _ = params_pair(amr, w["vmin"], w["vmax"], ert_eps=0.0)
+    plain, n_plain = gpu_render(ctx, w["camera"], w["tf"], p)
+    counts = []
+    for cf in (2, 4, 16):
+        # tau above every prediction: every segment is sampled coarsely
+        pl, _ = params_pair(amr, w["vmin"], w["vmax"], ert_eps=0.0, learned=2, tau=1.5,
+                            coarse_factor=cf)
+        img, n = gpu_render(ctx, w["camera"], w["tf"], pl)
+        assert np.all(np.isfinite(img))
+        counts.append(n)
+    assert n_plain > counts[0] > counts[1] > counts[2] > 0
+    assert counts[0] >= n_plain / 2 and counts[2] >= n_plain / 16
+    for cf in (1, 65):
+        pl, _ = params_pair(amr, w["vmin"], w["vmax"], learned=2, tau=0.5, coarse_factor=cf)
+        with pytest.raises(amr.AmrError) as e:
+            gpu_render(ctx, w["camera"], w["tf"], pl)
+        assert e.value.status == _lib.AMR_ERR_ARG
