@@ -258,9 +258,11 @@ def precision_eval(amr, hier, vmin, vmax, cam, tf, out, args, peak):
     res = {}
     ref = None
     for dtype, e in (("f32", 4), ("f16", 2), ("bf16", 2)):
+        t0 = time.perf_counter()
         ctx = amr.from_hierarchy(hier, dtype)
         ctx.amr_build_kdtree("ptr", gradient=True)
-        r = {"brick_mb": ctx.amr_get_stats().brick_bytes / 1e6}
+        r = {"brick_mb": ctx.amr_get_stats().brick_bytes / 1e6,
+             "build_s": time.perf_counter() - t0}
         for shade in (0, 1):
             p = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=shade, ert_eps=args.ert)
             n = ctx.amr_render(cam, tf, p, out, count_samples=True)
@@ -351,6 +353,25 @@ def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5):
                          "ms": dict(zip(names, table)), "seconds": tune_s}}
 
 
+def c3_eval(amr, args, peak):
+    """The deep 8-level hierarchy (1/16384 finest spacing, ~1e9 cells) at 2048², Phong:
+    FP32 / FP16 / BF16 cells, throughput and PSNR of each against the FP32-cell image."""
+    import torch
+    import synth
+
+    t0 = time.perf_counter()
+    h = synth.amr.make_c3(device="cuda")
+    gen_s = time.perf_counter() - t0
+    vmin, vmax = synth.amr.percentile_range(h)
+    precision = precision_eval(amr, h, vmin, vmax, synth.orbit_camera(3, SIZE, SIZE),
+                               torch.as_tensor(synth.ramp_tf(), device="cuda"),
+                               torch.empty((SIZE, SIZE, 4), dtype=torch.float32, device="cuda"),
+                               args, peak)
+    return {"patches": h.num_patches, "patches_per_level": h.patches_per_level(),
+            "cells": h.n_cells(), "levels": h.num_levels, "generate_s": gen_s,
+            "precision": precision}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -413,6 +434,8 @@ def main():
     ap.add_argument("--learned", type=int, default=1, help="evaluate the learned proposal")
     ap.add_argument("--precision", type=int, default=1, help="time FP16 / BF16 cell storage")
     ap.add_argument("--batch", type=int, default=1, help="time 64-view batched rendering")
+    ap.add_argument("--c3", type=int, default=0,
+                    help="also render the deep 8-level hierarchy (~1e9 cells; minutes)")
     ap.add_argument("--log-size", type=int, default=96)
     ap.add_argument("--log-cap", type=int, default=10_000_000)
     ap.add_argument("--log-keep", type=float, default=0.3)
@@ -552,6 +575,8 @@ def main():
         extra["precision"] = precision_eval(amr, hier, vmin, vmax, cam, tf, out, args, peak)
     if args.batch and world == 1 and args.storage == "ptr" and args.dtype == "f32":
         extra["batch"] = batch_eval(amr, ctx, vmin, vmax, args, peak)
+    if args.c3 and world == 1:
+        extra["c3"] = c3_eval(amr, args, peak)
     if args.learned and world == 1:
         extra["learned"] = learned_eval(amr, ctx, hier, vmin, vmax, tf, args)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -370,10 +370,33 @@ def _cache_path(key: str) -> Optional[str]:
     return os.path.join(root, hashlib.sha1(key.encode()).hexdigest()[:16] + ".npz")
 
 
+def _box_cells(bs) -> int:
+    return int(sum((b[3] - b[0]) * (b[4] - b[1]) * (b[5] - b[2]) for b in bs))
+
+
+def _fit_budget(fl, vals, coarse, n_l, tile, ratio, budget):
+    """Raise the refinement threshold until the refined patches hold at most `budget`
+    finer cells: keep the densest flagged cells (fl, densities vals), their number scaled
+    by the budget over the current cell count, and re-cluster (a few passes)."""
+    cells = _box_cells(coarse) * ratio ** 3
+    if cells <= budget:
+        return coarse
+    order = np.argsort(-vals, kind="stable")
+    keep = fl.shape[0]
+    for _ in range(8):
+        keep = max(1, int(keep * budget / cells * 0.97))
+        sel = fl[np.sort(order[:keep])]
+        coarse = _tile_patches(sel.astype(np.int64), n_l, tile, tile // 2, 4)
+        cells = _box_cells(coarse) * ratio ** 3
+        if cells <= budget:
+            break
+    return coarse
+
+
 def make_lognormal(seed: int = 2, num_levels: int = 5, n0: int = 128, patch0: int = 32,
                    threshold: float = 4.0, level_growth: float = 2.25, tile: int = 32,
                    M: int = 2048, device=None, name: str = "c2",
-                   use_cache: bool = True) -> Hierarchy:
+                   use_cache: bool = True, cell_budget: Optional[int] = None) -> Hierarchy:
     """Cosmology-like SAMR hierarchy.
 
     Level 0: (n0/patch0)^3 patches of patch0^3 cells on [0,1]^3.  The density is
@@ -383,8 +406,14 @@ def make_lognormal(seed: int = 2, num_levels: int = 5, n0: int = 128, patch0: in
     cells are clustered per tile of `tile` level-l cells on a global grid shifted by
     tile/2, so fine patches straddle coarse parents (non-nested refinement) and are
     8..2*tile fine cells per axis.  Each patch samples rho at its own cell centres.
+
+    cell_budget (optional) caps the cells of every refined level: when the patches of the
+    flagged cells would hold more, the threshold is raised to a quantile of the level's
+    flagged densities (refining the densest cells first) until they fit.
     """
     key = f"lognormal:{seed}:{num_levels}:{n0}:{patch0}:{threshold}:{level_growth}:{tile}:{M}"
+    if cell_budget is not None:
+        key += f":budget{int(cell_budget)}"
     path = _cache_path(key) if use_cache else None
     if path and os.path.exists(path):
         z = np.load(path, allow_pickle=False)
@@ -416,6 +445,7 @@ def make_lognormal(seed: int = 2, num_levels: int = 5, n0: int = 128, patch0: in
     for l in range(num_levels):
         h = 1.0 / (n0 * ratio ** l)
         flags = []
+        fvals = []
         thr = threshold * mean_rho * level_growth ** l
         for b in cur:
             xs = (np.arange(b[0], b[3]) + 0.5) * h
@@ -429,11 +459,16 @@ def make_lognormal(seed: int = 2, num_levels: int = 5, n0: int = 128, patch0: in
                 kk, jj, ii = np.nonzero(rho > thr)
                 if kk.size:
                     flags.append(np.stack([ii + b[0], jj + b[1], kk + b[2]], axis=1))
+                    if cell_budget is not None:
+                        fvals.append(rho[kk, jj, ii])
         if l + 1 == num_levels:
             break
         fl = np.concatenate(flags, axis=0) if flags else np.zeros((0, 3), dtype=np.int64)
         n_l = np.full(3, n0 * ratio ** l, dtype=np.int64)
         coarse = _tile_patches(fl.astype(np.int64), n_l, tile, tile // 2, 4)
+        if cell_budget is not None and coarse:
+            coarse = _fit_budget(fl, np.concatenate(fvals), coarse, n_l, tile, ratio,
+                                 int(cell_budget))
         cur = [[c * ratio for c in b] for b in coarse]
         if not cur:
             num_levels = l + 1
@@ -452,6 +487,15 @@ def make_lognormal(seed: int = 2, num_levels: int = 5, n0: int = 128, patch0: in
 
 def make_c2(seed: int = 2, device=None, use_cache: bool = True) -> Hierarchy:
     return make_lognormal(seed=seed, num_levels=5, device=device, name="c2", use_cache=use_cache)
+
+
+def make_c3(seed: int = 3, device=None, use_cache: bool = False,
+            cell_budget: int = 140_000_000) -> Hierarchy:
+    """Deep hierarchy: the C2 generator with 8 levels (finest spacing 1/16384), the density
+    threshold fixed at 4x the mean on every level, and each refined level capped at
+    `cell_budget` cells (about 1e9 cells and 2e4 patches in all)."""
+    return make_lognormal(seed=seed, num_levels=8, level_growth=1.0, device=device, name="c3",
+                          use_cache=use_cache, cell_budget=cell_budget)
 
 
 def percentile_range(hier: Hierarchy, q: float = 99.9):
