@@ -18,7 +18,7 @@ namespace amr {
 namespace {
 
 template <int ST, int SHADE, int TW, int TH>
-__global__ void __launch_bounds__(TW * TH, 512 / (TW * TH))
+__global__ void __launch_bounds__(TW * TH, (128 * kMinBlocks<SHADE>) / (TW * TH))
     batch_kernel(const __grid_constant__ BatchArgs B) {
   constexpr int NT = TW * TH;
   const RenderArgs& A = B.A;

@@ -820,11 +820,20 @@ __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const RayArg
   return false;
 }
 
-// resident blocks per SM the compiler must allow for (register budget 65536 / (128 x this));
-// 4 (<= 128 registers) measured fastest for the shaded kernels on C2 at 2048^2
+// Resident 128-thread blocks per SM the compiler must allow for, i.e. a register budget of
+// 65536 / (128 x this) per thread.  Measured on C2 at 2048^2 (Gsamples/s, Phong / unshaded):
+// 3 blocks 30.8 / 119.3, 4 blocks 34.1 / 119.4, 5 blocks 36.1 / 119.7, 6 blocks 33.2 / 126.0.
 #ifndef AMR_MIN_BLOCKS
-#define AMR_MIN_BLOCKS 4
+#define AMR_MIN_BLOCKS 4  // kernels outside the frame march (learned march)
 #endif
+#ifndef AMR_MIN_BLOCKS_SHADED
+#define AMR_MIN_BLOCKS_SHADED 5
+#endif
+#ifndef AMR_MIN_BLOCKS_PLAIN
+#define AMR_MIN_BLOCKS_PLAIN 6
+#endif
+template <int SHADE>
+constexpr int kMinBlocks = SHADE == 0 ? AMR_MIN_BLOCKS_PLAIN : AMR_MIN_BLOCKS_SHADED;
 
 // The whole march of pixel (i, j) of the view R: ray setup, kd-restart over the leaves,
 // sampling and compositing.  Returns premultiplied RGBA; adds to nsamp and status.
@@ -901,7 +910,7 @@ __device__ __forceinline__ void stage_tf(const float4* __restrict__ tf, int n, f
 }
 
 template <int ST, int INTERP, int SHADE>
-__global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) march_kernel(const __grid_constant__ RenderArgs A) {
+__global__ void __launch_bounds__(128, kMinBlocks<SHADE>) march_kernel(const __grid_constant__ RenderArgs A) {
   extern __shared__ float4 smem[];
   float4* s_tf = smem;
   int* s_nz = reinterpret_cast<int*>(smem + A.tf_n);

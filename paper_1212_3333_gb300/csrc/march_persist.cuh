@@ -18,7 +18,7 @@
 namespace amr {
 
 template <int ST, int INTERP, int SHADE>
-__global__ void __launch_bounds__(128, AMR_MIN_BLOCKS)
+__global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
     persist_kernel(const __grid_constant__ RenderArgs A, int samples_per_iter) {
   extern __shared__ float4 smem[];
   float4* s_tf = smem;
