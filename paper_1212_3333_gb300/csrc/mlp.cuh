@@ -51,18 +51,25 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// One hidden layer for the warp's 32 rows: acc = A * W^T (+ bias, ReLU later).
+// One hidden layer for the warp's 32 rows: acc = bias + A * W^T (ReLU follows).  The
+// accumulators start at the bias, so the epilogue is only ReLU and packing.
 // a: [2 m-tiles][KS k-steps][4] packed BF16 A fragments; W: smem rows of `stride` bf16.
 template <int KS>
 __device__ __forceinline__ void mlp_layer(const uint32_t (&a)[2][KS][4], const unsigned char* smem,
-                                          int woff, int stride, int lane, float (&acc)[2][8][4]) {
+                                          int woff, int stride, const float* bias, int lane,
+                                          float (&acc)[2][8][4]) {
   const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-  for (int m = 0; m < 2; ++m)
+  for (int n = 0; n < 8; ++n) {
+    const float2 b = *reinterpret_cast<const float2*>(bias + 8 * n + 2 * t);
 #pragma unroll
-    for (int n = 0; n < 8; ++n)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.0f;
+    for (int m = 0; m < 2; ++m) {
+      acc[m][n][0] = b.x;
+      acc[m][n][1] = b.y;
+      acc[m][n][2] = b.x;
+      acc[m][n][3] = b.y;
+    }
+  }
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
     const uint32_t* row =
@@ -77,22 +84,23 @@ __device__ __forceinline__ void mlp_layer(const uint32_t (&a)[2][KS][4], const u
   }
 }
 
-// bias + ReLU on accumulators, repacked as the next layer's A fragments (4 k-steps)
-__device__ __forceinline__ void mlp_relu_pack(const float (&acc)[2][8][4], const float* bias,
-                                              int lane, uint32_t (&a)[2][4][4]) {
-  const int t = lane & 3;
+// ReLU of the accumulators, rounded to BF16 and repacked as the next layer's A fragments
+// (4 k-steps).  Rounding is monotone and keeps 0, so max(round(x), 0) = round(max(x, 0)):
+// the maximum is taken on the packed pairs.
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __hmax2(__floats2bfloat162_rn(lo, hi), __float2bfloat162_rn(0.0f));
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mlp_relu_pack(const float (&acc)[2][8][4], uint32_t (&a)[2][4][4]) {
 #pragma unroll
   for (int m = 0; m < 2; ++m)
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      const int c0 = 16 * s + 2 * t;  // columns of n-tile 2s: c0, c0+1; of n-tile 2s+1: +8
-      const float b0 = bias[c0], b1 = bias[c0 + 1], b2 = bias[c0 + 8], b3 = bias[c0 + 9];
-      a[m][s][0] = pack_bf16(fmaxf(acc[m][2 * s][0] + b0, 0.f), fmaxf(acc[m][2 * s][1] + b1, 0.f));
-      a[m][s][1] = pack_bf16(fmaxf(acc[m][2 * s][2] + b0, 0.f), fmaxf(acc[m][2 * s][3] + b1, 0.f));
-      a[m][s][2] = pack_bf16(fmaxf(acc[m][2 * s + 1][0] + b2, 0.f),
-                             fmaxf(acc[m][2 * s + 1][1] + b3, 0.f));
-      a[m][s][3] = pack_bf16(fmaxf(acc[m][2 * s + 1][2] + b2, 0.f),
-                             fmaxf(acc[m][2 * s + 1][3] + b3, 0.f));
+      a[m][s][0] = relu_bf16x2(acc[m][2 * s][0], acc[m][2 * s][1]);
+      a[m][s][1] = relu_bf16x2(acc[m][2 * s][2], acc[m][2 * s][3]);
+      a[m][s][2] = relu_bf16x2(acc[m][2 * s + 1][0], acc[m][2 * s + 1][1]);
+      a[m][s][3] = relu_bf16x2(acc[m][2 * s + 1][2], acc[m][2 * s + 1][3]);
     }
 }
 
@@ -115,12 +123,12 @@ __device__ __forceinline__ float mlp_forward_warp(const unsigned char* wsm,
   }
   float acc[2][8][4];
   uint32_t a[2][4][4];
-  mlp_layer<1>(a1, wsm, kPackW1, kStride1, lane, acc);
-  mlp_relu_pack(acc, bias, lane, a);
-  mlp_layer<4>(a, wsm, kPackW2, kStrideH, lane, acc);
-  mlp_relu_pack(acc, bias + kMlpH, lane, a);
-  mlp_layer<4>(a, wsm, kPackW3, kStrideH, lane, acc);
-  mlp_relu_pack(acc, bias + 2 * kMlpH, lane, a);
+  mlp_layer<1>(a1, wsm, kPackW1, kStride1, bias, lane, acc);
+  mlp_relu_pack(acc, a);
+  mlp_layer<4>(a, wsm, kPackW2, kStrideH, bias + kMlpH, lane, acc);
+  mlp_relu_pack(acc, a);
+  mlp_layer<4>(a, wsm, kPackW3, kStrideH, bias + 2 * kMlpH, lane, acc);
+  mlp_relu_pack(acc, a);
   // output layer: one n-tile whose column 0 is the logit
   const uint32_t* w4 = reinterpret_cast<const uint32_t*>(wsm + kPackW4 + (size_t)g * kStrideH * 2);
   float o[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};

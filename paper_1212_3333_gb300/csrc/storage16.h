@@ -30,26 +30,26 @@ inline float bf16_value(uint16_t b) {
 inline uint16_t f16_bits(float x) {
   uint32_t u;
   std::memcpy(&u, &x, 4);
-  const uint16_t sign = (uint16_t)((u >> 16) & 0x8000u);
-  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)(sign | 0x7e00u);  // quiet NaN
-  const double v = std::fabs((double)x);
-  if (v == 0.0) return sign;
-  if (std::isinf(v)) return (uint16_t)(sign | 0x7c00u);
-  int e;
-  std::frexp(v, &e);               // v = f 2^e, f in [0.5, 1): leading bit at 2^(e-1)
-  int E = e - 1 < -14 ? -14 : e - 1;  // binary16 exponent (subnormals share -14)
-  const double s = std::ldexp(v, 10 - E);  // significand in units of the last place; exact
-  double m = std::floor(s);
-  const double rem = s - m;
-  if (rem > 0.5 || (rem == 0.5 && std::fmod(m, 2.0) != 0.0)) m += 1.0;
-  if (m >= 2048.0) {  // rounding carried into the next binade
-    m = 1024.0;
-    ++E;
+  const uint32_t sign = (u >> 16) & 0x8000u;
+  uint32_t a = u & 0x7fffffffu;
+  if (a > 0x7f800000u) return (uint16_t)(sign | 0x7e00u);  // quiet NaN
+  if (a >= 0x477ff000u) return (uint16_t)(sign | 0x7c00u); // |x| >= 65520 rounds to infinity
+  if (a >= 0x38800000u) {
+    // normal binary16 (|x| >= 2^-14): rebias the exponent (127 -> 15) and keep 10 fraction
+    // bits, adding half an ulp minus one plus the kept lsb (ties to even; a carry moves
+    // into the exponent)
+    a += 0x00000fffu + ((a >> 13) & 1u);
+    return (uint16_t)(sign | ((a - 0x38000000u) >> 13));
   }
-  if (E > 15) return (uint16_t)(sign | 0x7c00u);  // overflow: infinity
-  const uint32_t mi = (uint32_t)m;
-  if (mi < 1024u) return (uint16_t)(sign | mi);   // subnormal (E == -14)
-  return (uint16_t)(sign | ((uint32_t)(E + 15) << 10) | (mi - 1024u));
+  if (a <= 0x33000000u) return (uint16_t)sign;  // |x| <= 2^-25 rounds to zero
+  // subnormal binary16: |x| / 2^-24 rounded to an integer (1024 is the smallest normal)
+  const uint32_t e = a >> 23;                         // 102..112
+  const uint32_t mant = (a & 0x7fffffu) | 0x800000u;  // |x| = mant 2^(e - 150)
+  const uint32_t shift = 126u - e;                    // |x| / 2^-24 = mant / 2^shift
+  uint32_t m = mant >> shift;
+  const uint32_t rem = mant & ((1u << shift) - 1u), half = 1u << (shift - 1u);
+  if (rem > half || (rem == half && (m & 1u))) ++m;
+  return (uint16_t)(sign | m);
 }
 
 inline float f16_value(uint16_t h) {

@@ -86,3 +86,22 @@ def test_16bit_cells_need_a_linear_storage(storage):
         c.amr_build_host(storage)
     assert e.value.status == _lib.AMR_ERR_ARG
     c.amr_build_host("atlas_linear", gradient=True)
+
+
+@pytest.mark.parametrize("dtype,ref", [("f16", _f16), ("bf16", _bf16)])
+def test_rounding_over_random_bit_patterns(dtype, ref):
+    """200k random float32 bit patterns across every binade the cell type can hold."""
+    rng = np.random.default_rng(11 if dtype == "f16" else 12)
+    bits = rng.integers(0, 1 << 32, size=64 * 64 * 48, dtype=np.uint64).astype(np.uint32)
+    v = bits.view(np.float32).copy()
+    lim = 65504.0 if dtype == "f16" else 1e30
+    bad = ~np.isfinite(v) | (np.abs(v) > lim)
+    v[bad] = rng.uniform(-1, 1, size=int(bad.sum())).astype(np.float32)
+    d = v.reshape(48, 64, 64)
+    c32 = amr.amr_create(1, 2, (0, 0, 0), (1, 1, 1), [0], [[0, 0, 0, 64, 64, 48]], [d])
+    c32.amr_build_host("ptr")
+    c16 = amr.amr_create(1, 2, (0, 0, 0), (1, 1, 1), [0], [[0, 0, 0, 64, 64, 48]], [d],
+                         dtype=dtype)
+    c16.amr_build_host("ptr")
+    b32 = c32.amr_get_brick(0)
+    np.testing.assert_array_equal(c16.amr_get_brick(0).view(np.uint32), ref(b32).view(np.uint32))
