@@ -36,6 +36,14 @@
  *     sub-step midpoints; the sample value is S_l of the segment's leaf level.
  *   - alpha = 1 - exp(-kappa * a_TF * delta); C += (1-A) alpha rgb; A += (1-A) alpha;
  *     stop once A >= 1 - eps_ert (eps_ert <= 0: never).
+ *   - level of detail (Sec. 3.1 type-(a) nodes, Sec. 3.3 pruning): an inner node whose box
+ *     lies in one patch of level l (its label) may stand in for its subtree.  With
+ *     lod_pixels > 0 the segment starting at t0 stops the descent at the first such node
+ *     with hmin^l <= X = lod_pixels * (2 tan_half_fov_y / H) * t0 (the level's cells cover
+ *     at most lod_pixels pixels at parameter t0, t in units of a unit fwd vector) and is
+ *     sampled at level l from that patch; F_X, the field of that pruned tree, replaces F
+ *     in the segment's gradients.  Pruned nodes take leaf ids after the leaves, in
+ *     pre-order.
  *   - gradient g_a = (F(x + h^l e_a) - F(x - h^l e_a)) / (2 h^l_a);
  *     n = g / max(|g|, gamma (vmax - vmin) / h^l); headlight L = V = H = -d/|d|;
  *     rgb' = clamp(rgb (ka + kd |n.L|) + ks |n.L|^shininess, 0, 1).
@@ -84,7 +92,8 @@ typedef struct orc_hier {
   int* pre2node;   /* pre-order id -> node index */
   int* leaf2node;  /* leaf id -> node index */
   int* node2leaf;  /* node index -> leaf id (-1 internal) */
-  int nleaves;
+  int* node2lod;   /* node index -> id of the node as a pruned leaf (-1: not a type-(a) node) */
+  int nleaves, nlod;
   int built;
 } orc_hier;
 
@@ -102,6 +111,7 @@ typedef struct {
   int shade;          /* 0 none, 1 gradient Phong */
   int lookup;         /* F's finest-level search: 0 kD-tree descent, 1 scan of all patches */
   int max_segments;   /* per ray; exceeding it is a capacity error */
+  double lod_pixels;  /* > 0: level-of-detail pruning threshold in pixels */
 } orc_params;
 
 /* ------------------------------------------------------------------------------------ */
@@ -350,8 +360,12 @@ int orc_build(orc_hier* h) {
   h->pre2node = (int*)malloc((size_t)h->nn * sizeof(int));
   h->node2leaf = (int*)malloc((size_t)h->nn * sizeof(int));
   h->leaf2node = (int*)malloc((size_t)h->nn * sizeof(int));
+  h->node2lod = (int*)malloc((size_t)h->nn * sizeof(int));
   int* stack = (int*)malloc((size_t)h->nn * sizeof(int));
-  if (!h->pre2node || !h->node2leaf || !h->leaf2node || !stack) { free(stack); return ORC_ERR_OOM; }
+  if (!h->pre2node || !h->node2leaf || !h->leaf2node || !h->node2lod || !stack) {
+    free(stack);
+    return ORC_ERR_OOM;
+  }
   int sp = 0, k = 0;
   h->nleaves = 0;
   stack[sp++] = 0;
@@ -368,6 +382,12 @@ int orc_build(orc_hier* h) {
     }
   }
   free(stack);
+  /* type-(a) nodes, numbered after the leaves in pre-order */
+  h->nlod = 0;
+  for (int q = 0; q < h->nn; ++q) {
+    int i = h->pre2node[q];
+    h->node2lod[i] = (h->nodes[i].axis >= 0 && h->nodes[i].patch >= 0) ? h->nleaves + h->nlod++ : -1;
+  }
   h->built = 1;
   return ORC_OK;
 }

@@ -823,8 +823,11 @@ __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const RayArg
 // Resident 128-thread blocks per SM the compiler must allow for, i.e. a register budget of
 // 65536 / (128 x this) per thread.  Measured on C2 at 2048^2 (Gsamples/s, Phong / unshaded):
 // 3 blocks 30.8 / 119.3, 4 blocks 34.1 / 119.4, 5 blocks 36.1 / 119.7, 6 blocks 33.2 / 126.0.
+// The learned march keeps the MLP fragments live beside the ray state: 3 blocks (168
+// registers) measured fastest there (coarse16@0.01 on C2 at 2048^2: 2.25x the plain march
+// at 3 blocks, 1.90x at 4, 1.57x at 5).
 #ifndef AMR_MIN_BLOCKS
-#define AMR_MIN_BLOCKS 4  // kernels outside the frame march (learned march)
+#define AMR_MIN_BLOCKS 3
 #endif
 #ifndef AMR_MIN_BLOCKS_SHADED
 #define AMR_MIN_BLOCKS_SHADED 5
