@@ -52,7 +52,8 @@ class _Params(C.Structure):
                 ("vmin", C.c_double), ("vmax", C.c_double), ("ka", C.c_double),
                 ("kd", C.c_double), ("ks", C.c_double), ("shininess", C.c_double),
                 ("gamma", C.c_double), ("world_step", C.c_double), ("interp", C.c_int),
-                ("shade", C.c_int), ("lookup", C.c_int), ("max_segments", C.c_int)]
+                ("shade", C.c_int), ("lookup", C.c_int), ("max_segments", C.c_int),
+                ("lod_pixels", C.c_double)]
 
 
 def _load():
@@ -83,6 +84,9 @@ def _load():
             lib.orc_lookup_scan.argtypes = [P, dp, ip]
             lib.orc_lookup_leaf.argtypes = [P, dp]
             lib.orc_trace.argtypes = [P, C.POINTER(_Camera), C.c_int, C.c_int, ip, dp, dp, C.c_int]
+            lib.orc_trace_lod.argtypes = [P, C.POINTER(_Camera), C.c_int, C.c_int, C.c_double,
+                                          ip, dp, dp, C.c_int]
+            lib.orc_get_node_labels.argtypes = [P, ip, ip, ip]
             lib.orc_render_pixels.argtypes = [P, C.POINTER(_Camera), C.POINTER(C.c_float), C.c_int,
                                               C.POINTER(_Params), C.c_int, ip, ip, dp,
                                               C.POINTER(C.c_ulonglong), C.c_int]
@@ -136,11 +140,12 @@ class OracleParams:
     world_step: float = 0.0
     lookup: int = 0
     max_segments: int = 0
+    lod_pixels: float = 0.0  # > 0: level-of-detail pruning (Sec. 3.1 type-(a) nodes)
 
     def struct(self) -> _Params:
         p = _Params()
         for f in ("step_factor", "kappa", "ert_eps", "vmin", "vmax", "ka", "kd", "ks",
-                  "shininess", "gamma", "world_step"):
+                  "shininess", "gamma", "world_step", "lod_pixels"):
             setattr(p, f, float(getattr(self, f)))
         for f in ("interp", "shade", "lookup", "max_segments"):
             setattr(p, f, int(getattr(self, f)))
@@ -219,6 +224,18 @@ class Oracle:
             raise OracleError(rc, "orc_get_nodes")
         return axis, split, left, right, leaf
 
+    def node_labels(self):
+        """Pre-order node labels: patch, level (for an inner node: the patch of that level
+        holding its whole box, -1 if none) and the node's pruned-leaf id (-1 if none)."""
+        N = self.num_nodes
+        patch = np.zeros(N, dtype=np.int32)
+        level = np.zeros(N, dtype=np.int32)
+        lod = np.zeros(N, dtype=np.int32)
+        rc = self._lib.orc_get_node_labels(self._h, _ip(patch), _ip(level), _ip(lod))
+        if rc < 0:
+            raise OracleError(rc, "orc_get_node_labels")
+        return patch, level, lod
+
     # ------------------------------------------------------------------ field (Sec. 2, 4)
     def V(self, l: int, i: int, j: int, k: int) -> float:
         return float(self._lib.orc_V(self._h, l, i, j, k))
@@ -242,14 +259,15 @@ class Oracle:
         return int(self._lib.orc_lookup_leaf(self._h, _dp(xa)))
 
     # ------------------------------------------------------------------ rays (Sec. 3.3)
-    def trace(self, cam, i: int, j: int, cap: int = 1 << 16):
-        """Leaf-id sequence and segment parameters of pixel (i, j)."""
+    def trace(self, cam, i: int, j: int, cap: int = 1 << 16, lod_pixels: float = 0.0):
+        """Leaf-id sequence and segment parameters of pixel (i, j); with lod_pixels > 0
+        the pruned descent (pruned nodes have ids after the leaves)."""
         leaf = np.zeros(cap, dtype=np.int32)
         t0 = np.zeros(cap, dtype=np.float64)
         t1 = np.zeros(cap, dtype=np.float64)
         cs = camera_struct(cam)
-        n = self._lib.orc_trace(self._h, C.byref(cs), int(i), int(j), _ip(leaf), _dp(t0),
-                                _dp(t1), cap)
+        n = self._lib.orc_trace_lod(self._h, C.byref(cs), int(i), int(j), float(lod_pixels),
+                                    _ip(leaf), _dp(t0), _dp(t1), cap)
         if n < 0:
             raise OracleError(n, "orc_trace")
         return leaf[:n].copy(), t0[:n].copy(), t1[:n].copy()

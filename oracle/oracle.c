@@ -155,6 +155,7 @@ void orc_destroy(orc_hier* h) {
   free(h->pre2node);
   free(h->leaf2node);
   free(h->node2leaf);
+  free(h->node2lod);
   free(h);
 }
 
@@ -425,6 +426,19 @@ int orc_get_nodes(const orc_hier* h, int* axis, i64* split, int* left, int* righ
   return h->nn;
 }
 
+/* Labels in pre-order: patch and level of every node (for an inner node: the patch of
+ * that level holding its whole box, or -1), and its pruned-leaf id (-1 if none). */
+int orc_get_node_labels(const orc_hier* h, int* patch, int* level, int* lod) {
+  if (!h || !h->built) return ORC_ERR_STATE;
+  for (int k = 0; k < h->nn; ++k) {
+    const onode* n = &h->nodes[h->pre2node[k]];
+    patch[k] = n->patch;
+    level[k] = n->level;
+    lod[k] = h->node2lod[h->pre2node[k]];
+  }
+  return h->nlod;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* field: V_l, S_l, F (Sec. 2 and Sec. 4)                                               */
 /* ------------------------------------------------------------------------------------ */
@@ -531,25 +545,42 @@ static int scan_finest(const orc_hier* h, const i64* f, int* patch) {
   return -1;
 }
 
-/* leaf holding finest cell f, by descending the kD-tree (left iff f_a < split) */
-static int kd_leaf(const orc_hier* h, const i64* f) {
+/* smallest spacing of level l */
+static double hmin_level(const orc_hier* h, int l) {
+  double m = hl(h, l, 0);
+  if (hl(h, l, 1) < m) m = hl(h, l, 1);
+  if (hl(h, l, 2) < m) m = hl(h, l, 2);
+  return m;
+}
+
+/* level-of-detail stop: an inner node lying in one patch of level l whose cells are at
+ * most X wide (X <= 0: pruning off) */
+static int lod_stop(const orc_hier* h, const onode* n, double X) {
+  return X > 0.0 && n->axis >= 0 && n->patch >= 0 && hmin_level(h, n->level) <= X;
+}
+
+/* leaf (or pruned node) holding finest cell f, by descending the kD-tree (left iff
+ * f_a < split) */
+static int kd_leaf(const orc_hier* h, const i64* f, double X) {
   int i = 0;
   while (h->nodes[i].axis >= 0) {
     const onode* n = &h->nodes[i];
+    if (lod_stop(h, n, X)) return i;
     i = (f[n->axis] < n->split) ? n->left : n->right;
   }
   return i;
 }
 
-/* F(x): sample at the finest level whose patch holds (the clamped) x */
-static double F_field(const orc_hier* h, const double* x, int interp, int lookup) {
+/* F(x): sample at the finest level whose patch holds (the clamped) x; with pruning bound
+ * X > 0, F_X(x): sample at the level of the kD node the pruned descent stops at */
+static double F_field(const orc_hier* h, const double* x, int interp, int lookup, double X) {
   i64 f[3];
   finest_cell(h, x, f);
   int l, p;
-  if (lookup == 1) {
+  if (lookup == 1 && X <= 0.0) {
     l = scan_finest(h, f, &p);
   } else {
-    const onode* n = &h->nodes[kd_leaf(h, f)];
+    const onode* n = &h->nodes[kd_leaf(h, f, X)];
     l = n->level;
     p = n->patch;
   }
@@ -566,7 +597,7 @@ double orc_S(const orc_hier* h, int l, const double* x) {
 }
 double orc_F(const orc_hier* h, const double* x, int interp, int lookup) {
   if (!h || !h->built) return NAN;
-  return F_field(h, x, interp, lookup);
+  return F_field(h, x, interp, lookup, 0.0);
 }
 /* finest covering level of x by scan; *patch receives the patch */
 int orc_lookup_scan(const orc_hier* h, const double* x, int* patch) {
@@ -580,7 +611,7 @@ int orc_lookup_leaf(const orc_hier* h, const double* x) {
   if (!h || !h->built) return ORC_ERR_STATE;
   i64 f[3];
   finest_cell(h, x, f);
-  return h->node2leaf[kd_leaf(h, f)];
+  return h->node2leaf[kd_leaf(h, f, 0.0)];
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -628,12 +659,15 @@ static void make_ray(const orc_hier* h, const orc_camera* cam, int i, int j, ora
   ry->t_out = t_out;
 }
 
-/* descend from the root for the segment starting at t0; returns the leaf node index and
- * narrows *t1 (entering with the ray's exit parameter) */
-static int restart_descend(const orc_hier* h, const oray* ry, double t0, double* t1) {
+/* descend from the root for the segment starting at t0; returns the leaf node index (or
+ * the pruned inner node, for pruning bound X > 0) and narrows *t1 (entering with the
+ * ray's exit parameter) */
+static int restart_descend(const orc_hier* h, const oray* ry, double t0, double* t1,
+                           double X) {
   int i = 0;
   while (h->nodes[i].axis >= 0) {
     const onode* n = &h->nodes[i];
+    if (lod_stop(h, n, X)) return i;
     int a = n->axis;
     double sw = plane_world(h, a, n->split);
     if (ry->d[a] == 0.0) {
@@ -655,27 +689,40 @@ static int restart_descend(const orc_hier* h, const oray* ry, double t0, double*
   return i;
 }
 
+/* pixel footprint per unit ray parameter times the pruning threshold (0: pruning off) */
+static double lod_scale(const orc_camera* cam, double lod_pixels) {
+  if (!(lod_pixels > 0.0)) return 0.0;
+  return lod_pixels * ((2.0 * cam->tan_half_fov_y) / (double)cam->height);
+}
+
 /* Per-pixel traversal sequence: leaf ids and segment parameters.  Returns the number of
- * segments (0: the ray misses the root), or ORC_ERR_CAPACITY when `cap` is too small. */
-int orc_trace(const orc_hier* h, const orc_camera* cam, int i, int j, int* leaf,
-              double* t0s, double* t1s, int cap) {
+ * segments (0: the ray misses the root), or ORC_ERR_CAPACITY when `cap` is too small.
+ * lod_pixels > 0 prunes the descent (pruned nodes report their ids after the leaves). */
+int orc_trace_lod(const orc_hier* h, const orc_camera* cam, int i, int j, double lod_pixels,
+                  int* leaf, double* t0s, double* t1s, int cap) {
   if (!h || !h->built) return ORC_ERR_STATE;
   oray ry;
   make_ray(h, cam, i, j, &ry);
   if (!ry.hit) return 0;
+  const double ls = lod_scale(cam, lod_pixels);
   int n = 0;
   double t0 = ry.t_in;
   while (t0 < ry.t_out) {
     double t1 = ry.t_out;
-    int nd = restart_descend(h, &ry, t0, &t1);
+    int nd = restart_descend(h, &ry, t0, &t1, ls > 0.0 ? ls * t0 : 0.0);
     if (n >= cap) return ORC_ERR_CAPACITY;
-    leaf[n] = h->node2leaf[nd];
+    leaf[n] = h->nodes[nd].axis < 0 ? h->node2leaf[nd] : h->node2lod[nd];
     t0s[n] = t0;
     t1s[n] = t1;
     n++;
     t0 = t1;
   }
   return n;
+}
+
+int orc_trace(const orc_hier* h, const orc_camera* cam, int i, int j, int* leaf,
+              double* t0s, double* t1s, int cap) {
+  return orc_trace_lod(h, cam, i, j, 0.0, leaf, t0s, t1s, cap);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -712,11 +759,13 @@ static void render_pixel(const orc_hier* h, const orc_camera* cam, const float* 
   double dn = sqrt((ry.d[0] * ry.d[0] + ry.d[1] * ry.d[1]) + ry.d[2] * ry.d[2]);
   double Lv[3] = {-ry.d[0] / dn, -ry.d[1] / dn, -ry.d[2] / dn};
   double C[3] = {0.0, 0.0, 0.0}, A = 0.0;
+  const double ls = lod_scale(cam, pr->lod_pixels);
   double t0 = ry.t_in;
   int done = 0;
   while (t0 < ry.t_out && !done) {
     double t1 = ry.t_out;
-    int nd = restart_descend(h, &ry, t0, &t1);
+    const double X = ls > 0.0 ? ls * t0 : 0.0;  /* pruning bound of this segment */
+    int nd = restart_descend(h, &ry, t0, &t1, X);
     if (pr->max_segments > 0 && out->segments >= pr->max_segments) { out->status = 1; break; }
     out->segments++;
     const onode* leaf = &h->nodes[nd];
@@ -748,7 +797,8 @@ static void render_pixel(const orc_hier* h, const orc_camera* cam, const float* 
           double ha = hl(h, l, a);
           xp[a] = x[a] + ha;
           xm[a] = x[a] - ha;
-          g[a] = (F_field(h, xp, pr->interp, pr->lookup) - F_field(h, xm, pr->interp, pr->lookup)) /
+          g[a] = (F_field(h, xp, pr->interp, pr->lookup, X) -
+                  F_field(h, xm, pr->interp, pr->lookup, X)) /
                  (2.0 * ha);
         }
         double gn = sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);
