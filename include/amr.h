@@ -107,6 +107,13 @@ typedef struct {
                                (default 4) */
   int32_t coarse_factor;    /* learned mode 2: a segment predicted below tau takes
                                ceil(n / coarse_factor) samples, 2..64 (default 4) */
+  double lod_pixels;        /* level-of-detail pruning (Sec. 3.1 type-(a) nodes, Sec. 3.3):
+                               > 0 stops the descent at an inner node lying in one patch of
+                               level l once min_a h^l_a <= lod_pixels * (2 tan_half_fov_y / H)
+                               * t0 (t0 the segment's entry parameter, a unit fwd assumed),
+                               and samples it at level l; gradients then read the same pruned
+                               tree.  0 (default) renders every level.  Schedules 0 and 2,
+                               no learned proposal. */
 } amr_render_params;
 
 /* Fills p with the defaults: step 0.5, kappa 8, ert_eps 1e-4, vmin 0, vmax 1, ka 0.3,
@@ -334,10 +341,12 @@ amr_status amr_get_brick(const amr_ctx* ctx, int32_t patch, float* out, int64_t 
 /* Per-pixel traversal (Sec. 3.3 kd-restart) on the device: for pixel (i, j) with
  * p = j*W + i, leaf_seq_dev[p*max_len + k] is the k-th leaf id, t_seq_dev (nullable)
  * [p*max_len + k][2] its entry/exit ray parameters (float64), seq_len_dev[p] the number
- * of segments (0 for a miss, -1 when more than max_len).  All device buffers. */
-amr_status amr_trace(amr_ctx* ctx, const amr_camera* cam, int32_t* leaf_seq_dev,
-                     double* t_seq_dev, int32_t* seq_len_dev, int32_t max_len,
-                     void* cuda_stream);
+ * of segments (0 for a miss, -1 when more than max_len).  All device buffers.
+ * lod_pixels > 0 prunes the descent as amr_render_params.lod_pixels does; pruned inner
+ * nodes report ids after the M leaves (M + k for the k-th such node in pre-order). */
+amr_status amr_trace(amr_ctx* ctx, const amr_camera* cam, double lod_pixels,
+                     int32_t* leaf_seq_dev, double* t_seq_dev, int32_t* seq_len_dev,
+                     int32_t max_len, void* cuda_stream);
 
 #ifdef __cplusplus
 }

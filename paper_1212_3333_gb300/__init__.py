@@ -148,9 +148,11 @@ class AmrContext:
             int(reps), C.c_void_p(_stream_ptr(stream)), C.byref(best), ms), self._h)
         return best, list(ms)
 
-    def amr_trace(self, camera, leaf_seq, seq_len, max_len: int, t_seq=None, stream=None) -> None:
+    def amr_trace(self, camera, leaf_seq, seq_len, max_len: int, t_seq=None, stream=None,
+                  lod_pixels: float = 0.0) -> None:
         cam = camera if isinstance(camera, amr_camera) else make_camera(camera)
-        _check(self._lib.amr_trace(self._h, C.byref(cam), C.c_void_p(_dptr(leaf_seq)),
+        _check(self._lib.amr_trace(self._h, C.byref(cam), float(lod_pixels),
+                                   C.c_void_p(_dptr(leaf_seq)),
                                    C.c_void_p(_dptr(t_seq) if t_seq is not None else None),
                                    C.c_void_p(_dptr(seq_len)), int(max_len),
                                    C.c_void_p(_stream_ptr(stream))), self._h)

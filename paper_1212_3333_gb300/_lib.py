@@ -41,7 +41,7 @@ class amr_render_params(C.Structure):
                 ("row0", C.c_int32), ("rows", C.c_int32), ("skip", C.c_int32),
                 ("max_segments", C.c_int32), ("schedule", C.c_int32),
                 ("learned", C.c_int32), ("tau", C.c_double), ("samples_per_iter", C.c_int32),
-                ("coarse_factor", C.c_int32)]
+                ("coarse_factor", C.c_int32), ("lod_pixels", C.c_double)]
 
 
 class amr_stats(C.Structure):
@@ -111,7 +111,7 @@ _SIGS = {
                                 C.c_int64, C.POINTER(C.c_int64)]),
     "amr_get_brick": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_float), C.c_int64,
                                 C.POINTER(C.c_int64)]),
-    "amr_trace": (C.c_int, [_P, C.POINTER(amr_camera), _P, _P, _P, C.c_int32, _P]),
+    "amr_trace": (C.c_int, [_P, C.POINTER(amr_camera), C.c_double, _P, _P, _P, C.c_int32, _P]),
 }
 
 _lock = threading.Lock()

@@ -61,8 +61,9 @@ struct DLevel {
   double step;       // sample step f * min_a h^l_a (world units)
   int32_t sc;        // finest cells per level-l cell, r^(L-1-l)
   float inv_sc;      // 1 / sc
-  float hmin;        // min_a h^l_a as float (gradient floor)
+  float hmin;        // min_a h^l_a as float (gradient floor, pruning filter)
   float inv_step;    // 1 / step as float
+  double hmin_d;     // min_a h^l_a (exact pruning decisions)
 };
 
 struct RayArgs {
@@ -76,6 +77,13 @@ struct RayArgs {
   double root_w[6];     // root box, world coordinates
   int32_t root_f[6];    // root box, finest cells
   unsigned long long* counters;  // [0] samples, [1] status, [2..4] exact-path counts
+  // level-of-detail pruning (Sec. 3.1 type-(a) nodes): per node (breadth-first slots)
+  // (pruned-leaf id << 5 | level) or -1; X(t) = lod_scale * t bounds the cell size at
+  // which the descent stops; lod_scale == 0 turns pruning off
+  const int32_t* lod;
+  int32_t levels;
+  double lod_scale;
+  float lod_scale_f;
 };
 
 struct RenderArgs {
@@ -106,6 +114,7 @@ struct RenderArgs {
 
 struct TraceArgs {
   RayArgs ray;
+  DLevel lv[kMaxLevels];
   const DNode* nodes;
   int32_t* leaf_seq;
   double* t_seq;
@@ -125,6 +134,8 @@ struct BatchView {
   int32_t tf;       // transfer-function index
   int32_t pad;
   long long out;    // float4 offset of the view's [H][W] image in the output buffer
+  double lod_scale; // pruning scale of this view (0: off)
+  float lod_scale_f;
 };
 
 struct BatchArgs {

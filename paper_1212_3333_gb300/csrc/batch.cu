@@ -73,6 +73,8 @@ __global__ void __launch_bounds__(TW * TH, (128 * kMinBlocks<SHADE>) / (TW * TH)
         s_ray.height = bv.height;
         s_ray.row0 = 0;
         s_ray.rows = bv.height;
+        s_ray.lod_scale = bv.lod_scale;
+        s_ray.lod_scale_f = bv.lod_scale_f;
         s_tf_idx = bv.tf;
         s_w = bv.width;
         s_h = bv.height;

@@ -170,20 +170,23 @@ amr_status build_bricks(amr_ctx* c) {
   }
   // value range every sample of a leaf can reach: the brick cells under the trilinear
   // stencils of all points of the leaf box
+  // (leaves first, then the pruned inner nodes of level-of-detail rendering)
   const Tree& t = c->tree;
-  const size_t M = t.leaf_patch.size();
-  c->leaf_vmin.assign(M, 0.0f);
-  c->leaf_vmax.assign(M, 0.0f);
-  for (size_t m = 0; m < M; ++m) {
-    int p = t.leaf_patch[m];
+  const size_t M = t.leaf_patch.size(), ML = t.lod_patch.size();
+  c->leaf_vmin.assign(M + ML, 0.0f);
+  c->leaf_vmax.assign(M + ML, 0.0f);
+  for (size_t m = 0; m < M + ML; ++m) {
+    const bool lod = m >= M;
+    const int p = lod ? t.lod_patch[m - M] : t.leaf_patch[m];
+    const int32_t* box = lod ? &t.lod_box[6 * (m - M)] : &t.leaf_box[6 * m];
     const Patch& pt = c->patches[p];
     const int64_t sc = c->rpow[L - 1 - pt.level];
     BrickView bv = view(p);
     int64_t lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
       // leaf extent in brick coordinates: beta = X - lo + 0.5 with X = finest / sc
-      double bmin = (double)t.leaf_box[6 * m + a] / (double)sc - (double)pt.box[a] + 0.5;
-      double bmax = (double)t.leaf_box[6 * m + 3 + a] / (double)sc - (double)pt.box[a] + 0.5;
+      double bmin = (double)box[a] / (double)sc - (double)pt.box[a] + 0.5;
+      double bmax = (double)box[3 + a] / (double)sc - (double)pt.box[a] + 0.5;
       lo[a] = std::max<int64_t>(0, (int64_t)std::floor(bmin));
       hi[a] = std::min<int64_t>(bv.d[a] - 1, (int64_t)std::floor(bmax) + 1);
     }

@@ -64,6 +64,17 @@ void fill_ray(const amr_ctx* c, const amr_camera* cam, int row0, int rows, RayAr
   ra->height = cam->height;
   ra->row0 = row0;
   ra->rows = rows;
+  ra->lod = c->dev.lod;
+  ra->levels = c->L;
+  ra->lod_scale = 0.0;
+  ra->lod_scale_f = 0.0f;
+}
+
+// pixel footprint per unit ray parameter times the pruning threshold (0: pruning off),
+// in the operation order the FP64 reference uses
+double lod_scale(const amr_camera* cam, double lod_pixels) {
+  if (!(lod_pixels > 0.0)) return 0.0;
+  return lod_pixels * ((2.0 * cam->tan_half_fov_y) / (double)cam->height);
 }
 
 void fill_levels(const amr_ctx* c, DLevel* lv, double step_factor) {
@@ -77,6 +88,7 @@ void fill_levels(const amr_ctx* c, DLevel* lv, double step_factor) {
       if (a == 0 || d.h[a] < hmin) hmin = d.h[a];
     }
     d.step = step_factor * hmin;
+    d.hmin_d = hmin;
     d.sc = (int32_t)c->rpow[c->L - 1 - l];
     d.inv_sc = 1.0f / (float)d.sc;
     d.hmin = (float)hmin;
@@ -283,10 +295,16 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
     return fail(c, AMR_ERR_ARG, "samples_per_iter must be in [1, 64]");
   if (p->schedule == 2 && p->interp != AMR_INTERP_TRILINEAR)
     return fail(c, AMR_ERR_ARG, "the refill schedule renders trilinear");
+  if (!(p->lod_pixels >= 0.0) || !std::isfinite(p->lod_pixels))
+    return fail(c, AMR_ERR_ARG, "lod_pixels must be finite and non-negative");
+  if (p->lod_pixels > 0.0 && (p->schedule == 1 || p->learned != 0))
+    return fail(c, AMR_ERR_ARG, "level-of-detail pruning needs schedule 0 or 2 without the proposal");
   if (p->row0 < 0 || p->row0 >= cam->height) return fail(c, AMR_ERR_ARG, "row0 out of range");
   int rows = p->rows <= 0 ? cam->height - p->row0 : std::min(p->rows, cam->height - p->row0);
   std::memset(a, 0, sizeof *a);
   fill_ray(c, cam, p->row0, rows, &a->ray);
+  a->ray.lod_scale = lod_scale(cam, p->lod_pixels);
+  a->ray.lod_scale_f = (float)a->ray.lod_scale;
   fill_levels(c, a->lv, p->step_factor);
   a->nodes = c->dev.nodes;
   a->leaves = c->dev.leaves;
@@ -485,6 +503,8 @@ amr_status prepare_batch(amr_ctx* c, const amr_view* views, int32_t n_views, con
     bv.item0 = (int32_t)items;
     bv.tf = in.tf_index;
     bv.out = in.out_offset / 4;
+    bv.lod_scale = lod_scale(&in.cam, p->lod_pixels);
+    bv.lod_scale_f = (float)bv.lod_scale;
     items += (int64_t)bv.tiles_x * ((in.cam.height + tile_rows - 1) / tile_rows);
     if (items >= ((int64_t)1 << 31)) return fail(c, AMR_ERR_ARG, "too many pixel tiles");
   }
@@ -697,17 +717,24 @@ amr_status amr_get_brick(const amr_ctx* c, int32_t patch, float* out, int64_t ca
   return AMR_OK;
 }
 
-amr_status amr_trace(amr_ctx* c, const amr_camera* cam, int32_t* leaf_seq_dev, double* t_seq_dev,
-                     int32_t* seq_len_dev, int32_t max_len, void* cuda_stream) {
+amr_status amr_trace(amr_ctx* c, const amr_camera* cam, double lod_pixels, int32_t* leaf_seq_dev,
+                     double* t_seq_dev, int32_t* seq_len_dev, int32_t max_len, void* cuda_stream) {
   if (!c) return AMR_ERR_ARG;
   if (!c->device_built) return fail(c, AMR_ERR_STATE, "trace before amr_build_kdtree");
   amr_status s = check_camera(c, cam);
   if (s != AMR_OK) return s;
   if (!leaf_seq_dev || !seq_len_dev || max_len < 1)
     return fail(c, AMR_ERR_ARG, "bad trace buffers");
-  TraceArgs a;
+  if (!(lod_pixels >= 0.0) || !std::isfinite(lod_pixels))
+    return fail(c, AMR_ERR_ARG, "lod_pixels must be finite and non-negative");
+  std::unique_ptr<TraceArgs> ap(new (std::nothrow) TraceArgs());
+  if (!ap) return fail(c, AMR_ERR_OOM, "out of host memory");
+  TraceArgs& a = *ap;
   std::memset(&a, 0, sizeof a);
   fill_ray(c, cam, 0, cam->height, &a.ray);
+  fill_levels(c, a.lv, 0.5);
+  a.ray.lod_scale = lod_scale(cam, lod_pixels);
+  a.ray.lod_scale_f = (float)a.ray.lod_scale;
   a.nodes = c->dev.nodes;
   a.leaf_seq = leaf_seq_dev;
   a.t_seq = t_seq_dev;

@@ -24,6 +24,10 @@ struct Tree {
   std::vector<int32_t> axis, split, left, right, leaf;  // per node, pre-order
   std::vector<int32_t> leaf_box;                        // 6 per leaf, finest cells
   std::vector<int32_t> leaf_patch, leaf_level;
+  // level-of-detail: inner nodes whose box lies in one patch (Sec. 3.1 type (a)) may be
+  // rendered as leaves of that patch's level; they take ids M, M+1, ... in pre-order
+  std::vector<int32_t> node_lod;                        // per node, pre-order: id or -1
+  std::vector<int32_t> lod_box, lod_patch, lod_level;   // per pruned leaf
   int max_depth = 0;
 };
 
@@ -54,6 +58,7 @@ struct DeviceState {
   float4* img_scratch = nullptr;
   unsigned char* proposal = nullptr;             // packed MLP weights (amr_set_proposal)
   size_t img_scratch_bytes = 0;
+  int32_t* lod = nullptr;                        // per node slot: (id << 5 | level) or -1
   int device = -1;
 };
 
@@ -108,6 +113,7 @@ amr_status launch_log(amr_ctx* c, const RenderArgs& a, int storage, float* featu
 const char* mlp_last_error();
 void fill_levels(const amr_ctx* c, DLevel* lv, double step_factor);
 void fill_ray(const amr_ctx* c, const amr_camera* cam, int row0, int rows, RayArgs* ra);
+double lod_scale(const amr_camera* cam, double lod_pixels);
 
 amr_status fail(amr_ctx* c, amr_status s, const std::string& msg);
 

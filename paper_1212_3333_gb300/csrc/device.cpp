@@ -18,10 +18,12 @@ namespace {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                \
   } while (0)
 
-// breadth-first re-layout: children of a node are adjacent, the top levels contiguous
-std::vector<DNode> layout_nodes(const Tree& t) {
+// breadth-first re-layout: children of a node are adjacent, the top levels contiguous;
+// lod receives each slot's pruned-leaf entry (id << 5 | level) or -1
+std::vector<DNode> layout_nodes(const Tree& t, std::vector<int32_t>& lod) {
   const size_t n = t.axis.size();
   std::vector<DNode> out(n);
+  lod.assign(n, -1);
   std::deque<std::pair<int, int>> q;  // (pre-order id, bfs slot)
   q.push_back({0, 0});
   int next = 1;
@@ -41,6 +43,11 @@ std::vector<DNode> layout_nodes(const Tree& t) {
       q.push_back({t.right[pre], first + 1});
     }
     out[slot] = d;
+    const int32_t q = t.node_lod.empty() ? -1 : t.node_lod[pre];
+    if (q >= 0) {
+      const int32_t lvl = t.lod_level[(size_t)q - t.leaf_patch.size()];
+      lod[slot] = (q << 5) | lvl;
+    }
   }
   return out;
 }
@@ -181,6 +188,7 @@ void release_device(amr_ctx* c) {
   if (d.gatlas_array) cudaFreeArray((cudaArray_t)d.gatlas_array);
   cudaFree(d.gpool);
   cudaFree(d.nodes);
+  cudaFree(d.lod);
   cudaFree(d.leaves);
   cudaFree(d.patches);
   cudaFree(d.pool);
@@ -202,14 +210,19 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   const size_t M = t.leaf_patch.size();
   if (t.axis.size() >= (size_t)kIndexMask || M >= (size_t)kIndexMask)
     return fail(c, AMR_ERR_CAPACITY, "tree too large for 30-bit node indices");
-  std::vector<DNode> nodes = layout_nodes(t);
-  std::vector<DLeaf> leaves(M);
-  for (size_t m = 0; m < M; ++m) {
+  std::vector<int32_t> lodv;
+  std::vector<DNode> nodes = layout_nodes(t, lodv);
+  const size_t ML = t.lod_patch.size();
+  if (M + ML >= ((size_t)1 << 26)) return fail(c, AMR_ERR_CAPACITY, "too many leaves");
+  std::vector<DLeaf> leaves(M + ML);
+  for (size_t m = 0; m < M + ML; ++m) {
     DLeaf& l = leaves[m];
     std::memset(&l, 0, sizeof l);
-    for (int k = 0; k < 6; ++k) (k < 3 ? l.lo[k] : l.hi[k - 3]) = t.leaf_box[6 * m + k];
-    l.patch = t.leaf_patch[m];
-    l.level = t.leaf_level[m];
+    const bool lod = m >= M;
+    const int32_t* box = lod ? &t.lod_box[6 * (m - M)] : &t.leaf_box[6 * m];
+    for (int k = 0; k < 6; ++k) (k < 3 ? l.lo[k] : l.hi[k - 3]) = box[k];
+    l.patch = lod ? t.lod_patch[m - M] : t.leaf_patch[m];
+    l.level = lod ? t.lod_level[m - M] : t.leaf_level[m];
     // the range of the cells as stored; rounding is monotone, so the rounded extremes
     // bound every rounded cell and empty-space skipping stays exact
     l.vmin = storage_round(c->dtype, c->leaf_vmin[m]);
@@ -224,7 +237,8 @@ amr_status upload(amr_ctx* c, void* stream_v) {
     }
   }
   CK(cudaMalloc(&d.nodes, nodes.size() * sizeof(DNode)));
-  CK(cudaMalloc(&d.leaves, std::max<size_t>(1, M) * sizeof(DLeaf)));
+  CK(cudaMalloc(&d.lod, lodv.size() * sizeof(int32_t)));
+  CK(cudaMalloc(&d.leaves, std::max<size_t>(1, M + ML) * sizeof(DLeaf)));
   CK(cudaMalloc(&d.patches, P * sizeof(DPatch)));
   CK(cudaMalloc(&d.counters, kNumCounters * sizeof(unsigned long long)));
   CK(cudaMemsetAsync(d.counters, 0, kNumCounters * sizeof(unsigned long long), stream));
@@ -264,8 +278,10 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   }
   CK(cudaMemcpyAsync(d.nodes, nodes.data(), nodes.size() * sizeof(DNode), cudaMemcpyHostToDevice,
                      stream));
-  if (M)
-    CK(cudaMemcpyAsync(d.leaves, leaves.data(), M * sizeof(DLeaf), cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(d.lod, lodv.data(), lodv.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                     stream));
+  if (M + ML)
+    CK(cudaMemcpyAsync(d.leaves, leaves.data(), (M + ML) * sizeof(DLeaf), cudaMemcpyHostToDevice,
                        stream));
   CK(cudaMemcpyAsync(d.patches, pt.data(), P * sizeof(DPatch), cudaMemcpyHostToDevice, stream));
   CK(cudaStreamSynchronize(stream));

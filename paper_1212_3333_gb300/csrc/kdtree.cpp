@@ -281,6 +281,21 @@ class Builder {
         t.right[k] = pre[b.right];
       }
     }
+    // inner nodes lying in one patch (labelled when they were still leaves) can stand in
+    // for their subtree at that patch's level: ids after the leaves, in pre-order
+    t.node_lod.assign(n, -1);
+    t.lod_box.clear();
+    t.lod_patch.clear();
+    t.lod_level.clear();
+    const int32_t M = (int32_t)t.leaf_patch.size();
+    for (size_t k = 0; k < n; ++k) {
+      const BNode& b = nodes_[order[k]];
+      if (b.axis < 0 || b.patch < 0) continue;
+      t.node_lod[k] = M + (int32_t)t.lod_patch.size();
+      for (int q = 0; q < 6; ++q) t.lod_box.push_back((int32_t)b.box[q]);
+      t.lod_patch.push_back(b.patch);
+      t.lod_level.push_back(b.level);
+    }
     if (t.max_depth >= kMaxDepth)
       return fail(c_, AMR_ERR_CAPACITY, "kD-tree deeper than the device descent bound");
     return AMR_OK;

@@ -63,6 +63,7 @@ struct RayF {
   float Xe[3], Dd[3];
   float tau_out, e_out;
   float dn;
+  float t_in;            // root entry parameter (level-of-detail distance)
   int exact_axes;        // bit a set: planes on axis a are always decided in FP64
 };
 
@@ -201,7 +202,50 @@ __device__ __forceinline__ void make_frame(const RayArgs& A, const RayX& r, RayF
   }
   const double tau_out = r.t_out - r.t_in;
   f.tau_out = (float)tau_out;
+  f.t_in = (float)r.t_in;
   f.e_out = ldexpf(f.tau_out + 1.0f, -22);
+}
+
+// Level-of-detail pruning (Sec. 3.1: a type-(a) node's region is held by at least two
+// levels; Sec. 3.3: the descent may stop there when the coarser cells project small
+// enough).  For the segment starting at t0 the bound is X = lod_scale * t0 (a pixel's
+// footprint at t0 times the threshold in pixels), and the descent stops at the first inner
+// node whose label level l has min_a h^l_a <= X, i.e. l >= lod_min: the smallest such
+// level, or kNoLod when pruning is off or no level qualifies.
+constexpr int kNoLod = 1 << 20;
+
+static __device__ __noinline__ int lod_min_exact(const RayArgs& R, const DLevel* lv, int px,
+                                                 int py, int pid0) {
+  RayX r;
+  make_ray(R, px, py, r);
+  const double X = __dmul_rn(R.lod_scale, exact_t(R, r, pid0));
+  for (int l = 0; l < R.levels; ++l)
+    if (lv[l].hmin_d <= X) return l;
+  return kNoLod;
+}
+
+// FP32 filter: t0 ~ t_in + tau0 within e0 and a few roundings; a level within the bound of
+// X is decided on the exact FP64 values.
+__device__ __forceinline__ int lod_min_level(const RayArgs& R, const DLevel* lv, const RayF& rf,
+                                             int px, int py, int pid0, float tau0, float e0) {
+  if (!(R.lod_scale_f > 0.0f)) return kNoLod;
+  const float t0 = rf.t_in + tau0;
+  const float X = R.lod_scale_f * t0;
+  const float eX = R.lod_scale_f * (e0 + ldexpf(rf.t_in + fabsf(t0) + 1.0f, -22)) + ldexpf(X, -21);
+  for (int l = 0; l < R.levels; ++l) {
+    const float hm = lv[l].hmin, eh = ldexpf(hm, -22);
+    if (hm + eh < X - eX) return l;  // certainly h <= X
+    if (hm - eh > X + eX) continue;  // certainly h > X
+    return lod_min_exact(R, lv, px, py, pid0);
+  }
+  return kNoLod;
+}
+
+// Pruned leaf of inner node i for bound lod_min, or -1.
+__device__ __forceinline__ int lod_stop(const RayArgs& R, uint32_t i, int lod_min) {
+  if (lod_min >= kNoLod) return -1;
+  const int q = __ldg(R.lod + i);
+  return (q >= 0 && (q & 31) >= lod_min) ? (q >> 5) : -1;
 }
 
 // kd-restart descent (Sec. 3.3) for the segment starting at (pid0, tau0): returns the leaf
@@ -217,7 +261,8 @@ __device__ __forceinline__ void make_frame(const RayArgs& A, const RayX& r, RayF
 // and the same t1 bit for bit.
 __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const RayArgs& A, int px,
                                        int py, const RayF& rf, uint32_t& start, int pid0,
-                                       float tau0, float e0, int& pid1, float& tau1, float& e1) {
+                                       float tau0, float e0, int& pid1, float& tau1, float& e1,
+                                       int lod_min = kNoLod) {
   uint32_t i = start;
   bool pushing = true;  // no narrowing yet: the chosen child still holds all of [t0, t_out]
   for (int depth = 0; depth < kMaxDepth; ++depth) {
@@ -225,6 +270,8 @@ __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const Ra
     const uint32_t ax = nd.meta >> 30;
     const uint32_t idx = nd.meta & kIndexMask;
     if (ax == kLeafAxis) return (int)idx;
+    const int pruned = lod_stop(A, i, lod_min);
+    if (pruned >= 0) return pruned;
     const float B = sel3f(ax, rf.B[0], rf.B[1], rf.B[2]);
     if (B == 0.0f) {  // ray parallel to the plane: the origin's (eye's) side, exactly
       const double o = sel3(ax, A.eye[0], A.eye[1], A.eye[2]);
@@ -273,15 +320,18 @@ __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const Ra
   return -1;
 }
 
-// Point location by integer finest-cell coordinates (left iff f_a < split).
-__device__ __forceinline__ int locate_cell(const DNode* __restrict__ nodes, int f0, int f1,
-                                           int f2) {
+// Point location by integer finest-cell coordinates (left iff f_a < split), stopping at a
+// pruned node when lod_min says so.
+__device__ __forceinline__ int locate_cell(const DNode* __restrict__ nodes, const RayArgs& R,
+                                           int lod_min, int f0, int f1, int f2) {
   uint32_t i = 0;
   for (int depth = 0; depth < kMaxDepth; ++depth) {
     const DNode nd = nodes[i];
     const uint32_t ax = nd.meta >> 30;
     const uint32_t idx = nd.meta & kIndexMask;
     if (ax == kLeafAxis) return (int)idx;
+    const int pruned = lod_stop(R, i, lod_min);
+    if (pruned >= 0) return pruned;
     i = idx + (sel3i(ax, f0, f1, f2) < nd.split ? 0u : 1u);
   }
   return -1;
@@ -424,6 +474,7 @@ struct SegState {
   float margin;       // bound on |FP32 beta - beta of the exact FP64 sample position|
   int pid0, pid1, n;  // exact segment: t0, t1 by plane id, n samples
   int px, py;         // pixel (the exact paths rebuild its ray)
+  int lod_min;        // pruning bound of the segment (gradient neighbours use the same)
 };
 
 // finest cell of an exact point, clamped into the root (the reference's rule)
@@ -445,7 +496,7 @@ __device__ __forceinline__ int nearest_index_exact(const RayArgs& A, const DLeve
 // the decision to FP64.  Takes scalars only, so the caller keeps its state in registers.
 template <int ST, int INTERP>
 __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs& R, int px, int py,
-                                             int leaf,
+                                             int leaf, int lod_min,
                                              int pid0, int pid1, int n, int k, float margin,
                                              float bn0, float bn1, float bn2, int a, float sign) {
   const DLeaf cl = A.leaves[leaf];
@@ -469,6 +520,11 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs&
       lid = (int)idx;
       break;
     }
+    const int pruned = lod_stop(R, i, lod_min);
+    if (pruned >= 0) {
+      lid = pruned;
+      break;
+    }
     const float diff = sel3f(ax, xr[0], xr[1], xr[2]) -
                        (float)(nd.split - sel3i(ax, cl.lo[0], cl.lo[1], cl.lo[2]));
     if (fabsf(diff) <= mf) {
@@ -490,7 +546,8 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs&
   };
   if (amb) {
     exact_point();
-    lid = locate_cell(A.nodes, finest_cell_exact(R, xe[0], 0), finest_cell_exact(R, xe[1], 1),
+    lid = locate_cell(A.nodes, R, lod_min, finest_cell_exact(R, xe[0], 0),
+                      finest_cell_exact(R, xe[1], 1),
                       finest_cell_exact(R, xe[2], 2));
   }
   if (lid < 0) return 0.0f;
@@ -561,8 +618,8 @@ __device__ __forceinline__ float neighbour_value(const RenderArgs& A, const RayA
         return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
     }
   }
-  return neighbour_slow<ST, INTERP>(A, R, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k, s.margin,
-                                    bn[0], bn[1], bn[2], AX, (float)SG);
+  return neighbour_slow<ST, INTERP>(A, R, s.px, s.py, s.leaf, s.lod_min, s.pid0, s.pid1, s.n, k,
+                                    s.margin, bn[0], bn[1], bn[2], AX, (float)SG);
 }
 
 // Value at the sample itself (the segment's own leaf and level, Sec. 3.3).
@@ -732,8 +789,10 @@ struct SegSetup {
 __device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& rf, const DLeaf& lf,
                                               const DLevel& lv, int lid, int pid0, int pid1,
                                               float tau0, float e0, float tau1, float e1, int n,
-                                              int px, int py, SegSetup& g) {
+                                              int px, int py, SegSetup& g,
+                                              int lod_min = kNoLod) {
   SegState& s = g.s;
+  s.lod_min = lod_min;
   s.brick = load_brick(A.patches, lf.patch);
   s.level = lf.level;
   s.leaf = lid;
@@ -865,7 +924,8 @@ __device__ __forceinline__ float4 march_ray(const RenderArgs& A, const RayArgs& 
       ++seg;
       int pid1 = kPidOut;
       float tau1 = rf.tau_out, e1 = rf.e_out;
-      const int lid = descend(A.nodes, R, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
+      const int lmin = lod_min_level(R, A.lv, rf, i, j, pid0, tau0, e0);
+      const int lid = descend(A.nodes, R, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1, lmin);
       if (lid < 0) {
         status |= kStatusDevice;
         break;
@@ -884,7 +944,7 @@ __device__ __forceinline__ float4 march_ray(const RenderArgs& A, const RayArgs& 
         continue;
       }
       SegSetup g;
-      setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
+      setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g, lmin);
       if (sample_segment<ST, INTERP, SHADE>(A, R, s_tf, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
         pid1 = kPidOut;  // early ray termination
       pid0 = pid1;

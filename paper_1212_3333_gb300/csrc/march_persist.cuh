@@ -131,8 +131,9 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
           ++seg;
           int pid1 = kPidOut;
           float tau1 = rf.tau_out, e1 = rf.e_out;
+          const int lmin = lod_min_level(R, A.lv, rf, i, R.row0 + jr, pid0, tau0, e0);
           const int lid = descend(A.nodes, R, i, R.row0 + jr, rf, start, pid0, tau0, e0, pid1,
-                                  tau1, e1);
+                                  tau1, e1, lmin);
           if (lid < 0) {
             status |= kStatusDevice;
             finish();
@@ -151,7 +152,8 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
             e0 = e1;
             continue;
           }
-          setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, R.row0 + jr, g);
+          setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, R.row0 + jr, g,
+                        lmin);
           k = 0;
           pid0 = pid1;  // where the next segment starts
           tau0 = tau1;

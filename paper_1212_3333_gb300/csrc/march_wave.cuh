@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
               bmax = fmaxf(bmax, fabsf(b0) + nfl * fabsf(db) + (float)s.brick.dim[a]);
             }
             s.margin = ex * lv.inv_sc + ldexpf(bmax + 2.0f, -21);
+            s.lod_min = kNoLod;  // this schedule renders without pruning
           }
           pid0 = pid1;
           tau0 = tau1;

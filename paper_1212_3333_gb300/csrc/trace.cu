@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
     }
     int pid1 = kPidOut;
     float tau1 = rf.tau_out, e1 = rf.e_out;
-    const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
+    const int lmin = lod_min_level(A.ray, A.lv, rf, i, j, pid0, tau0, e0);
+    const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1, lmin);
     if (lid < 0) {
       status |= kStatusDevice;
       break;

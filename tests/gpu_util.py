@@ -15,7 +15,8 @@ def params_pair(amr, vmin, vmax, **kw):
         setattr(p, k, v)
     o = oracle.OracleParams(vmin=float(vmin), vmax=float(vmax), step_factor=p.step_factor,
                             kappa=p.kappa, ert_eps=p.ert_eps, interp=p.interp, shade=p.shade,
-                            ka=p.ka, kd=p.kd, ks=p.ks, shininess=p.shininess, gamma=p.gamma)
+                            ka=p.ka, kd=p.kd, ks=p.ks, shininess=p.shininess, gamma=p.gamma,
+                            lod_pixels=p.lod_pixels)
     return p, o
 
 
@@ -30,14 +31,14 @@ def gpu_render(ctx, cam, tf, p, count_samples=True):
     return out.cpu().numpy().astype(np.float64), n
 
 
-def gpu_trace(ctx, cam, max_len=4096):
+def gpu_trace(ctx, cam, max_len=4096, lod_pixels=0.0):
     import torch
 
     npx = cam.width * cam.height
     seq = torch.full((npx * max_len,), -7, dtype=torch.int32, device="cuda")
     tseq = torch.zeros((npx * max_len * 2,), dtype=torch.float64, device="cuda")
     ln = torch.full((npx,), -7, dtype=torch.int32, device="cuda")
-    ctx.amr_trace(cam, seq, ln, max_len, t_seq=tseq)
+    ctx.amr_trace(cam, seq, ln, max_len, t_seq=tseq, lod_pixels=lod_pixels)
     torch.cuda.synchronize()
     return (seq.cpu().numpy().reshape(npx, max_len), tseq.cpu().numpy().reshape(npx, max_len, 2),
             ln.cpu().numpy())
