@@ -292,6 +292,37 @@ def precision_eval(amr, hier, vmin, vmax, cam, tf, out, args, peak):
     return res
 
 
+def lod_eval(amr, ctx, vmin, vmax, cam, tf, out, args, lods=(0.5, 1.0, 2.0, 4.0)):
+    """Level-of-detail pruning (Sec. 3.1 type-(a) nodes) on the bench view: samples, time
+    and PSNR against the unpruned image for a few thresholds (pixels)."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    base = dict(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
+
+    def run(prm):
+        n = ctx.amr_render(cam, tf, prm, out, count_samples=True)
+        ctx.amr_render(cam, tf, prm, out)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            ctx.amr_render(cam, tf, prm, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return n, a.elapsed_time(b) / 3, out.double().clone()
+
+    n0, ms0, ref = run(amr.amr_default_params(**base))
+    res = {"off": {"samples": n0, "ms": ms0, "gsamples_s": n0 / ms0 / 1e6}}
+    for lod in lods:
+        n, ms, img = run(amr.amr_default_params(**base, lod_pixels=lod))
+        mse = float(((img - ref) ** 2).mean())
+        res[f"{lod:g}px"] = {"samples": n, "ms": ms, "gsamples_s": n / ms / 1e6,
+                             "speedup": ms0 / ms,
+                             "psnr_vs_unpruned_db": float("inf") if mse == 0 else
+                             10 * math.log10(1 / mse)}
+    return res
+
+
 def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5, lo=256, hi=2048,
                tune_views=16):
     """Batched multi-view rendering: 64 seeded views with square sides uniform in
@@ -367,13 +398,19 @@ def c3_eval(amr, args, peak):
     h = synth.amr.make_c3(device="cuda")
     gen_s = time.perf_counter() - t0
     vmin, vmax = synth.amr.percentile_range(h)
-    precision = precision_eval(amr, h, vmin, vmax, synth.orbit_camera(3, SIZE, SIZE),
-                               torch.as_tensor(synth.ramp_tf(), device="cuda"),
-                               torch.empty((SIZE, SIZE, 4), dtype=torch.float32, device="cuda"),
-                               args, peak)
+    cam = synth.orbit_camera(3, SIZE, SIZE)
+    tf = torch.as_tensor(synth.ramp_tf(), device="cuda")
+    out = torch.empty((SIZE, SIZE, 4), dtype=torch.float32, device="cuda")
+    precision = precision_eval(amr, h, vmin, vmax, cam, tf, out, args, peak)
+    ctx = amr.from_hierarchy(h)
+    ctx.amr_build_kdtree("ptr", gradient=True)
+    lod = lod_eval(amr, ctx, vmin, vmax, cam, tf, out, args)
+    st = ctx.amr_get_stats()
+    ctx.amr_destroy()
     return {"patches": h.num_patches, "patches_per_level": h.patches_per_level(),
             "cells": h.n_cells(), "levels": h.num_levels, "generate_s": gen_s,
-            "precision": precision}
+            "tree": {"nodes": st.num_nodes, "leaves": st.num_leaves, "depth": st.max_depth},
+            "precision": precision, "lod": lod}
 
 
 def run_reference(args):
@@ -438,6 +475,7 @@ def main():
     ap.add_argument("--learned", type=int, default=1, help="evaluate the learned proposal")
     ap.add_argument("--precision", type=int, default=1, help="time FP16 / BF16 cell storage")
     ap.add_argument("--batch", type=int, default=1, help="time 64-view batched rendering")
+    ap.add_argument("--lod", type=int, default=1, help="time level-of-detail pruning")
     ap.add_argument("--c3", type=int, default=0,
                     help="also render the deep 8-level hierarchy (~1e9 cells; minutes)")
     ap.add_argument("--log-size", type=int, default=96)
@@ -575,6 +613,8 @@ def main():
                                   "efficiency_with_halo": s2.atlas_efficiency_halo}
             c2.amr_destroy()
         extra["storages"] = comp
+    if args.lod and world == 1:
+        extra["lod"] = lod_eval(amr, ctx, vmin, vmax, cam, tf, out, args)
     if args.precision and world == 1:
         extra["precision"] = precision_eval(amr, hier, vmin, vmax, cam, tf, out, args, peak)
     if args.batch and world == 1 and args.storage == "ptr" and args.dtype == "f32":
