@@ -81,7 +81,7 @@ struct RayArgs {
   // (pruned-leaf id << 5 | level) or -1; X(t) = lod_scale * t bounds the cell size at
   // which the descent stops; lod_scale == 0 turns pruning off
   const int32_t* lod;
-  int32_t levels;
+  int32_t levels;       // 1 + the finest level of a type-(a) node (0: none)
   double lod_scale;
   float lod_scale_f;
 };

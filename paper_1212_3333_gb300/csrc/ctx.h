@@ -28,6 +28,7 @@ struct Tree {
   // rendered as leaves of that patch's level; they take ids M, M+1, ... in pre-order
   std::vector<int32_t> node_lod;                        // per node, pre-order: id or -1
   std::vector<int32_t> lod_box, lod_patch, lod_level;   // per pruned leaf
+  int lod_levels = 0;  // 1 + the finest level of a pruned leaf (0: none)
   int max_depth = 0;
 };
 

@@ -287,6 +287,7 @@ class Builder {
     t.lod_box.clear();
     t.lod_patch.clear();
     t.lod_level.clear();
+    t.lod_levels = 0;
     const int32_t M = (int32_t)t.leaf_patch.size();
     for (size_t k = 0; k < n; ++k) {
       const BNode& b = nodes_[order[k]];
@@ -295,6 +296,7 @@ class Builder {
       for (int q = 0; q < 6; ++q) t.lod_box.push_back((int32_t)b.box[q]);
       t.lod_patch.push_back(b.patch);
       t.lod_level.push_back(b.level);
+      t.lod_levels = std::max(t.lod_levels, b.level + 1);
     }
     if (t.max_depth >= kMaxDepth)
       return fail(c_, AMR_ERR_CAPACITY, "kD-tree deeper than the device descent bound");

@@ -258,7 +258,9 @@ __device__ __forceinline__ int lod_stop(const RayArgs& R, uint32_t i, int lod_mi
 // before any narrowing, i.e. a node whose box holds the whole remaining ray [t0, t_out].
 // Every later restart takes the same one-sided decisions above it (t0 only grows and t1
 // is t_out there), so restarting at `start` instead of the root yields the same leaves
-// and the same t1 bit for bit.
+// and the same t1 bit for bit.  With level-of-detail pruning on, `start` stays at or above
+// every type-(a) node on the path: the pruning bound grows with t0, so a later segment
+// may stop at an ancestor that this one passed.
 __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const RayArgs& A, int px,
                                        int py, const RayF& rf, uint32_t& start, int pid0,
                                        float tau0, float e0, int& pid1, float& tau1, float& e1,
@@ -270,8 +272,11 @@ __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const Ra
     const uint32_t ax = nd.meta >> 30;
     const uint32_t idx = nd.meta & kIndexMask;
     if (ax == kLeafAxis) return (int)idx;
-    const int pruned = lod_stop(A, i, lod_min);
-    if (pruned >= 0) return pruned;
+    // type-(a) node (pruning on for this ray): stop here if its level is coarse enough;
+    // never push the restart below it, since a later segment may stop at it
+    const int q = A.lod_scale_f > 0.0f ? __ldg(A.lod + i) : -1;
+    if (q >= 0 && (q & 31) >= lod_min) return q >> 5;
+    pushing = pushing && q < 0;
     const float B = sel3f(ax, rf.B[0], rf.B[1], rf.B[2]);
     if (B == 0.0f) {  // ray parallel to the plane: the origin's (eye's) side, exactly
       const double o = sel3(ax, A.eye[0], A.eye[1], A.eye[2]);
