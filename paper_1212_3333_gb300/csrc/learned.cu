@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(128) log_kernel(const __grid_constant__ Render
   uint32_t start = 0;
   for (int seg = 0; pid0 != kPidOut && seg < A.max_segments; ++seg) {
     int pid1 = kPidOut;
-    float tau1 = rf.tau_out, e1 = rf.e_out;
+    float tau1 = rf.tau_out, e1 = exit_bound(rf);
     const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
     if (lid < 0) break;
     const DLeaf lf = A.leaves[lid];
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
       } else {
         ++nseg;
         tau1 = rf.tau_out;
-        e1 = rf.e_out;
+        e1 = exit_bound(rf);
         lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;

@@ -61,7 +61,7 @@ struct RayF {
   float B[3], C[3];      // leading parts
   float Bl[3], Cl[3];    // trailing parts (B = B + Bl, C = C + Cl to ~2^-48)
   float Xe[3], Dd[3];
-  float tau_out, e_out;
+  float tau_out;         // t_out - t_in (its bound: exit_bound)
   float dn;
   float t_in;            // root entry parameter (level-of-detail distance)
   int exact_axes;        // bit a set: planes on axis a are always decided in FP64
@@ -203,8 +203,10 @@ __device__ __forceinline__ void make_frame(const RayArgs& A, const RayX& r, RayF
   const double tau_out = r.t_out - r.t_in;
   f.tau_out = (float)tau_out;
   f.t_in = (float)r.t_in;
-  f.e_out = ldexpf(f.tau_out + 1.0f, -22);
 }
+
+// error bound of tau_out (recomputed where needed instead of held per ray)
+__device__ __forceinline__ float exit_bound(const RayF& f) { return ldexpf(f.tau_out + 1.0f, -22); }
 
 // Level-of-detail pruning (Sec. 3.1: a type-(a) node's region is held by at least two
 // levels; Sec. 3.3: the descent may stop there when the coarser cells project small
@@ -473,14 +475,25 @@ __device__ __forceinline__ float cell_at(const RenderArgs& A, const BrickRef& b,
 struct SegState {
   BrickRef brick;
   int level;
-  int leaf;
+  int leaf;           // leaf id (bits 0..25) and the segment's pruning bound (26..31; 63: none)
   int leaf_lo[3];     // finest cells
   float bl[3], bh[3]; // leaf box in brick coordinates
   float margin;       // bound on |FP32 beta - beta of the exact FP64 sample position|
   int pid0, pid1, n;  // exact segment: t0, t1 by plane id, n samples
   int px, py;         // pixel (the exact paths rebuild its ray)
-  int lod_min;        // pruning bound of the segment (gradient neighbours use the same)
 };
+
+// SegState.leaf packing: the pruning bound rides in the top bits of the leaf id
+constexpr uint32_t kLeafBits = 26, kLeafMask = (1u << kLeafBits) - 1u, kLodNone = 63u;
+__device__ __forceinline__ int pack_leaf(int leaf, int lod_min) {
+  const uint32_t l = lod_min >= kNoLod ? kLodNone : (uint32_t)lod_min;
+  return (int)(((uint32_t)leaf & kLeafMask) | (l << kLeafBits));
+}
+__device__ __forceinline__ int leaf_of(int packed) { return (int)((uint32_t)packed & kLeafMask); }
+__device__ __forceinline__ int lod_of(int packed) {
+  const uint32_t l = (uint32_t)packed >> kLeafBits;
+  return l == kLodNone ? kNoLod : (int)l;
+}
 
 // finest cell of an exact point, clamped into the root (the reference's rule)
 __device__ __forceinline__ int finest_cell_exact(const RayArgs& A, double x, int a) {
@@ -501,9 +514,10 @@ __device__ __forceinline__ int nearest_index_exact(const RayArgs& A, const DLeve
 // the decision to FP64.  Takes scalars only, so the caller keeps its state in registers.
 template <int ST, int INTERP>
 __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs& R, int px, int py,
-                                             int leaf, int lod_min,
+                                             int leaf_lod,
                                              int pid0, int pid1, int n, int k, float margin,
                                              float bn0, float bn1, float bn2, int a, float sign) {
+  const int leaf = leaf_of(leaf_lod), lod_min = lod_of(leaf_lod);
   const DLeaf cl = A.leaves[leaf];
   const DLevel& lv = A.lv[cl.level];
   const BrickRef cb = load_brick(A.patches, cl.patch);
@@ -623,7 +637,7 @@ __device__ __forceinline__ float neighbour_value(const RenderArgs& A, const RayA
         return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
     }
   }
-  return neighbour_slow<ST, INTERP>(A, R, s.px, s.py, s.leaf, s.lod_min, s.pid0, s.pid1, s.n, k,
+  return neighbour_slow<ST, INTERP>(A, R, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k,
                                     s.margin, bn[0], bn[1], bn[2], AX, (float)SG);
 }
 
@@ -639,7 +653,7 @@ __device__ __forceinline__ float sample_value(const RenderArgs& A, const RayArgs
     const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
     if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > s.margin)
       return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
-    return nearest_sample_exact<ST>(A, R, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k);
+    return nearest_sample_exact<ST>(A, R, s.px, s.py, leaf_of(s.leaf), s.pid0, s.pid1, s.n, k);
   }
 }
 
@@ -797,10 +811,9 @@ __device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& r
                                               int px, int py, SegSetup& g,
                                               int lod_min = kNoLod) {
   SegState& s = g.s;
-  s.lod_min = lod_min;
   s.brick = load_brick(A.patches, lf.patch);
   s.level = lf.level;
-  s.leaf = lid;
+  s.leaf = pack_leaf(lid, lod_min);
   s.pid0 = pid0;
   s.pid1 = pid1;
   s.n = n;
@@ -928,7 +941,7 @@ __device__ __forceinline__ float4 march_ray(const RenderArgs& A, const RayArgs& 
       }
       ++seg;
       int pid1 = kPidOut;
-      float tau1 = rf.tau_out, e1 = rf.e_out;
+      float tau1 = rf.tau_out, e1 = exit_bound(rf);
       const int lmin = lod_min_level(R, A.lv, rf, i, j, pid0, tau0, e0);
       const int lid = descend(A.nodes, R, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1, lmin);
       if (lid < 0) {

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
           }
           ++seg;
           int pid1 = kPidOut;
-          float tau1 = rf.tau_out, e1 = rf.e_out;
+          float tau1 = rf.tau_out, e1 = exit_bound(rf);
           const int lmin = lod_min_level(R, A.lv, rf, i, R.row0 + jr, pid0, tau0, e0);
           const int lid = descend(A.nodes, R, i, R.row0 + jr, rf, start, pid0, tau0, e0, pid1,
                                   tau1, e1, lmin);

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
       } else {
         ++nseg;
         int pid1 = kPidOut;
-        float tau1 = rf.tau_out, e1 = rf.e_out;
+        float tau1 = rf.tau_out, e1 = exit_bound(rf);
         const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
             SegState& s = ws.s;
             s.brick = load_brick(A.patches, lf.patch);
             s.level = lf.level;
-            s.leaf = lid;
+            s.leaf = pack_leaf(lid, kNoLod);
             s.pid0 = pid0;
             s.pid1 = pid1;
             s.n = n;
@@ -158,7 +158,6 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
               bmax = fmaxf(bmax, fabsf(b0) + nfl * fabsf(db) + (float)s.brick.dim[a]);
             }
             s.margin = ex * lv.inv_sc + ldexpf(bmax + 2.0f, -21);
-            s.lod_min = kNoLod;  // this schedule renders without pruning
           }
           pid0 = pid1;
           tau0 = tau1;
