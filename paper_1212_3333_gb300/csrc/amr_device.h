@@ -41,7 +41,9 @@ struct DLeaf {
   int32_t patch;
   int32_t level;
   float vmin, vmax;      // range of every value a sample of this leaf can interpolate
-  int32_t pad[2];
+  int32_t faces;         // bit 2a (+1): the level cell beyond the lower (upper) face on axis
+                         // a lies in the same patch and is not refined
+  int32_t pad;
 };
 
 struct DPatch {

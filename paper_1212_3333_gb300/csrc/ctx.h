@@ -24,6 +24,7 @@ struct Tree {
   std::vector<int32_t> axis, split, left, right, leaf;  // per node, pre-order
   std::vector<int32_t> leaf_box;                        // 6 per leaf, finest cells
   std::vector<int32_t> leaf_patch, leaf_level;
+  std::vector<uint8_t> leaf_faces;  // per leaf: DLeaf::faces
   // level-of-detail: inner nodes whose box lies in one patch (Sec. 3.1 type (a)) may be
   // rendered as leaves of that patch's level; they take ids M, M+1, ... in pre-order
   std::vector<int32_t> node_lod;                        // per node, pre-order: id or -1

@@ -223,6 +223,7 @@ amr_status upload(amr_ctx* c, void* stream_v) {
     for (int k = 0; k < 6; ++k) (k < 3 ? l.lo[k] : l.hi[k - 3]) = box[k];
     l.patch = lod ? t.lod_patch[m - M] : t.leaf_patch[m];
     l.level = lod ? t.lod_level[m - M] : t.leaf_level[m];
+    l.faces = (lod || t.leaf_faces.empty()) ? 0 : t.leaf_faces[m];
     // the range of the cells as stored; rounding is monotone, so the rounded extremes
     // bound every rounded cell and empty-space skipping stays exact
     l.vmin = storage_round(c->dtype, c->leaf_vmin[m]);

@@ -133,6 +133,13 @@ class Builder {
     if (q[3 + a] > s) collect(nodes_[i].right, q, patch, slot, lists, owners);
   }
 
+  // every leaf overlapping box q belongs to patch p
+  bool same_patch(int i, const int64_t* q, int p) const {
+    if (!intersect(nodes_[i].box, q, nullptr)) return true;
+    if (nodes_[i].axis < 0) return nodes_[i].patch == p;
+    return same_patch(nodes_[i].left, q, p) && same_patch(nodes_[i].right, q, p);
+  }
+
   static void offer(Candidate& best, int64_t cost, int64_t bal, int axis, int64_t s) {
     if (!best.valid || cost < best.cost || (cost == best.cost && bal < best.bal)) {
       best.valid = true;
@@ -280,6 +287,33 @@ class Builder {
         t.left[k] = pre[b.left];
         t.right[k] = pre[b.right];
       }
+    }
+    // same-patch faces: the slab of one level cell beyond a leaf face that lies inside the
+    // leaf's patch and overlaps only leaves of that patch (so gradient neighbours there read
+    // the leaf's own brick)
+    t.leaf_faces.assign(t.leaf_patch.size(), 0);
+    for (size_t k = 0; k < n; ++k) {
+      const BNode& b = nodes_[order[k]];
+      if (b.axis >= 0) continue;
+      const Patch& pt = c_->patches[b.patch];
+      const int64_t sc = c_->rpow[c_->L - 1 - b.level];
+      uint8_t f = 0;
+      for (int a = 0; a < 3; ++a)
+        for (int side = 0; side < 2; ++side) {
+          int64_t q[6];
+          std::memcpy(q, b.box, sizeof q);
+          if (side == 0) {
+            q[3 + a] = b.box[a];
+            q[a] = b.box[a] - sc;
+            if (q[a] < pt.fbox[a]) continue;
+          } else {
+            q[a] = b.box[3 + a];
+            q[3 + a] = b.box[3 + a] + sc;
+            if (q[3 + a] > pt.fbox[3 + a]) continue;
+          }
+          if (same_patch(0, q, b.patch)) f |= (uint8_t)(1u << (2 * a + side));
+        }
+      t.leaf_faces[(size_t)t.leaf[k]] = f;
     }
     // inner nodes lying in one patch (labelled when they were still leaves) can stand in
     // for their subtree at that patch's level: ids after the leaves, in pre-order

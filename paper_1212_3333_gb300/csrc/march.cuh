@@ -531,6 +531,7 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs&
   bool amb = false;
   uint32_t i = 0;
   int lid = -1;
+  const bool pruning = lod_min < kNoLod;
   for (int depth = 0; depth < kMaxDepth; ++depth) {
     const DNode nd = A.nodes[i];
     const uint32_t ax = nd.meta >> 30;
@@ -539,10 +540,12 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs&
       lid = (int)idx;
       break;
     }
-    const int pruned = lod_stop(R, i, lod_min);
-    if (pruned >= 0) {
-      lid = pruned;
-      break;
+    if (pruning) {
+      const int pruned = lod_stop(R, i, lod_min);
+      if (pruned >= 0) {
+        lid = pruned;
+        break;
+      }
     }
     const float diff = sel3f(ax, xr[0], xr[1], xr[2]) -
                        (float)(nd.split - sel3i(ax, cl.lo[0], cl.lo[1], cl.lo[2]));
@@ -834,6 +837,12 @@ __device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& r
     s.leaf_lo[a] = lf.lo[a];
     s.bl[a] = (float)(lf.lo[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
     s.bh[a] = (float)(lf.hi[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
+    // a same-patch face widens the region whose neighbours read this brick by one cell
+    // (not under pruning: the pruned field may stop above the neighbouring leaf)
+    if (lod_min >= kNoLod) {
+      if ((lf.faces >> (2 * a)) & 1) s.bl[a] -= 1.0f;
+      if ((lf.faces >> (2 * a + 1)) & 1) s.bh[a] += 1.0f;
+    }
     const float ea = fabsf(rf.Dd[a]) * etau +
                      ldexpf(fabsf(rf.Xe[a]) + fabsf(xm) + nfl * fabsf(dtau * rf.Dd[a]) + 1.0f, -21);
     ex = fmaxf(ex, ea);
