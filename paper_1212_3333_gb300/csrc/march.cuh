@@ -837,9 +837,10 @@ __device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& r
     s.leaf_lo[a] = lf.lo[a];
     s.bl[a] = (float)(lf.lo[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
     s.bh[a] = (float)(lf.hi[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
-    // a same-patch face widens the region whose neighbours read this brick by one cell
-    // (not under pruning: the pruned field may stop above the neighbouring leaf)
-    if (lod_min >= kNoLod) {
+    // a same-patch face widens the region whose neighbours read this brick by one cell.
+    // Under pruning only when the bound is finer than this leaf's level: then no node the
+    // pruned descent could stop at overlaps the (level-l) cells beyond the face
+    if (lod_min > lf.level) {
       if ((lf.faces >> (2 * a)) & 1) s.bl[a] -= 1.0f;
       if ((lf.faces >> (2 * a + 1)) & 1) s.bh[a] += 1.0f;
     }
