@@ -308,6 +308,7 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   fill_levels(c, a->lv, p->step_factor);
   a->nodes = c->dev.nodes;
   a->leaves = c->dev.leaves;
+  a->face_node = c->dev.face_node;
   a->patches = c->dev.patches;
   a->pool = c->dev.pool;
   a->gpool = (const float4*)c->dev.gpool;

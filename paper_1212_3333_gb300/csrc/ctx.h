@@ -25,6 +25,8 @@ struct Tree {
   std::vector<int32_t> leaf_box;                        // 6 per leaf, finest cells
   std::vector<int32_t> leaf_patch, leaf_level;
   std::vector<uint8_t> leaf_faces;  // per leaf: DLeaf::faces
+  std::vector<int32_t> face_node;   // per leaf and face (2a + side): pre-order id of the
+                                    // deepest node holding the level cell beyond that face
   // level-of-detail: inner nodes whose box lies in one patch (Sec. 3.1 type (a)) may be
   // rendered as leaves of that patch's level; they take ids M, M+1, ... in pre-order
   std::vector<int32_t> node_lod;                        // per node, pre-order: id or -1
@@ -61,6 +63,7 @@ struct DeviceState {
   unsigned char* proposal = nullptr;             // packed MLP weights (amr_set_proposal)
   size_t img_scratch_bytes = 0;
   int32_t* lod = nullptr;                        // per node slot: (id << 5 | level) or -1
+  int32_t* face_node = nullptr;                  // per leaf and face: node slot (neighbour start)
   int device = -1;
 };
 

@@ -20,16 +20,19 @@ namespace {
 
 // breadth-first re-layout: children of a node are adjacent, the top levels contiguous;
 // lod receives each slot's pruned-leaf entry (id << 5 | level) or -1
-std::vector<DNode> layout_nodes(const Tree& t, std::vector<int32_t>& lod) {
+std::vector<DNode> layout_nodes(const Tree& t, std::vector<int32_t>& lod,
+                                std::vector<int32_t>& slot_of) {
   const size_t n = t.axis.size();
   std::vector<DNode> out(n);
   lod.assign(n, -1);
+  slot_of.assign(n, 0);
   std::deque<std::pair<int, int>> q;  // (pre-order id, bfs slot)
   q.push_back({0, 0});
   int next = 1;
   while (!q.empty()) {
     auto [pre, slot] = q.front();
     q.pop_front();
+    slot_of[pre] = slot;
     DNode d;
     if (t.axis[pre] < 0) {
       d.meta = ((uint32_t)kLeafAxis << 30) | ((uint32_t)t.leaf[pre] & kIndexMask);
@@ -189,6 +192,7 @@ void release_device(amr_ctx* c) {
   cudaFree(d.gpool);
   cudaFree(d.nodes);
   cudaFree(d.lod);
+  cudaFree(d.face_node);
   cudaFree(d.leaves);
   cudaFree(d.patches);
   cudaFree(d.pool);
@@ -210,8 +214,10 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   const size_t M = t.leaf_patch.size();
   if (t.axis.size() >= (size_t)kIndexMask || M >= (size_t)kIndexMask)
     return fail(c, AMR_ERR_CAPACITY, "tree too large for 30-bit node indices");
-  std::vector<int32_t> lodv;
-  std::vector<DNode> nodes = layout_nodes(t, lodv);
+  std::vector<int32_t> lodv, slot_of;
+  std::vector<DNode> nodes = layout_nodes(t, lodv, slot_of);
+  std::vector<int32_t> face_slots(std::max<size_t>(1, t.face_node.size()), 0);
+  for (size_t k = 0; k < t.face_node.size(); ++k) face_slots[k] = slot_of[t.face_node[k]];
   const size_t ML = t.lod_patch.size();
   if (M + ML >= ((size_t)1 << 26)) return fail(c, AMR_ERR_CAPACITY, "too many leaves");
   std::vector<DLeaf> leaves(M + ML);
@@ -239,6 +245,7 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   }
   CK(cudaMalloc(&d.nodes, nodes.size() * sizeof(DNode)));
   CK(cudaMalloc(&d.lod, lodv.size() * sizeof(int32_t)));
+  CK(cudaMalloc(&d.face_node, face_slots.size() * sizeof(int32_t)));
   CK(cudaMalloc(&d.leaves, std::max<size_t>(1, M + ML) * sizeof(DLeaf)));
   CK(cudaMalloc(&d.patches, P * sizeof(DPatch)));
   CK(cudaMalloc(&d.counters, kNumCounters * sizeof(unsigned long long)));
@@ -281,6 +288,8 @@ amr_status upload(amr_ctx* c, void* stream_v) {
                      stream));
   CK(cudaMemcpyAsync(d.lod, lodv.data(), lodv.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                      stream));
+  CK(cudaMemcpyAsync(d.face_node, face_slots.data(), face_slots.size() * sizeof(int32_t),
+                     cudaMemcpyHostToDevice, stream));
   if (M + ML)
     CK(cudaMemcpyAsync(d.leaves, leaves.data(), (M + ML) * sizeof(DLeaf), cudaMemcpyHostToDevice,
                        stream));

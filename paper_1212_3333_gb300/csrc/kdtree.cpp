@@ -292,6 +292,9 @@ class Builder {
     // leaf's patch and overlaps only leaves of that patch (so gradient neighbours there read
     // the leaf's own brick)
     t.leaf_faces.assign(t.leaf_patch.size(), 0);
+    t.face_node.assign(6 * t.leaf_patch.size(), 0);
+    std::vector<int> node2pre(n);
+    for (size_t k = 0; k < n; ++k) node2pre[order[k]] = (int)k;
     for (size_t k = 0; k < n; ++k) {
       const BNode& b = nodes_[order[k]];
       if (b.axis >= 0) continue;
@@ -305,12 +308,30 @@ class Builder {
           if (side == 0) {
             q[3 + a] = b.box[a];
             q[a] = b.box[a] - sc;
-            if (q[a] < pt.fbox[a]) continue;
           } else {
             q[a] = b.box[3 + a];
             q[3 + a] = b.box[3 + a] + sc;
-            if (q[3 + a] > pt.fbox[3 + a]) continue;
           }
+          // deepest node holding the slab (clipped to the root: points beyond it descend
+          // like their clamped positions)
+          int64_t qc[6];
+          for (int r = 0; r < 3; ++r) {
+            qc[r] = std::max(q[r], c_->root[r]);
+            qc[3 + r] = std::min(q[3 + r], c_->root[3 + r]);
+          }
+          int i = 0;
+          if (qc[a] < qc[3 + a]) {
+            while (nodes_[i].axis >= 0) {
+              const int ax = nodes_[i].axis;
+              const int64_t sp = nodes_[i].split;
+              if (qc[3 + ax] <= sp) i = nodes_[i].left;
+              else if (qc[ax] >= sp) i = nodes_[i].right;
+              else break;
+            }
+          }
+          t.face_node[6 * (size_t)t.leaf[k] + 2 * a + side] = node2pre[i];
+          if ((side == 0 && q[a] < pt.fbox[a]) || (side == 1 && q[3 + a] > pt.fbox[3 + a]))
+            continue;
           if (same_patch(0, q, b.patch)) f |= (uint8_t)(1u << (2 * a + side));
         }
       t.leaf_faces[(size_t)t.leaf[k]] = f;

@@ -529,9 +529,11 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs&
   for (int q = 0; q < 3; ++q)
     xr[q] = (bn[q] - ((float)(cl.lo[q] - cb.lo[q] * lv.sc) * lv.inv_sc + 0.5f)) * scf;
   bool amb = false;
-  uint32_t i = 0;
   int lid = -1;
   const bool pruning = lod_min < kNoLod;
+  // the neighbour lies in the level cell beyond face (a, sign) of the leaf: start at the
+  // deepest node holding that cell (from the root under pruning, which may stop above it)
+  uint32_t i = pruning ? 0u : (uint32_t)__ldg(A.face_node + 6 * leaf + 2 * a + (sign > 0.0f ? 1 : 0));
   for (int depth = 0; depth < kMaxDepth; ++depth) {
     const DNode nd = A.nodes[i];
     const uint32_t ax = nd.meta >> 30;
