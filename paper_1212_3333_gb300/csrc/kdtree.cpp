@@ -312,15 +312,16 @@ class Builder {
             q[a] = b.box[3 + a];
             q[3 + a] = b.box[3 + a] + sc;
           }
-          // deepest node holding the slab (clipped to the root: points beyond it descend
-          // like their clamped positions)
+          // deepest node holding the leaf and the slab (clipped to the root: points beyond
+          // it descend like their clamped positions); a neighbour lookup may also land in
+          // the leaf itself, near its boundary
           int64_t qc[6];
           for (int r = 0; r < 3; ++r) {
-            qc[r] = std::max(q[r], c_->root[r]);
-            qc[3 + r] = std::min(q[3 + r], c_->root[3 + r]);
+            qc[r] = std::max(std::min(q[r], b.box[r]), c_->root[r]);
+            qc[3 + r] = std::min(std::max(q[3 + r], b.box[3 + r]), c_->root[3 + r]);
           }
           int i = 0;
-          if (qc[a] < qc[3 + a]) {
+          {
             while (nodes_[i].axis >= 0) {
               const int ax = nodes_[i].axis;
               const int64_t sp = nodes_[i].split;

@@ -531,8 +531,8 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs&
   bool amb = false;
   int lid = -1;
   const bool pruning = lod_min < kNoLod;
-  // the neighbour lies in the level cell beyond face (a, sign) of the leaf: start at the
-  // deepest node holding that cell (from the root under pruning, which may stop above it)
+  // the neighbour lies in the leaf or in the level cell beyond its face (a, sign): start at
+  // the deepest node holding both (from the root under pruning, which may stop above it)
   uint32_t i = pruning ? 0u : (uint32_t)__ldg(A.face_node + 6 * leaf + 2 * a + (sign > 0.0f ? 1 : 0));
   for (int depth = 0; depth < kMaxDepth; ++depth) {
     const DNode nd = A.nodes[i];
