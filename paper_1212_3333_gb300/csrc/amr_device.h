@@ -93,8 +93,9 @@ struct RenderArgs {
   DLevel lv[kMaxLevels];
   const DNode* nodes;
   const DLeaf* leaves;
-  const int32_t* face_node;    // per leaf and face (2a + side): node slot holding the leaf and
-                               // the cell beyond that face (start of neighbour lookups)
+  const int32_t* face_node;    // per leaf, 12: per face (2a + side) the node slot holding the
+                               // leaf and the cell beyond the face, then the cell alone
+                               // (starts of neighbour lookups)
   const DPatch* patches;
   const void* pool;            // linear atlas base (element type of the storage)
   const float4* gpool;         // linear atlas of gradient bricks (float4 per cell)

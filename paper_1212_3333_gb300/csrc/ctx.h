@@ -25,8 +25,9 @@ struct Tree {
   std::vector<int32_t> leaf_box;                        // 6 per leaf, finest cells
   std::vector<int32_t> leaf_patch, leaf_level;
   std::vector<uint8_t> leaf_faces;  // per leaf: DLeaf::faces
-  std::vector<int32_t> face_node;   // per leaf and face (2a + side): pre-order id of the
-                                    // deepest node holding the leaf and the cell beyond that face
+  std::vector<int32_t> face_node;   // per leaf, 12: for each face (2a + side) the pre-order id
+                                    // of the deepest node holding the leaf and the cell beyond
+                                    // that face, then of the one holding that cell alone
   // level-of-detail: inner nodes whose box lies in one patch (Sec. 3.1 type (a)) may be
   // rendered as leaves of that patch's level; they take ids M, M+1, ... in pre-order
   std::vector<int32_t> node_lod;                        // per node, pre-order: id or -1

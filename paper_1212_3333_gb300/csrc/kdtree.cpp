@@ -292,7 +292,7 @@ class Builder {
     // leaf's patch and overlaps only leaves of that patch (so gradient neighbours there read
     // the leaf's own brick)
     t.leaf_faces.assign(t.leaf_patch.size(), 0);
-    t.face_node.assign(6 * t.leaf_patch.size(), 0);
+    t.face_node.assign(12 * t.leaf_patch.size(), 0);
     std::vector<int> node2pre(n);
     for (size_t k = 0; k < n; ++k) node2pre[order[k]] = (int)k;
     for (size_t k = 0; k < n; ++k) {
@@ -315,22 +315,27 @@ class Builder {
           // deepest node holding the leaf and the slab (clipped to the root: points beyond
           // it descend like their clamped positions); a neighbour lookup may also land in
           // the leaf itself, near its boundary
-          int64_t qc[6];
-          for (int r = 0; r < 3; ++r) {
-            qc[r] = std::max(std::min(q[r], b.box[r]), c_->root[r]);
-            qc[3 + r] = std::min(std::max(q[3 + r], b.box[3 + r]), c_->root[3 + r]);
-          }
-          int i = 0;
-          {
-            while (nodes_[i].axis >= 0) {
-              const int ax = nodes_[i].axis;
-              const int64_t sp = nodes_[i].split;
-              if (qc[3 + ax] <= sp) i = nodes_[i].left;
-              else if (qc[ax] >= sp) i = nodes_[i].right;
-              else break;
+          // (second: the slab alone, for a neighbour known to lie beyond the face)
+          for (int only_slab = 0; only_slab < 2; ++only_slab) {
+            int64_t qc[6];
+            for (int r = 0; r < 3; ++r) {
+              const int64_t lo = only_slab ? q[r] : std::min(q[r], b.box[r]);
+              const int64_t hi = only_slab ? q[3 + r] : std::max(q[3 + r], b.box[3 + r]);
+              qc[r] = std::max(lo, c_->root[r]);
+              qc[3 + r] = std::min(hi, c_->root[3 + r]);
             }
+            int i = 0;
+            if (qc[a] < qc[3 + a]) {
+              while (nodes_[i].axis >= 0) {
+                const int ax = nodes_[i].axis;
+                const int64_t sp = nodes_[i].split;
+                if (qc[3 + ax] <= sp) i = nodes_[i].left;
+                else if (qc[ax] >= sp) i = nodes_[i].right;
+                else break;
+              }
+            }
+            t.face_node[12 * (size_t)t.leaf[k] + 6 * only_slab + 2 * a + side] = node2pre[i];
           }
-          t.face_node[6 * (size_t)t.leaf[k] + 2 * a + side] = node2pre[i];
           if ((side == 0 && q[a] < pt.fbox[a]) || (side == 1 && q[3 + a] > pt.fbox[3 + a]))
             continue;
           if (same_patch(0, q, b.patch)) f |= (uint8_t)(1u << (2 * a + side));

@@ -532,8 +532,15 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs&
   int lid = -1;
   const bool pruning = lod_min < kNoLod;
   // the neighbour lies in the leaf or in the level cell beyond its face (a, sign): start at
-  // the deepest node holding both (from the root under pruning, which may stop above it)
-  uint32_t i = pruning ? 0u : (uint32_t)__ldg(A.face_node + 6 * leaf + 2 * a + (sign > 0.0f ? 1 : 0));
+  // the deepest node holding both, or the cell alone when the point is clearly beyond the
+  // face (from the root under pruning, which may stop above them)
+  uint32_t i = 0;
+  if (!pruning) {
+    const float xa = sel3f(a, xr[0], xr[1], xr[2]);
+    const float ext = (float)(sel3i(a, cl.hi[0], cl.hi[1], cl.hi[2]) - sel3i(a, cl.lo[0], cl.lo[1], cl.lo[2]));
+    const bool beyond = sign > 0.0f ? xa >= ext + mf : xa < -mf;
+    i = (uint32_t)__ldg(A.face_node + 12 * leaf + (beyond ? 6 : 0) + 2 * a + (sign > 0.0f ? 1 : 0));
+  }
   for (int depth = 0; depth < kMaxDepth; ++depth) {
     const DNode nd = A.nodes[i];
     const uint32_t ax = nd.meta >> 30;
