@@ -53,7 +53,8 @@ class _Params(C.Structure):
                 ("kd", C.c_double), ("ks", C.c_double), ("shininess", C.c_double),
                 ("gamma", C.c_double), ("world_step", C.c_double), ("interp", C.c_int),
                 ("shade", C.c_int), ("lookup", C.c_int), ("max_segments", C.c_int),
-                ("lod_pixels", C.c_double)]
+                ("lod_pixels", C.c_double), ("shadow", C.c_int), ("light", C.c_double * 3),
+                ("light_step", C.c_double), ("light_ambient", C.c_double)]
 
 
 def _load():
@@ -87,6 +88,8 @@ def _load():
             lib.orc_trace_lod.argtypes = [P, C.POINTER(_Camera), C.c_int, C.c_int, C.c_double,
                                           ip, dp, dp, C.c_int]
             lib.orc_get_node_labels.argtypes = [P, ip, ip, ip]
+            lib.orc_shadow_T.restype = C.c_double
+            lib.orc_shadow_T.argtypes = [P, C.POINTER(C.c_float), C.c_int, C.POINTER(_Params), dp]
             lib.orc_render_pixels.argtypes = [P, C.POINTER(_Camera), C.POINTER(C.c_float), C.c_int,
                                               C.POINTER(_Params), C.c_int, ip, ip, dp,
                                               C.POINTER(C.c_ulonglong), C.c_int]
@@ -141,14 +144,20 @@ class OracleParams:
     lookup: int = 0
     max_segments: int = 0
     lod_pixels: float = 0.0  # > 0: level-of-detail pruning (Sec. 3.1 type-(a) nodes)
+    shadow: int = 0          # 1: secondary rays to a point light
+    light: tuple = (0.0, 0.0, 0.0)
+    light_step: float = 0.0
+    light_ambient: float = 0.2
 
     def struct(self) -> _Params:
         p = _Params()
         for f in ("step_factor", "kappa", "ert_eps", "vmin", "vmax", "ka", "kd", "ks",
-                  "shininess", "gamma", "world_step", "lod_pixels"):
+                  "shininess", "gamma", "world_step", "lod_pixels", "light_step",
+                  "light_ambient"):
             setattr(p, f, float(getattr(self, f)))
-        for f in ("interp", "shade", "lookup", "max_segments"):
+        for f in ("interp", "shade", "lookup", "max_segments", "shadow"):
             setattr(p, f, int(getattr(self, f)))
+        p.light[:] = [float(v) for v in self.light]
         return p
 
 
@@ -271,6 +280,14 @@ class Oracle:
         if n < 0:
             raise OracleError(n, "orc_trace")
         return leaf[:n].copy(), t0[:n].copy(), t1[:n].copy()
+
+    def shadow_T(self, x, tf: np.ndarray, params: OracleParams) -> float:
+        """Transmittance from world point x to params.light (secondary ray)."""
+        tfa = np.ascontiguousarray(tf, dtype=np.float32).reshape(-1, 4)
+        xa = np.ascontiguousarray(x, dtype=np.float64)
+        ps = params.struct()
+        return float(self._lib.orc_shadow_T(self._h, tfa.ctypes.data_as(C.POINTER(C.c_float)),
+                                            tfa.shape[0], C.byref(ps), _dp(xa)))
 
     def render(self, cam, tf: np.ndarray, params: OracleParams,
                pixels: Optional[np.ndarray] = None, nthreads: int = 0):
