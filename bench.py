@@ -323,6 +323,34 @@ def lod_eval(amr, ctx, vmin, vmax, cam, tf, out, args, lods=(0.5, 1.0, 2.0, 4.0)
     return res
 
 
+def shadow_eval(amr, ctx, vmin, vmax, args, size=512):
+    """Secondary rays to a central point light (the paper's global-illumination example):
+    frame time at `size`² with and without them, Phong, light step half a level-0 cell."""
+    import torch
+    import synth
+
+    cam = synth.orbit_camera(2, size, size)
+    tf = torch.as_tensor(synth.ramp_tf(), device="cuda")
+    out = torch.empty((size, size, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {"size": size}
+    for name, kw in (("plain", {}), ("shadow", {"shadow": 1, "light": (0.5, 0.5, 0.5),
+                                                "light_step": 0.5 / 128, "light_ambient": 0.2})):
+        prm = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
+                                     **kw)
+        n = ctx.amr_render(cam, tf, prm, out, count_samples=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(2):
+            ctx.amr_render(cam, tf, prm, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 2
+        res[name] = {"ms": ms, "frames_per_s": 1e3 / ms, "samples": n}
+    res["slowdown"] = res["shadow"]["ms"] / res["plain"]["ms"]
+    return res
+
+
 def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5, lo=256, hi=2048,
                tune_views=16):
     """Batched multi-view rendering: 64 seeded views with square sides uniform in
@@ -476,6 +504,7 @@ def main():
     ap.add_argument("--precision", type=int, default=1, help="time FP16 / BF16 cell storage")
     ap.add_argument("--batch", type=int, default=1, help="time 64-view batched rendering")
     ap.add_argument("--lod", type=int, default=1, help="time level-of-detail pruning")
+    ap.add_argument("--shadow", type=int, default=1, help="time secondary rays to a point light")
     ap.add_argument("--c3", type=int, default=0,
                     help="also render the deep 8-level hierarchy (~1e9 cells; minutes)")
     ap.add_argument("--log-size", type=int, default=96)
@@ -613,6 +642,9 @@ def main():
                                   "efficiency_with_halo": s2.atlas_efficiency_halo}
             c2.amr_destroy()
         extra["storages"] = comp
+    if args.shadow and world == 1 and args.storage in ("ptr", "atlas_linear") and \
+            args.dtype == "f32":
+        extra["shadow"] = shadow_eval(amr, ctx, vmin, vmax, args)
     if args.lod and world == 1:
         extra["lod"] = lod_eval(amr, ctx, vmin, vmax, cam, tf, out, args)
     if args.precision and world == 1:

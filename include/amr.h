@@ -114,6 +114,16 @@ typedef struct {
                                and samples it at level l; gradients then read the same pruned
                                tree.  0 (default) renders every level.  Schedules 0 and 2,
                                no learned proposal. */
+  int32_t shadow;           /* 1: secondary rays to a point light (the global-illumination
+                               example of Sec. 5): an opaque sample at x is lit by
+                               I = light_ambient + (1 - light_ambient) T, T the transmittance
+                               of the part of x -> light inside the root box, marched with
+                               n = max(1, ceil(len / light_step)) midpoint samples of the AMR
+                               field (T = prod exp(-kappa a_TF len / n), 0 once <= 1e-4);
+                               its colour is multiplied by I.  Trilinear; not schedule 1. */
+  double light[3];          /* light position (world) */
+  double light_step;        /* world step along secondary rays (> 0 with shadow) */
+  double light_ambient;     /* in [0, 1] (default 0.2) */
 } amr_render_params;
 
 /* Fills p with the defaults: step 0.5, kappa 8, ert_eps 1e-4, vmin 0, vmax 1, ka 0.3,

@@ -41,7 +41,9 @@ class amr_render_params(C.Structure):
                 ("row0", C.c_int32), ("rows", C.c_int32), ("skip", C.c_int32),
                 ("max_segments", C.c_int32), ("schedule", C.c_int32),
                 ("learned", C.c_int32), ("tau", C.c_double), ("samples_per_iter", C.c_int32),
-                ("coarse_factor", C.c_int32), ("lod_pixels", C.c_double)]
+                ("coarse_factor", C.c_int32), ("lod_pixels", C.c_double),
+                ("shadow", C.c_int32), ("light", C.c_double * 3), ("light_step", C.c_double),
+                ("light_ambient", C.c_double)]
 
 
 class amr_stats(C.Structure):

@@ -26,6 +26,7 @@ constexpr int kMaxSamplesPerSegment = 1 << 22;
 // [3] exact sample counts, [4] exact neighbour / nearest positions
 constexpr int kNumCounters = 8;
 constexpr int kQueueCounter = 5;       // counters[5]: head of the batched work queue
+constexpr int kShadeShadowBit = 4;     // kernel shading variant bit: secondary rays
 constexpr int kMaxBatchViews = 128;
 // status bits raised by kernels (OR-ed into counters[1])
 constexpr unsigned long long kStatusCapacity = 1ull;   // segment or sample bound hit
@@ -113,6 +114,9 @@ struct RenderArgs {
   float tau;                     // proposal threshold on the predicted contribution
   int32_t learned;               // 0 off, 1 skip, 2 coarse (coarse_factor x step) below tau
   float inv_levels;              // 1 / (L - 1), 0 for one level
+  int32_t shadow;                // secondary rays to the point light
+  float light_f[3];              // light position, finest-cell units
+  float light_step, light_ambient;
   int32_t samples_per_iter;      // refill schedule: samples per lane between warp steps
   int32_t coarse_factor;         // learned mode 2: step multiplier below tau
 };

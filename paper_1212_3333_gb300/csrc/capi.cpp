@@ -124,6 +124,7 @@ void amr_default_params(amr_render_params* p) {
   p->tau = 1e-3;
   p->samples_per_iter = 4;
   p->coarse_factor = 4;
+  p->light_ambient = 0.2;
 }
 
 amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double domain_lo[3],
@@ -299,6 +300,17 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
     return fail(c, AMR_ERR_ARG, "lod_pixels must be finite and non-negative");
   if (p->lod_pixels > 0.0 && (p->schedule == 1 || p->learned != 0))
     return fail(c, AMR_ERR_ARG, "level-of-detail pruning needs schedule 0 or 2 without the proposal");
+  if (p->shadow != 0 && p->shadow != 1) return fail(c, AMR_ERR_ARG, "shadow must be 0 or 1");
+  if (p->shadow) {
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(p->light[a])) return fail(c, AMR_ERR_ARG, "light must be finite");
+    if (!(p->light_step > 0.0) || !std::isfinite(p->light_step))
+      return fail(c, AMR_ERR_ARG, "light_step must be positive");
+    if (!(p->light_ambient >= 0.0 && p->light_ambient <= 1.0))
+      return fail(c, AMR_ERR_ARG, "light_ambient must be in [0, 1]");
+    if (p->interp != AMR_INTERP_TRILINEAR || p->schedule != 0 || p->learned != 0)
+      return fail(c, AMR_ERR_ARG, "secondary rays need trilinear sampling, schedule 0, no proposal");
+  }
   if (p->row0 < 0 || p->row0 >= cam->height) return fail(c, AMR_ERR_ARG, "row0 out of range");
   int rows = p->rows <= 0 ? cam->height - p->row0 : std::min(p->rows, cam->height - p->row0);
   std::memset(a, 0, sizeof *a);
@@ -334,6 +346,11 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->learned = p->learned;
   a->inv_levels = c->L > 1 ? 1.0f / (float)(c->L - 1) : 0.0f;
   a->samples_per_iter = p->samples_per_iter;
+  a->shadow = p->shadow;
+  for (int q = 0; q < 3; ++q)
+    a->light_f[q] = (float)((p->light[q] - c->dlo[q]) * a->ray.inv_hf[q]);
+  a->light_step = (float)p->light_step;
+  a->light_ambient = (float)p->light_ambient;
   a->coarse_factor = p->coarse_factor;
   if (c->dtype != AMR_F32 && (p->interp != AMR_INTERP_TRILINEAR || p->schedule == 1))
     return fail(c, AMR_ERR_ARG, "16-bit cells render trilinear with schedule 0 or 2");
@@ -357,9 +374,10 @@ static int kernel_storage(const amr_ctx* c) {
 
 // shading variant: 2 = Phong reading the gradient bricks (trilinear only), when built
 static int kernel_shade(const amr_ctx* c, const amr_render_params* p) {
+  int sh = p->shade;
   if (p->shade && p->interp == AMR_INTERP_TRILINEAR && c->want_gradient && c->dev.gpool_bytes)
-    return 2;
-  return p->shade;
+    sh = 2;
+  return sh | (p->shadow ? kShadeShadowBit : 0);
 }
 
 static amr_status finish_render(amr_ctx* c, cudaStream_t st, uint64_t* samples_out) {
@@ -463,8 +481,9 @@ amr_status prepare_batch(amr_ctx* c, const amr_view* views, int32_t n_views, con
     return fail(c, AMR_ERR_ARG, "need 1 <= n_tf <= 8 and n_tf * tf_n <= 2048");
   if (p->row0 != 0 || p->rows > 0)
     return fail(c, AMR_ERR_ARG, "batched views render whole images (row0 = 0, rows <= 0)");
-  if (p->interp != AMR_INTERP_TRILINEAR || p->schedule != 0 || p->learned != 0)
-    return fail(c, AMR_ERR_ARG, "batched rendering is trilinear, per-ray, without the proposal");
+  if (p->interp != AMR_INTERP_TRILINEAR || p->schedule != 0 || p->learned != 0 || p->shadow)
+    return fail(c, AMR_ERR_ARG,
+                "batched rendering is trilinear, per-ray, without the proposal or secondary rays");
   if (cfg.rays_per_thread < 1 || cfg.rays_per_thread > 8 || cfg.blocks_per_sm < 0)
     return fail(c, AMR_ERR_ARG, "batch config: rays_per_thread in [1, 8], blocks_per_sm >= 0");
   if (!((cfg.tile_w == 8 && cfg.tile_h == 8) || (cfg.tile_w == 16 && cfg.tile_h == 8) ||

@@ -215,6 +215,9 @@ __device__ __forceinline__ float exit_bound(const RayF& f) { return ldexpf(f.tau
 // node whose label level l has min_a h^l_a <= X, i.e. l >= lod_min: the smallest such
 // level, or kNoLod when pruning is off or no level qualifies.
 constexpr int kNoLod = 1 << 20;
+// shading variant bits of the kernels' SHADE parameter: 0 none, 1 Phong, 2 Phong with
+// gradient bricks, plus kShadeShadow for secondary rays to the point light
+constexpr int kShadeShadow = kShadeShadowBit;
 
 static __device__ __noinline__ int lod_min_exact(const RayArgs& R, const DLevel* lv, int px,
                                                  int py, int pid0) {
@@ -861,6 +864,64 @@ __device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& r
   s.margin = ex * lv.inv_sc + ldexpf(bmax + 2.0f, -21);
 }
 
+// Secondary ray from a sample to the point light (the global-illumination example of
+// Sec. 5): transmittance of the part of the segment X -> light inside the root box, marched
+// with n = max(1, ceil(len / light_step)) midpoint samples of the AMR field (the finest
+// leaf holding each point, trilinear in its brick), stopping with 0 once T <= 1e-4.
+// X in finest-cell units.  Consecutive samples usually stay in one leaf, which is reused.
+template <int ST>
+__device__ __noinline__ float shadow_transmittance(const RenderArgs& A, const RayArgs& R,
+                                                   const float4* s_tf, float x0, float x1,
+                                                   float x2) {
+  const float X[3] = {x0, x1, x2};
+  float D[3], s_out = 1.0f, len2 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    D[a] = A.light_f[a] - X[a];
+    if (D[a] != 0.0f) {
+      const float bound = (float)(D[a] > 0.0f ? R.root_f[3 + a] : R.root_f[a]);
+      s_out = fminf(s_out, (bound - X[a]) / D[a]);
+    }
+    const float w = D[a] * (float)R.hf[a];
+    len2 = fmaf(w, w, len2);
+  }
+  s_out = fmaxf(s_out, 0.0f);
+  const float len = s_out * sqrtf(len2);
+  const int n = (int)fminf(fmaxf(ceilf(len / A.light_step), 1.0f), 65536.0f);
+  const float delta = len / (float)n;
+  float T = 1.0f;
+  int leaf = -1;
+  DLeaf lf;
+  BrickRef b;
+  float inv_sc = 1.0f;
+  for (int k = 0; k < n; ++k) {
+    const float sk = ((float)k + 0.5f) / (float)n * s_out;
+    float P[3];
+    int f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      P[a] = fmaf(sk, D[a], X[a]);
+      f[a] = min(max((int)floorf(P[a]), R.root_f[a]), R.root_f[3 + a] - 1);
+    }
+    const bool inside = leaf >= 0 && f[0] >= lf.lo[0] && f[0] < lf.hi[0] && f[1] >= lf.lo[1] &&
+                        f[1] < lf.hi[1] && f[2] >= lf.lo[2] && f[2] < lf.hi[2];
+    if (!inside) {
+      leaf = locate_cell(A.nodes, R, kNoLod, f[0], f[1], f[2]);
+      if (leaf < 0) return T;
+      lf = A.leaves[leaf];
+      b = load_brick(A.patches, lf.patch);
+      inv_sc = A.lv[lf.level].inv_sc;
+    }
+    const float v = trilinear<ST>(A, b, fmaf(P[0], inv_sc, 0.5f - (float)b.lo[0]),
+                                  fmaf(P[1], inv_sc, 0.5f - (float)b.lo[1]),
+                                  fmaf(P[2], inv_sc, 0.5f - (float)b.lo[2]));
+    const float a_tf = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range).w;
+    T *= expf(-A.kappa * a_tf * delta);
+    if (T <= 1e-4f) return 0.0f;
+  }
+  return T;
+}
+
 // Sample k of a segment (Sec. 3: emission-absorption compositing; Sec. 4: gradient
 // shading), composited front to back into (C, Acc).  Returns true when early ray
 // termination stops the ray at this sample.
@@ -878,9 +939,9 @@ __device__ __forceinline__ bool sample_one(const RenderArgs& A, const RayArgs& R
   if (c.w <= 0.0f) return false;
   const float alpha = -expm1f(-A.kappa * c.w * g.delta);
   float cr = c.x, cg = c.y, cb = c.z;
-  if constexpr (SHADE >= 1) {
+  if constexpr ((SHADE & 3) >= 1) {
     float gr[3];
-    gradient<ST, INTERP, (SHADE == 2)>(A, R, s, beta, k, lv, gr);
+    gradient<ST, INTERP, ((SHADE & 3) == 2)>(A, R, s, beta, k, lv, gr);
     const float gn = sqrtf(fmaf(gr[0], gr[0], fmaf(gr[1], gr[1], gr[2] * gr[2])));
     const float gf = A.gfloor_num / lv.hmin;
     const float den = fmaxf(gn, gf);
@@ -891,6 +952,17 @@ __device__ __forceinline__ bool sample_one(const RenderArgs& A, const RayArgs& R
     cr = fminf(fmaxf(fmaf(cr, diff, spec), 0.0f), 1.0f);
     cg = fminf(fmaxf(fmaf(cg, diff, spec), 0.0f), 1.0f);
     cb = fminf(fmaxf(fmaf(cb, diff, spec), 0.0f), 1.0f);
+  }
+  if constexpr ((SHADE & kShadeShadow) != 0) {
+    // the sample in finest-cell units: beta = X / sc - lo + 0.5
+    const float sc = (float)lv.sc;
+    const float T = shadow_transmittance<ST>(A, R, s_tf, (beta[0] - 0.5f + (float)s.brick.lo[0]) * sc,
+                                             (beta[1] - 0.5f + (float)s.brick.lo[1]) * sc,
+                                             (beta[2] - 0.5f + (float)s.brick.lo[2]) * sc);
+    const float I = fmaf(1.0f - A.light_ambient, T, A.light_ambient);
+    cr *= I;
+    cg *= I;
+    cb *= I;
   }
   const float w = (1.0f - Acc) * alpha;
   C0 = fmaf(w, cr, C0);
@@ -932,7 +1004,7 @@ __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const RayArg
 #define AMR_MIN_BLOCKS_PLAIN 6
 #endif
 template <int SHADE>
-constexpr int kMinBlocks = SHADE == 0 ? AMR_MIN_BLOCKS_PLAIN : AMR_MIN_BLOCKS_SHADED;
+constexpr int kMinBlocks = (SHADE & 3) == 0 ? AMR_MIN_BLOCKS_PLAIN : AMR_MIN_BLOCKS_SHADED;
 
 // The whole march of pixel (i, j) of the view R: ray setup, kd-restart over the leaves,
 // sampling and compositing.  Returns premultiplied RGBA; adds to nsamp and status.

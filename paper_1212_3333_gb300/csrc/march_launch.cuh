@@ -47,7 +47,20 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
   const size_t tf_bytes = (size_t)a.tf_n * sizeof(float4) + (size_t)(a.tf_n + 1) * sizeof(int);
   if (grid.x == 0 || grid.y == 0) return AMR_OK;
   cudaError_t e;
-  if (schedule == 2) {
+  if (shade & kShadeShadow) {
+    // secondary rays to the point light: per-ray schedule, trilinear, FP32 linear storages
+    if constexpr (ST == ST_PTR || ST == ST_ATLAS_LINEAR) {
+      if (interp != 1 || schedule != 0)
+        return fail(c, AMR_ERR_ARG, "secondary rays render trilinear with schedule 0");
+      const size_t smem = tf_bytes;
+      const int base = shade & 3;
+      if (base == 0) e = launch_one(march_kernel<ST, 1, kShadeShadow>, grid, block, smem, s, a);
+      else if (base == 1) e = launch_one(march_kernel<ST, 1, 1 | kShadeShadow>, grid, block, smem, s, a);
+      else e = launch_one(march_kernel<ST, 1, 2 | kShadeShadow>, grid, block, smem, s, a);
+    } else {
+      return fail(c, AMR_ERR_ARG, "secondary rays need the ptr or atlas_linear storage, FP32 cells");
+    }
+  } else if (schedule == 2) {
     // persistent warps with ray refill (trilinear)
     if (interp != 1) return fail(c, AMR_ERR_ARG, "the refill schedule renders trilinear");
     const size_t smem = tf_bytes;

@@ -16,7 +16,8 @@ def params_pair(amr, vmin, vmax, **kw):
     o = oracle.OracleParams(vmin=float(vmin), vmax=float(vmax), step_factor=p.step_factor,
                             kappa=p.kappa, ert_eps=p.ert_eps, interp=p.interp, shade=p.shade,
                             ka=p.ka, kd=p.kd, ks=p.ks, shininess=p.shininess, gamma=p.gamma,
-                            lod_pixels=p.lod_pixels)
+                            lod_pixels=p.lod_pixels, shadow=p.shadow, light=tuple(p.light),
+                            light_step=p.light_step, light_ambient=p.light_ambient)
     return p, o
 
 

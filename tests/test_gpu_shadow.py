@@ -1,0 +1,79 @@
+"""GPU parity of secondary rays to a point light (the global-illumination example of
+Sec. 5): images against the FP64 oracle (whose transmittance is pinned by closed forms),
+for a light inside and outside the domain, unshaded and Phong, with and without gradient
+bricks, in both linear storages; unsupported combinations are rejected."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import assert_image_close, gpu_render, params_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amr():
+    import paper_1212_3333_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def c1():
+    w = synth.c1_workload(width=96, height=80)
+    return w, oracle.Oracle(w["hier"])
+
+
+@pytest.mark.parametrize("storage", ["ptr", "atlas_linear"])
+@pytest.mark.parametrize("gradient", [False, True])
+@pytest.mark.parametrize("light", [(0.5, 0.5, 0.5), (1.6, -0.4, 0.9)])
+def test_shadow_image_c1(amr, c1, storage, gradient, light):
+    w, o = c1
+    ctx = amr.from_hierarchy(w["hier"])
+    ctx.amr_build_kdtree(storage, gradient=gradient)
+    for shade in (0, 1):
+        p, op = params_pair(amr, w["vmin"], w["vmax"], shade=shade, shadow=1, light=light,
+                            light_step=1.0 / 128, light_ambient=0.15)
+        img, n = gpu_render(ctx, w["camera"], w["tf"], p)
+        ref, smp = o.render(w["camera"], w["tf"], op)
+        assert_image_close(img, ref, what=f"shadow {storage} grad={gradient} shade={shade}")
+        assert int(n) == int(smp.sum()) or abs(int(n) - int(smp.sum())) <= 0.001 * smp.sum()
+        plain, _ = gpu_render(ctx, w["camera"], w["tf"], params_pair(
+            amr, w["vmin"], w["vmax"], shade=shade)[0])
+        assert np.all(img[..., :3] <= plain[..., :3] + 1e-6)
+        assert np.array_equal(img[..., 3], plain[..., 3])
+        assert np.mean(img[..., :3]) < 0.95 * np.mean(plain[..., :3])
+
+
+def test_shadow_rejections(amr, c1):
+    import torch
+
+    from paper_1212_3333_gb300 import _lib
+
+    w, _ = c1
+    ctx = amr.from_hierarchy(w["hier"])
+    ctx.amr_build_kdtree("texobj")
+    p, _ = params_pair(amr, w["vmin"], w["vmax"], shadow=1, light=(0.5, 0.5, 0.5),
+                       light_step=0.01)
+    with pytest.raises(amr.AmrError) as e:
+        gpu_render(ctx, w["camera"], w["tf"], p)
+    assert e.value.status == _lib.AMR_ERR_ARG
+    ctx = amr.from_hierarchy(w["hier"])
+    ctx.amr_build_kdtree("ptr")
+    for kw in (dict(schedule=1), dict(schedule=2), dict(interp=0), dict(light_step=0.0),
+               dict(light_ambient=1.5), dict(light=(np.nan, 0.0, 0.0))):
+        base = dict(shadow=1, light=(0.5, 0.5, 0.5), light_step=0.01)
+        base.update(kw)
+        p, _ = params_pair(amr, w["vmin"], w["vmax"], **base)
+        with pytest.raises(amr.AmrError) as e:
+            gpu_render(ctx, w["camera"], w["tf"], p)
+        assert e.value.status == _lib.AMR_ERR_ARG, kw
+    views, offsets, total = amr.make_views([w["camera"]], [0])
+    out = torch.zeros((total,), device="cuda")
+    tfs = torch.as_tensor(np.stack(synth.tf_variants()), device="cuda")
+    p, _ = params_pair(amr, w["vmin"], w["vmax"], shadow=1, light=(0.5, 0.5, 0.5),
+                       light_step=0.01)
+    with pytest.raises(amr.AmrError) as e:
+        ctx.amr_render_batch(views, tfs, p, out)
+    assert e.value.status == _lib.AMR_ERR_ARG
