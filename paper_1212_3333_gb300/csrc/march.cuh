@@ -436,32 +436,52 @@ __device__ __forceinline__ float4 fetch4(const RenderArgs& A, const BrickRef& b,
 // Trilinear interpolation at brick coordinate beta (brick index = cell - lo + 1, cell
 // centres at integer beta).  Coordinates are clamped into the brick, which reproduces edge
 // replication where the brick touches the domain boundary.
+// The eight cells around a brick position and the interpolation weights: fetched first,
+// combined later, so a sample's loads can be issued while the previous sample is shaded.
+struct Corners {
+  float v[8];
+  float wx, wy, wz;
+  __device__ __forceinline__ float value() const {
+    const float c00 = fmaf(wx, v[1] - v[0], v[0]);
+    const float c10 = fmaf(wx, v[3] - v[2], v[2]);
+    const float c01 = fmaf(wx, v[5] - v[4], v[4]);
+    const float c11 = fmaf(wx, v[7] - v[6], v[6]);
+    const float c0 = fmaf(wy, c10 - c00, c00);
+    const float c1 = fmaf(wy, c11 - c01, c01);
+    return fmaf(wz, c1 - c0, c0);
+  }
+};
+
 template <int ST>
-__device__ __forceinline__ float trilinear(const RenderArgs& A, const BrickRef& b, float bx,
-                                           float by, float bz) {
+__device__ __forceinline__ Corners trilinear_fetch(const RenderArgs& A, const BrickRef& b,
+                                                   float bx, float by, float bz) {
   bx = fminf(fmaxf(bx, 0.0f), (float)(b.dim[0] - 1));
   by = fminf(fmaxf(by, 0.0f), (float)(b.dim[1] - 1));
   bz = fminf(fmaxf(bz, 0.0f), (float)(b.dim[2] - 1));
   const int ix = min((int)bx, b.dim[0] - 2);
   const int iy = min((int)by, b.dim[1] - 2);
   const int iz = min((int)bz, b.dim[2] - 2);
-  const float wx = bx - (float)ix, wy = by - (float)iy, wz = bz - (float)iz;
+  Corners c;
+  c.wx = bx - (float)ix;
+  c.wy = by - (float)iy;
+  c.wz = bz - (float)iz;
   const long long l0 = (long long)ix + (long long)b.sy * iy + (long long)b.sz * iz;
-  const float v000 = fetch<ST>(A, b, l0, ix, iy, iz);
-  const float v100 = fetch<ST>(A, b, l0 + 1, ix + 1, iy, iz);
-  const float v010 = fetch<ST>(A, b, l0 + b.sy, ix, iy + 1, iz);
-  const float v110 = fetch<ST>(A, b, l0 + b.sy + 1, ix + 1, iy + 1, iz);
-  const float v001 = fetch<ST>(A, b, l0 + b.sz, ix, iy, iz + 1);
-  const float v101 = fetch<ST>(A, b, l0 + b.sz + 1, ix + 1, iy, iz + 1);
-  const float v011 = fetch<ST>(A, b, l0 + b.sz + b.sy, ix, iy + 1, iz + 1);
-  const float v111 = fetch<ST>(A, b, l0 + b.sz + b.sy + 1, ix + 1, iy + 1, iz + 1);
-  const float c00 = fmaf(wx, v100 - v000, v000);
-  const float c10 = fmaf(wx, v110 - v010, v010);
-  const float c01 = fmaf(wx, v101 - v001, v001);
-  const float c11 = fmaf(wx, v111 - v011, v011);
-  const float c0 = fmaf(wy, c10 - c00, c00);
-  const float c1 = fmaf(wy, c11 - c01, c01);
-  return fmaf(wz, c1 - c0, c0);
+  c.v[0] = fetch<ST>(A, b, l0, ix, iy, iz);
+  c.v[1] = fetch<ST>(A, b, l0 + 1, ix + 1, iy, iz);
+  c.v[2] = fetch<ST>(A, b, l0 + b.sy, ix, iy + 1, iz);
+  c.v[3] = fetch<ST>(A, b, l0 + b.sy + 1, ix + 1, iy + 1, iz);
+  c.v[4] = fetch<ST>(A, b, l0 + b.sz, ix, iy, iz + 1);
+  c.v[5] = fetch<ST>(A, b, l0 + b.sz + 1, ix + 1, iy, iz + 1);
+  c.v[6] = fetch<ST>(A, b, l0 + b.sz + b.sy, ix, iy + 1, iz + 1);
+  c.v[7] = fetch<ST>(A, b, l0 + b.sz + b.sy + 1, ix + 1, iy + 1, iz + 1);
+  return c;
+}
+
+// Trilinear interpolation at brick position (bx, by, bz), clamped into the brick.
+template <int ST>
+__device__ __forceinline__ float trilinear(const RenderArgs& A, const BrickRef& b, float bx,
+                                           float by, float bz) {
+  return trilinear_fetch<ST>(A, b, bx, by, bz).value();
 }
 
 // Nearest cell value at integer brick index (clamped).
@@ -925,16 +945,14 @@ __device__ __noinline__ float shadow_transmittance(const RenderArgs& A, const Ra
 // Sample k of a segment (Sec. 3: emission-absorption compositing; Sec. 4: gradient
 // shading), composited front to back into (C, Acc).  Returns true when early ray
 // termination stops the ray at this sample.
+// Colour, opacity and compositing of sample k with value v at brick position beta.
 template <int ST, int INTERP, int SHADE>
-__device__ __forceinline__ bool sample_one(const RenderArgs& A, const RayArgs& R,
-                                           const float4* s_tf, const SegSetup& g,
-                                           const DLevel& lv, int k, float Lx, float Ly, float Lz,
-                                           float& C0, float& C1, float& C2, float& Acc) {
+__device__ __forceinline__ bool composite_sample(const RenderArgs& A, const RayArgs& R,
+                                                 const float4* s_tf, const SegSetup& g,
+                                                 const DLevel& lv, int k, const float* beta,
+                                                 float v, float Lx, float Ly, float Lz,
+                                                 float& C0, float& C1, float& C2, float& Acc) {
   const SegState& s = g.s;
-  float beta[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
-  const float v = sample_value<ST, INTERP>(A, R, s, beta, k);
   const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
   if (c.w <= 0.0f) return false;
   const float alpha = -expm1f(-A.kappa * c.w * g.delta);
@@ -972,6 +990,21 @@ __device__ __forceinline__ bool sample_one(const RenderArgs& A, const RayArgs& R
   return Acc >= A.ert_thresh;
 }
 
+
+template <int ST, int INTERP, int SHADE>
+__device__ __forceinline__ bool sample_one(const RenderArgs& A, const RayArgs& R,
+                                           const float4* s_tf, const SegSetup& g,
+                                           const DLevel& lv, int k, float Lx, float Ly, float Lz,
+                                           float& C0, float& C1, float& C2, float& Acc) {
+  const SegState& s = g.s;
+  float beta[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
+  const float v = sample_value<ST, INTERP>(A, R, s, beta, k);
+  return composite_sample<ST, INTERP, SHADE>(A, R, s_tf, g, lv, k, beta, v, Lx, Ly, Lz, C0, C1,
+                                            C2, Acc);
+}
+
 // March the samples of one segment front to back.  Returns true when early ray
 // termination stops the ray inside the segment.
 template <int ST, int INTERP, int SHADE>
@@ -980,12 +1013,36 @@ __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const RayArg
                                                const SegSetup& g, const DLevel& lv, float Lx,
                                                float Ly, float Lz, float& C0, float& C1, float& C2,
                                                float& Acc, unsigned& nsamp) {
-  for (int k = 0; k < g.s.n; ++k) {
-    ++nsamp;
-    if (sample_one<ST, INTERP, SHADE>(A, R, s_tf, g, lv, k, Lx, Ly, Lz, C0, C1, C2, Acc))
-      return true;
+  if constexpr (INTERP == 1 && SHADE == 0) {
+    // software pipeline: the cells of sample k + 1 are requested before sample k is
+    // composited (unshaded only: with shading the extra live registers spill, measured
+    // 13 % slower on C2 at 2048^2; unshaded 2 % faster)
+    Corners next = trilinear_fetch<ST>(A, g.s.brick, g.b0[0], g.b0[1], g.b0[2]);
+    for (int k = 0; k < g.s.n; ++k) {
+      const float v = next.value();
+      float beta[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
+      if (k + 1 < g.s.n) {
+        float bn[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) bn[a] = fmaf((float)(k + 1), g.db[a], g.b0[a]);
+        next = trilinear_fetch<ST>(A, g.s.brick, bn[0], bn[1], bn[2]);
+      }
+      ++nsamp;
+      if (composite_sample<ST, INTERP, SHADE>(A, R, s_tf, g, lv, k, beta, v, Lx, Ly, Lz, C0, C1,
+                                              C2, Acc))
+        return true;
+    }
+    return false;
+  } else {
+    for (int k = 0; k < g.s.n; ++k) {
+      ++nsamp;
+      if (sample_one<ST, INTERP, SHADE>(A, R, s_tf, g, lv, k, Lx, Ly, Lz, C0, C1, C2, Acc))
+        return true;
+    }
+    return false;
   }
-  return false;
 }
 
 // Resident 128-thread blocks per SM the compiler must allow for, i.e. a register budget of
