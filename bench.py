@@ -461,7 +461,7 @@ def run_reference(args):
         if s >= args.warmup:
             vals.append(cb["value"])
     v = statistics.mean(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(hier, args, "oracle", args.size),
@@ -476,7 +476,8 @@ def _config(hier, args, storage, size=SIZE):
                          f"{hier.n_cells():.3g} FP32 cells; {size}x{size} view; "
                          f"{'Phong' if args.shade else 'unshaded'} trilinear; step 0.5 h^l; "
                          f"ERT eps {args.ert}"),
-            "storage": storage + ("+gradient bricks" if getattr(args, "gradient", 0) else ""),
+            "storage": storage + ("+gradient bricks" if getattr(args, "gradient", 0) and
+                                  storage != "oracle" else ""),
             "cells": getattr(args, "dtype", "f32"),
             "image": [size, size], "shade": args.shade,
             "l2": "inputs larger than L2: 602 MB of bricks vs 129 MB L2, no flush"}
