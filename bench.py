@@ -180,8 +180,8 @@ def learned_eval(amr, ctx, hier, vmin, vmax, tf, args, taus=(1e-4, 3e-4, 1e-3, 3
     """Learned segment proposal on the same hierarchy: log segments from 256 seeded poses
     (seeds 1000-1255), train the MLP with the library's kernels, then time held-out views
     (seeds 2000-2007) at the bench size: plain march, exact min/max skipping, and min/max +
-    learned skipping (and 4x / 16x coarser sampling) for each tau, PSNR against the plain
-    march."""
+    learned skipping (and 4x / 16x / 64x coarser sampling) for each tau, PSNR against the
+    plain march."""
     import torch
 
     import synth
@@ -217,7 +217,7 @@ def learned_eval(amr, ctx, hier, vmin, vmax, tf, args, taus=(1e-4, 3e-4, 1e-3, 3
     configs = {"plain": {}, "minmax": {"skip": 1}}
     for tau in taus:
         configs[f"skip@{tau:g}"] = {"skip": 1, "learned": 1, "tau": tau}
-        for cf in (4, 16):
+        for cf in (4, 16, 64):
             configs[f"coarse{cf}@{tau:g}"] = {"skip": 1, "learned": 2, "tau": tau,
                                               "coarse_factor": cf}
     res = {k: {"ms": 0.0, "psnr_min": float("inf"), "samples": 0} for k in configs}
