@@ -342,6 +342,21 @@ amr_status amr_get_leaves(const amr_ctx* ctx, int32_t* box6, int32_t* patch, int
 amr_status amr_get_nodes(const amr_ctx* ctx, int32_t* axis, int32_t* split, int32_t* left,
                          int32_t* right, int32_t* leaf, int64_t cap, int64_t* n);
 
+/* Type-(a) nodes (Sec. 3.1) in the order of their pruned-leaf ids M, M+1, ...: box
+ * (finest cells, 6 per node), the patch of that level holding the box, its level, and the
+ * node's pre-order id.  cap in nodes; *n receives their count. */
+amr_status amr_get_lod_leaves(const amr_ctx* ctx, int32_t* box6, int32_t* patch, int32_t* level,
+                              int32_t* node, int64_t cap, int64_t* n);
+
+/* Per leaf (canonical order): faces, bit 2a (+1) set when the level cell beyond the lower
+ * (upper) face on axis a lies in the leaf's patch and overlaps only leaves of that patch;
+ * face_node [12 per leaf]: for each face 2a + side the pre-order id of the deepest node
+ * holding the leaf and that cell (clipped to the root), then of the one holding the cell
+ * alone (the root when the cell lies outside it).  These drive the kernels' gradient
+ * neighbour lookups.  cap in leaves; *n receives the leaf count. */
+amr_status amr_get_leaf_faces(const amr_ctx* ctx, int32_t* faces, int32_t* face_node, int64_t cap,
+                              int64_t* n);
+
 /* The host brick of patch p with its one-cell halo: float32 [(nz+2)][(ny+2)][(nx+2)],
  * brick index b = level cell c - lo + 1.  cap in floats; *n receives the brick size.
  * With 16-bit cells the values are the rounded ones the device holds. */

@@ -175,6 +175,30 @@ class AmrContext:
                                         level.ctypes.data_as(ip), m, C.byref(n)), self._h)
         return box, patch, level
 
+    def amr_get_lod_leaves(self):
+        """Type-(a) nodes in pruned-leaf id order: box int32[k,6], patch, level, pre-order id."""
+        n = C.c_int64(0)
+        self._lib.amr_get_lod_leaves(self._h, None, None, None, None, 0, C.byref(n))
+        m = n.value
+        box = np.zeros((m, 6), dtype=np.int32)
+        arrs = [np.zeros(m, dtype=np.int32) for _ in range(3)]
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))  # noqa: E731
+        _check(self._lib.amr_get_lod_leaves(self._h, ip(box), ip(arrs[0]), ip(arrs[1]),
+                                            ip(arrs[2]), m, C.byref(n)), self._h)
+        return box, arrs[0], arrs[1], arrs[2]
+
+    def amr_get_leaf_faces(self):
+        """Per leaf: same-patch face bits and the 12 neighbour-lookup start nodes."""
+        n = C.c_int64(0)
+        self._lib.amr_get_leaf_faces(self._h, None, None, 0, C.byref(n))
+        m = n.value
+        faces = np.zeros(m, dtype=np.int32)
+        nodes = np.zeros((m, 12), dtype=np.int32)
+        ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))  # noqa: E731
+        _check(self._lib.amr_get_leaf_faces(self._h, ip(faces), ip(nodes), m, C.byref(n)),
+               self._h)
+        return faces, nodes
+
     def amr_get_nodes(self):
         n = C.c_int64(0)
         self._lib.amr_get_nodes(self._h, None, None, None, None, None, 0, C.byref(n))

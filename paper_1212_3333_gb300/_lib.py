@@ -111,6 +111,11 @@ _SIGS = {
     "amr_get_nodes": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                 C.c_int64, C.POINTER(C.c_int64)]),
+    "amr_get_lod_leaves": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int64,
+                                     C.POINTER(C.c_int64)]),
+    "amr_get_leaf_faces": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int64,
+                                     C.POINTER(C.c_int64)]),
     "amr_get_brick": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_float), C.c_int64,
                                 C.POINTER(C.c_int64)]),
     "amr_trace": (C.c_int, [_P, C.POINTER(amr_camera), C.c_double, _P, _P, _P, C.c_int32, _P]),

@@ -725,6 +725,38 @@ amr_status amr_get_nodes(const amr_ctx* c, int32_t* axis, int32_t* split, int32_
   return AMR_OK;
 }
 
+amr_status amr_get_lod_leaves(const amr_ctx* c, int32_t* box6, int32_t* patch, int32_t* level,
+                              int32_t* node, int64_t cap, int64_t* n) {
+  if (!c || !n) return AMR_ERR_ARG;
+  if (!c->host_built) return AMR_ERR_STATE;
+  const Tree& t = c->tree;
+  const int64_t m = (int64_t)t.lod_patch.size();
+  *n = m;
+  if (cap < m) return AMR_ERR_CAPACITY;
+  if (m && (!box6 || !patch || !level || !node)) return AMR_ERR_ARG;
+  std::memcpy(box6, t.lod_box.data(), sizeof(int32_t) * 6 * (size_t)m);
+  std::memcpy(patch, t.lod_patch.data(), sizeof(int32_t) * (size_t)m);
+  std::memcpy(level, t.lod_level.data(), sizeof(int32_t) * (size_t)m);
+  const int32_t M = (int32_t)t.leaf_patch.size();
+  for (size_t k = 0; k < t.node_lod.size(); ++k)
+    if (t.node_lod[k] >= 0) node[t.node_lod[k] - M] = (int32_t)k;
+  return AMR_OK;
+}
+
+amr_status amr_get_leaf_faces(const amr_ctx* c, int32_t* faces, int32_t* face_node, int64_t cap,
+                              int64_t* n) {
+  if (!c || !n) return AMR_ERR_ARG;
+  if (!c->host_built) return AMR_ERR_STATE;
+  const Tree& t = c->tree;
+  const int64_t m = (int64_t)t.leaf_patch.size();
+  *n = m;
+  if (cap < m) return AMR_ERR_CAPACITY;
+  if (!faces || !face_node) return AMR_ERR_ARG;
+  for (int64_t k = 0; k < m; ++k) faces[k] = t.leaf_faces[(size_t)k];
+  std::memcpy(face_node, t.face_node.data(), sizeof(int32_t) * 12 * (size_t)m);
+  return AMR_OK;
+}
+
 amr_status amr_get_brick(const amr_ctx* c, int32_t patch, float* out, int64_t cap, int64_t* n) {
   if (!c || !n) return AMR_ERR_ARG;
   if (!c->host_built) return AMR_ERR_STATE;
