@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
                      os.path.join(CSRC, f), "-o", obj])
     for f in cpp:
         obj = os.path.join(BUILD, f + ".o")
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall",
+        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fopenmp", "-Wall",
                      f"-I{cuda}/include", "-c", os.path.join(CSRC, f), "-o", obj])
 
     def run(cmd):
@@ -75,7 +75,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
                 print(err, file=sys.stderr)
     objs = [os.path.join(BUILD, f + ".o") for f in cu + cpp]
     tmp = LIB + f".{os.getpid()}.tmp"
-    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+    run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -115,7 +115,16 @@ amr_status build_bricks(amr_ctx* c) {
     double c1 = c01 * (1.0 - w[1]) + c11 * w[1];
     return c0 * (1.0 - w[2]) + c1 * w[2];
   };
-  for (int p : order) {
+  // levels in turn (a halo reads only coarser, completed bricks); patches of one level in
+  // parallel
+  bool uncovered = false;
+  size_t first = 0;
+  while (first < P) {
+    size_t last = first;
+    while (last < P && c->patches[order[last]].level == c->patches[order[first]].level) ++last;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long long oi = (long long)first; oi < (long long)last; ++oi) {
+    const int p = order[(size_t)oi];
     const Patch& pt = c->patches[p];
     const int l = pt.level;
     const int64_t sc = c->rpow[L - 1 - l];
@@ -159,15 +168,22 @@ amr_status build_bricks(amr_ctx* c) {
         if (interior_row) {
           std::memcpy(row + 1, pt.data.data() + (size_t)(pt.n[0] * ((bj - 1) + pt.n[1] * (bk - 1))),
                       sizeof(float) * (size_t)pt.n[0]);
-          if (!halo_value(0, bj, bk, row) || !halo_value(d0 - 1, bj, bk, row + d0 - 1))
-            return fail(c, AMR_ERR_DEVICE, "halo cell not covered by any coarser level");
+          if (!halo_value(0, bj, bk, row) || !halo_value(d0 - 1, bj, bk, row + d0 - 1)) {
+#pragma omp atomic write
+            uncovered = true;
+          }
         } else {
           for (int64_t bi = 0; bi < d0; ++bi)
-            if (!halo_value(bi, bj, bk, row + bi))
-              return fail(c, AMR_ERR_DEVICE, "halo cell not covered by any coarser level");
+            if (!halo_value(bi, bj, bk, row + bi)) {
+#pragma omp atomic write
+              uncovered = true;
+            }
         }
       }
   }
+    first = last;
+  }
+  if (uncovered) return fail(c, AMR_ERR_DEVICE, "halo cell not covered by any coarser level");
   // value range every sample of a leaf can reach: the brick cells under the trilinear
   // stencils of all points of the leaf box
   // (leaves first, then the pruned inner nodes of level-of-detail rendering)
@@ -175,7 +191,9 @@ amr_status build_bricks(amr_ctx* c) {
   const size_t M = t.leaf_patch.size(), ML = t.lod_patch.size();
   c->leaf_vmin.assign(M + ML, 0.0f);
   c->leaf_vmax.assign(M + ML, 0.0f);
-  for (size_t m = 0; m < M + ML; ++m) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long long mi = 0; mi < (long long)(M + ML); ++mi) {
+    const size_t m = (size_t)mi;
     const bool lod = m >= M;
     const int p = lod ? t.lod_patch[m - M] : t.leaf_patch[m];
     const int32_t* box = lod ? &t.lod_box[6 * (m - M)] : &t.leaf_box[6 * m];
@@ -212,7 +230,9 @@ amr_status build_bricks(amr_ctx* c) {
 amr_status build_gradient_bricks(amr_ctx* c) {
   const size_t P = c->patches.size();
   c->gbricks.assign(P, {});
-  for (size_t p = 0; p < P; ++p) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long long pi = 0; pi < (long long)P; ++pi) {
+    const size_t p = (size_t)pi;
     const int64_t d0 = c->patches[p].n[0] + 2, d1 = c->patches[p].n[1] + 2,
                   d2 = c->patches[p].n[2] + 2;
     const std::vector<float>& v = c->bricks[p];

@@ -263,7 +263,9 @@ amr_status upload(amr_ctx* c, void* stream_v) {
     // 16-bit cells (and 4 x 16-bit value + central differences)
     {
       std::vector<std::vector<uint16_t>> b16(P);
-      for (size_t p = 0; p < P; ++p) {
+#pragma omp parallel for schedule(dynamic, 4)
+      for (long long pi = 0; pi < (long long)P; ++pi) {
+        const size_t p = (size_t)pi;
         const std::vector<float>& b = c->bricks[p];
         b16[p].resize(b.size());
         for (size_t i = 0; i < b.size(); ++i) b16[p][i] = storage_bits(c->dtype, b[i]);
@@ -273,7 +275,9 @@ amr_status upload(amr_ctx* c, void* stream_v) {
     }
     if (c->want_gradient) {
       std::vector<std::vector<ushort4>> g16(P);
-      for (size_t p = 0; p < P; ++p) {
+#pragma omp parallel for schedule(dynamic, 4)
+      for (long long pi = 0; pi < (long long)P; ++pi) {
+        const size_t p = (size_t)pi;
         const std::vector<float4>& g = c->gbricks[p];
         g16[p].resize(g.size());
         for (size_t i = 0; i < g.size(); ++i)

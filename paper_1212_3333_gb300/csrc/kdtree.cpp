@@ -295,7 +295,9 @@ class Builder {
     t.face_node.assign(12 * t.leaf_patch.size(), 0);
     std::vector<int> node2pre(n);
     for (size_t k = 0; k < n; ++k) node2pre[order[k]] = (int)k;
-    for (size_t k = 0; k < n; ++k) {
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long long kk = 0; kk < (long long)n; ++kk) {
+      const size_t k = (size_t)kk;
       const BNode& b = nodes_[order[k]];
       if (b.axis >= 0) continue;
       const Patch& pt = c_->patches[b.patch];
