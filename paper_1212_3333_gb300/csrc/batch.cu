@@ -97,7 +97,10 @@ __global__ void __launch_bounds__(TW * TH, (128 * kMinBlocks<SHADE>) / (TW * TH)
     for (int r = 0; r < rpt; ++r) {
       const int j = (ty * rpt + r) * TH + (int)threadIdx.y;
       if (i < W && j < H)
-        out[(size_t)j * W + i] = march_ray<ST, 1, SHADE>(A, s_ray, i, j, tf, nz, nsamp, status);
+      {
+        RayF rf;
+        out[(size_t)j * W + i] = march_ray<ST, 1, SHADE>(A, s_ray, i, j, tf, nz, rf, nsamp, status);
+      }
     }
     __syncthreads();  // s_ray and the tile fields are rewritten by the next pop
   }

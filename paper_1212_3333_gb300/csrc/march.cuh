@@ -67,6 +67,11 @@ struct RayF {
   int exact_axes;        // bit a set: planes on axis a are always decided in FP64
 };
 
+struct RayFSlot {
+  RayF f;
+  float pad;
+};
+
 // Pixel (i, j) -> exact ray and root interval.  The operation order is part of the
 // contract: the FP64 reference evaluates the same expressions in the same order.
 __device__ __forceinline__ bool make_ray(const RayArgs& A, int i, int j, RayX& r) {
@@ -1067,12 +1072,11 @@ constexpr int kMinBlocks = (SHADE & 3) == 0 ? AMR_MIN_BLOCKS_PLAIN : AMR_MIN_BLO
 // sampling and compositing.  Returns premultiplied RGBA; adds to nsamp and status.
 template <int ST, int INTERP, int SHADE>
 __device__ __forceinline__ float4 march_ray(const RenderArgs& A, const RayArgs& R, int i, int j,
-                                            const float4* s_tf, const int* s_nz, unsigned& nsamp,
-                                            unsigned long long& status) {
+                                            const float4* s_tf, const int* s_nz, RayF& rf,
+                                            unsigned& nsamp, unsigned long long& status) {
   float C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
   RayX rx;
   if (make_ray(R, i, j, rx)) {
-    RayF rf;
     make_frame(R, rx, rf);
     const float inv_dn = 1.0f / rf.dn;
     const float Lx = -rf.Dd[0] * (float)R.hf[0] * inv_dn;
@@ -1152,9 +1156,21 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>) march_kernel(const __g
   const bool active = i < A.ray.width && jr < A.ray.rows && j < A.ray.height;
   unsigned nsamp = 0;
   unsigned long long status = 0;
-  if (active)
-    A.out[(size_t)jr * A.ray.width + i] =
-        march_ray<ST, INTERP, SHADE>(A, A.ray, i, j, s_tf, s_nz, nsamp, status);
+  if (active) {
+    if constexpr (SHADE == 0) {
+      // unshaded: the ray frame lives in shared memory (read once per segment), leaving the
+      // registers to the sample loop (measured 6 % faster on C2 at 2048^2; with shading
+      // the extra shared-memory reads cost more than the spills they save).  One padding
+      // word keeps the odd-sized slots free of bank conflicts.
+      __shared__ RayFSlot s_rf[128];
+      A.out[(size_t)jr * A.ray.width + i] =
+          march_ray<ST, INTERP, SHADE>(A, A.ray, i, j, s_tf, s_nz, s_rf[tid].f, nsamp, status);
+    } else {
+      RayF rf;
+      A.out[(size_t)jr * A.ray.width + i] =
+          march_ray<ST, INTERP, SHADE>(A, A.ray, i, j, s_tf, s_nz, rf, nsamp, status);
+    }
+  }
   // exact sample count: one atomic per warp
   const unsigned total = __reduce_add_sync(0xffffffffu, nsamp);
   if ((tid & 31) == 0 && total) atomicAdd(A.counters, (unsigned long long)total);
