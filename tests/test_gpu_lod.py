@@ -171,3 +171,24 @@ def test_pruned_c2_sampled(amr, c2, lod):
         if len(leaf):
             np.testing.assert_array_equal(seq[q, :len(leaf)], leaf)
             assert np.array_equal(tseq[q, :len(leaf), 0], t0)
+
+
+def test_pruned_16bit_cells(amr, c1):
+    """Pruning with FP16 cells: the pruned traversal is the FP32 one (it depends on the
+    geometry only), and the image stays close to the FP32-cell pruned image."""
+    w, o = c1
+    cam = synth.orbit_camera(4, 96, 80)
+    lod = _mid_lod(w["hier"], cam)
+    c32 = amr.from_hierarchy(w["hier"])
+    c32.amr_build_kdtree("ptr", gradient=True)
+    c16 = amr.from_hierarchy(w["hier"], "f16")
+    c16.amr_build_kdtree("ptr", gradient=True)
+    p, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1, lod_pixels=lod, ert_eps=0.0)
+    a, na = gpu_render(c32, cam, w["tf"], p)
+    b, nb = gpu_render(c16, cam, w["tf"], p)
+    assert na == nb
+    assert np.abs(a - b).max() < 2e-3
+    s32 = gpu_trace(c32, cam, max_len=512, lod_pixels=lod)
+    s16 = gpu_trace(c16, cam, max_len=512, lod_pixels=lod)
+    for x, y in zip(s32, s16):
+        assert np.array_equal(x, y)

@@ -52,13 +52,14 @@ def test_shadow_rejections(amr, c1):
     from paper_1212_3333_gb300 import _lib
 
     w, _ = c1
-    ctx = amr.from_hierarchy(w["hier"])
-    ctx.amr_build_kdtree("texobj")
     p, _ = params_pair(amr, w["vmin"], w["vmax"], shadow=1, light=(0.5, 0.5, 0.5),
                        light_step=0.01)
-    with pytest.raises(amr.AmrError) as e:
-        gpu_render(ctx, w["camera"], w["tf"], p)
-    assert e.value.status == _lib.AMR_ERR_ARG
+    for storage, dtype in (("texobj", "f32"), ("ptr", "f16")):
+        ctx = amr.from_hierarchy(w["hier"], dtype)
+        ctx.amr_build_kdtree(storage)
+        with pytest.raises(amr.AmrError) as e:
+            gpu_render(ctx, w["camera"], w["tf"], p)
+        assert e.value.status == _lib.AMR_ERR_ARG
     ctx = amr.from_hierarchy(w["hier"])
     ctx.amr_build_kdtree("ptr")
     for kw in (dict(schedule=1), dict(schedule=2), dict(interp=0), dict(light_step=0.0),
