@@ -131,6 +131,23 @@ class Proposal:
             losses.append(float(self.loss.item()))
         return losses
 
+    def save(self, path: str) -> None:
+        """Checkpoint: FP32 parameters, Adam moments and step count (.npz)."""
+        np.savez(path, params=self.params.cpu().numpy(), m=self.m.cpu().numpy(),
+                 v=self.v.cpu().numpy(), step=np.int64(self.step))
+
+    @classmethod
+    def load(cls, path: str) -> "Proposal":
+        """Resume from a checkpoint written by save()."""
+        import torch
+
+        z = np.load(path)
+        prop = cls(z["params"])
+        prop.m.copy_(torch.as_tensor(z["m"]))
+        prop.v.copy_(torch.as_tensor(z["v"]))
+        prop.step = int(z["step"])
+        return prop
+
     def pack(self, stream=None):
         _check(self._lib.amr_mlp_pack(C.c_void_p(_dptr(self.params)), C.c_void_p(_dptr(self.packed)),
                                       C.c_void_p(_stream_ptr(stream))), None)

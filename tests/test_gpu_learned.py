@@ -203,3 +203,21 @@ def test_coarse_factor_scales_the_sample_count(mods, c1_learned):
         with pytest.raises(amr.AmrError) as e:
             gpu_render(ctx, w["camera"], w["tf"], pl)
         assert e.value.status == _lib.AMR_ERR_ARG
+
+
+def test_checkpoint_resume_continues_training_exactly(mods, tmp_path):
+    torch, amr, proposal = mods
+    rng = np.random.default_rng(8)
+    x = torch.as_tensor(rng.uniform(0, 1, size=(4096, 12)).astype(np.float32), device="cuda")
+    t = torch.as_tensor(rng.uniform(0, 1, size=4096).astype(np.float32) ** 3, device="cuda")
+    a = proposal.Proposal(seed=3)
+    a.train(x, t, epochs=2, batch=1024, lr=1e-3)
+    path = str(tmp_path / "ckpt.npz")
+    a.save(path)
+    b = proposal.Proposal.load(path)
+    for p in (a, b):
+        p.loss_grad(x, t, 0, 1024, 1, 0)
+        p.adam(1e-3)
+    torch.cuda.synchronize()
+    assert a.step == b.step == 9
+    assert torch.equal(a.params, b.params) and torch.equal(a.m, b.m) and torch.equal(a.v, b.v)
