@@ -205,7 +205,7 @@ def test_coarse_factor_scales_the_sample_count(mods, c1_learned):
         assert e.value.status == _lib.AMR_ERR_ARG
 
 
-def test_checkpoint_resume_continues_training_exactly(mods, tmp_path):
+def test_checkpoint_resume_continues_training(mods, tmp_path):
     torch, amr, proposal = mods
     rng = np.random.default_rng(8)
     x = torch.as_tensor(rng.uniform(0, 1, size=(4096, 12)).astype(np.float32), device="cuda")
@@ -220,4 +220,6 @@ def test_checkpoint_resume_continues_training_exactly(mods, tmp_path):
         p.adam(1e-3)
     torch.cuda.synchronize()
     assert a.step == b.step == 9
-    assert torch.equal(a.params, b.params) and torch.equal(a.m, b.m) and torch.equal(a.v, b.v)
+    # (gradients are summed with atomics, so the last bits may differ between runs)
+    for u, w in ((a.params, b.params), (a.m, b.m), (a.v, b.v)):
+        torch.testing.assert_close(u, w, rtol=1e-5, atol=1e-8)
