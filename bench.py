@@ -170,8 +170,14 @@ def cpu_baseline(hier, cam, tf, vmin, vmax, shade, budget_s=15.0, seed=0):
         total_pix += n
         if dt < budget_s / 8:
             n *= 2
+    # one thread on a small sample, for the per-core rate
+    pix = np.stack([rng.integers(0, cam.width, 256), rng.integers(0, cam.height, 256)], 1)
+    t = time.perf_counter()
+    _, smp1 = o.render(cam, tf, op, pixels=pix.astype(np.int32), nthreads=1)
+    one = int(smp1.sum()) / (time.perf_counter() - t)
     return {"value": total_samples / total_s / 1e9, "unit": UNIT, "cores": threads,
-            "kind": "oracle",
+            "kind": "oracle", "host_cpus": os.cpu_count(),
+            "single_thread_msamples_s": one / 1e6,
             "sample": f"{total_pix} seeded random pixels of the {cam.width}x{cam.height} frame "
                       f"({total_samples} samples, {total_s:.1f} s), FP64 oracle, {threads} threads"}
 
