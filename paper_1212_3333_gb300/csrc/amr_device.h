@@ -5,6 +5,7 @@
 //                      c + 1), so the top of the tree is a contiguous prefix that one
 //                      cache line per few nodes serves to a whole warp (Sec. 3.2 stores the
 //                      second child at the next texel for the same reason).
+//   int4   node_box[2N] 32 B per node slot: its box (rope restarts).
 //   DLeaf  leaves[M]  48 B each, canonical (pre-order) leaf id order.
 //   DPatch patches[P] 48 B each: where a patch's brick lives and how to address it.
 //   bricks            one brick per patch with a one-cell halo (Sec. 4), float32, x fastest,
@@ -96,7 +97,9 @@ struct RenderArgs {
   const DLeaf* leaves;
   const int32_t* face_node;    // per leaf, 12: per face (2a + side) the node slot holding the
                                // leaf and the cell beyond the face, then the cell alone
-                               // (starts of neighbour lookups)
+                               // (starts of neighbour lookups; the second half: ropes)
+  const int4* node_box;        // per node slot, 2: box lo (x, y, z, 0), hi (x, y, z, 0),
+                               // finest cells (rope restarts)
   const DPatch* patches;
   const void* pool;            // linear atlas base (element type of the storage)
   const float4* gpool;         // linear atlas of gradient bricks (float4 per cell)
@@ -125,6 +128,8 @@ struct TraceArgs {
   RayArgs ray;
   DLevel lv[kMaxLevels];
   const DNode* nodes;
+  const int32_t* face_node;
+  const int4* node_box;
   int32_t* leaf_seq;
   double* t_seq;
   int32_t* seq_len;

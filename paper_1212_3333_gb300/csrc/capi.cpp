@@ -321,6 +321,7 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->nodes = c->dev.nodes;
   a->leaves = c->dev.leaves;
   a->face_node = c->dev.face_node;
+  a->node_box = c->dev.node_box;
   a->patches = c->dev.patches;
   a->pool = c->dev.pool;
   a->gpool = (const float4*)c->dev.gpool;
@@ -788,6 +789,8 @@ amr_status amr_trace(amr_ctx* c, const amr_camera* cam, double lod_pixels, int32
   a.ray.lod_scale = lod_scale(cam, lod_pixels);
   a.ray.lod_scale_f = (float)a.ray.lod_scale;
   a.nodes = c->dev.nodes;
+  a.face_node = c->dev.face_node;
+  a.node_box = c->dev.node_box;
   a.leaf_seq = leaf_seq_dev;
   a.t_seq = t_seq_dev;
   a.seq_len = seq_len_dev;

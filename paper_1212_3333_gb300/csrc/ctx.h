@@ -65,6 +65,7 @@ struct DeviceState {
   size_t img_scratch_bytes = 0;
   int32_t* lod = nullptr;                        // per node slot: (id << 5 | level) or -1
   int32_t* face_node = nullptr;                  // per leaf and face: node slot (neighbour start)
+  int4* node_box = nullptr;                      // per node slot: box lo, hi (ropes)
   int device = -1;
 };
 

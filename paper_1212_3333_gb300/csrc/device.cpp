@@ -19,20 +19,31 @@ namespace {
   } while (0)
 
 // breadth-first re-layout: children of a node are adjacent, the top levels contiguous;
-// lod receives each slot's pruned-leaf entry (id << 5 | level) or -1
-std::vector<DNode> layout_nodes(const Tree& t, std::vector<int32_t>& lod,
-                                std::vector<int32_t>& slot_of) {
+// lod receives each slot's pruned-leaf entry (id << 5 | level) or -1, box each slot's box
+// (lo, hi as two int4, finest cells) starting from the root box
+std::vector<DNode> layout_nodes(const Tree& t, const int64_t* root, std::vector<int32_t>& lod,
+                                std::vector<int32_t>& slot_of, std::vector<int4>& box) {
   const size_t n = t.axis.size();
   std::vector<DNode> out(n);
   lod.assign(n, -1);
   slot_of.assign(n, 0);
-  std::deque<std::pair<int, int>> q;  // (pre-order id, bfs slot)
-  q.push_back({0, 0});
+  box.assign(2 * std::max<size_t>(n, 1), make_int4(0, 0, 0, 0));
+  struct Item {
+    int pre, slot;
+    int32_t b[6];
+  };
+  std::deque<Item> q;
+  Item r{0, 0, {}};
+  for (int k = 0; k < 6; ++k) r.b[k] = (int32_t)root[k];
+  q.push_back(r);
   int next = 1;
   while (!q.empty()) {
-    auto [pre, slot] = q.front();
+    const Item it = q.front();
     q.pop_front();
+    const int pre = it.pre, slot = it.slot;
     slot_of[pre] = slot;
+    box[2 * (size_t)slot] = make_int4(it.b[0], it.b[1], it.b[2], 0);
+    box[2 * (size_t)slot + 1] = make_int4(it.b[3], it.b[4], it.b[5], 0);
     DNode d;
     if (t.axis[pre] < 0) {
       d.meta = ((uint32_t)kLeafAxis << 30) | ((uint32_t)t.leaf[pre] & kIndexMask);
@@ -40,10 +51,16 @@ std::vector<DNode> layout_nodes(const Tree& t, std::vector<int32_t>& lod,
     } else {
       int first = next;
       next += 2;
-      d.meta = ((uint32_t)t.axis[pre] << 30) | ((uint32_t)first & kIndexMask);
+      const int ax = t.axis[pre];
+      d.meta = ((uint32_t)ax << 30) | ((uint32_t)first & kIndexMask);
       d.split = t.split[pre];
-      q.push_back({t.left[pre], first});
-      q.push_back({t.right[pre], first + 1});
+      Item lc{t.left[pre], first, {}}, rc{t.right[pre], first + 1, {}};
+      std::memcpy(lc.b, it.b, sizeof lc.b);
+      std::memcpy(rc.b, it.b, sizeof rc.b);
+      lc.b[3 + ax] = t.split[pre];
+      rc.b[ax] = t.split[pre];
+      q.push_back(lc);
+      q.push_back(rc);
     }
     out[slot] = d;
     const int32_t q = t.node_lod.empty() ? -1 : t.node_lod[pre];
@@ -193,6 +210,7 @@ void release_device(amr_ctx* c) {
   cudaFree(d.nodes);
   cudaFree(d.lod);
   cudaFree(d.face_node);
+  cudaFree(d.node_box);
   cudaFree(d.leaves);
   cudaFree(d.patches);
   cudaFree(d.pool);
@@ -215,7 +233,8 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   if (t.axis.size() >= (size_t)kIndexMask || M >= (size_t)kIndexMask)
     return fail(c, AMR_ERR_CAPACITY, "tree too large for 30-bit node indices");
   std::vector<int32_t> lodv, slot_of;
-  std::vector<DNode> nodes = layout_nodes(t, lodv, slot_of);
+  std::vector<int4> boxes;
+  std::vector<DNode> nodes = layout_nodes(t, c->root, lodv, slot_of, boxes);
   std::vector<int32_t> face_slots(std::max<size_t>(1, t.face_node.size()), 0);
   for (size_t k = 0; k < t.face_node.size(); ++k) face_slots[k] = slot_of[t.face_node[k]];
   const size_t ML = t.lod_patch.size();
@@ -246,6 +265,7 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   CK(cudaMalloc(&d.nodes, nodes.size() * sizeof(DNode)));
   CK(cudaMalloc(&d.lod, lodv.size() * sizeof(int32_t)));
   CK(cudaMalloc(&d.face_node, face_slots.size() * sizeof(int32_t)));
+  CK(cudaMalloc(&d.node_box, boxes.size() * sizeof(int4)));
   CK(cudaMalloc(&d.leaves, std::max<size_t>(1, M + ML) * sizeof(DLeaf)));
   CK(cudaMalloc(&d.patches, P * sizeof(DPatch)));
   CK(cudaMalloc(&d.counters, kNumCounters * sizeof(unsigned long long)));
@@ -294,6 +314,8 @@ amr_status upload(amr_ctx* c, void* stream_v) {
                      stream));
   CK(cudaMemcpyAsync(d.face_node, face_slots.data(), face_slots.size() * sizeof(int32_t),
                      cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(d.node_box, boxes.data(), boxes.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                     stream));
   if (M + ML)
     CK(cudaMemcpyAsync(d.leaves, leaves.data(), (M + ML) * sizeof(DLeaf), cudaMemcpyHostToDevice,
                        stream));

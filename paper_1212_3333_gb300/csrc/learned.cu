@@ -74,11 +74,14 @@ __global__ void __launch_bounds__(128) log_kernel(const __grid_constant__ Render
   int pid0 = kPidIn;
   float tau0 = 0.0f, e0 = 0.0f;
   uint32_t start = 0;
+  int prev = -1;
   for (int seg = 0; pid0 != kPidOut && seg < A.max_segments; ++seg) {
     int pid1 = kPidOut;
     float tau1 = rf.tau_out, e1 = exit_bound(rf);
-    const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
+    const int lid = next_leaf(A.nodes, A.face_node, A.node_box, A.ray, i, j, rf, start, prev, pid0,
+                              tau0, e0, pid1, tau1, e1);
     if (lid < 0) break;
+    prev = lid;
     const DLeaf lf = A.leaves[lid];
     const DLevel& lv = A.lv[lf.level];
     int n = min(segment_count(A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv),
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
   int pid0 = kPidIn;
   float tau0 = 0.0f, e0 = 0.0f;
   uint32_t start = 0;
-  int nseg = 0;
+  int nseg = 0, prev = -1;
   while (__any_sync(0xffffffffu, live)) {
     int n = 0, lid = -1, pid1 = kPidOut;
     float tau1 = 0.0f, e1 = 0.0f;
@@ -169,11 +172,13 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
         ++nseg;
         tau1 = rf.tau_out;
         e1 = exit_bound(rf);
-        lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
+        lid = next_leaf(A.nodes, A.face_node, A.node_box, A.ray, i, j, rf, start, prev, pid0, tau0,
+                        e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;
           live = false;
         } else {
+          prev = lid;
           lf = A.leaves[lid];
           n = segment_count(A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, A.lv[lf.level]);
           if (n > kMaxSamplesPerSegment) {

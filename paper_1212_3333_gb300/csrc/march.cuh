@@ -258,6 +258,17 @@ __device__ __forceinline__ int lod_stop(const RayArgs& R, uint32_t i, int lod_mi
   return (q >= 0 && (q & 31) >= lod_min) ? (q >> 5) : -1;
 }
 
+// FP32 ray parameter tau_s of split plane s on axis ax and its error bound (infinite on
+// the axes whose planes are always decided in FP64).
+__device__ __forceinline__ float plane_tau(const RayF& rf, uint32_t ax, int s, float& es) {
+  const float sf = (float)s;
+  const float ts = fmaf(sf, sel3f(ax, rf.B[0], rf.B[1], rf.B[2]), sel3f(ax, rf.C[0], rf.C[1], rf.C[2])) +
+                   fmaf(sf, sel3f(ax, rf.Bl[0], rf.Bl[1], rf.Bl[2]),
+                        sel3f(ax, rf.Cl[0], rf.Cl[1], rf.Cl[2]));
+  es = ((rf.exact_axes >> ax) & 1) ? __int_as_float(0x7f800000) : ldexpf(fabsf(ts) + 1.0f, -22);
+  return ts;
+}
+
 // kd-restart descent (Sec. 3.3) for the segment starting at (pid0, tau0): returns the leaf
 // holding the ray just after t0 and narrows (pid1, tau1, e1) to the first split plane
 // beyond t0.  Near child = the side entered first (d_a > 0: lower); t_s >= t1 -> near
@@ -271,12 +282,17 @@ __device__ __forceinline__ int lod_stop(const RayArgs& R, uint32_t i, int lod_mi
 // and the same t1 bit for bit.  With level-of-detail pruning on, `start` stays at or above
 // every type-(a) node on the path: the pruning bound grows with t0, so a later segment
 // may stop at an ancestor that this one passed.
-__device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const RayArgs& A, int px,
-                                       int py, const RayF& rf, uint32_t& start, int pid0,
-                                       float tau0, float e0, int& pid1, float& tau1, float& e1,
-                                       int lod_min = kNoLod) {
-  uint32_t i = start;
-  bool pushing = true;  // no narrowing yet: the chosen child still holds all of [t0, t_out]
+//
+// `from` is where the descent begins: `start` itself (push = true), or a node known to hold
+// the ray just after t0 whose ancestors' narrowing the caller has already applied (a rope,
+// push = false: `start` is left as it is).
+__device__ __forceinline__ int descend_from(const DNode* __restrict__ nodes, const RayArgs& A,
+                                            int px, int py, const RayF& rf, uint32_t from,
+                                            bool push, uint32_t& start, int pid0, float tau0,
+                                            float e0, int& pid1, float& tau1, float& e1,
+                                            int lod_min) {
+  uint32_t i = from;
+  bool pushing = push;  // no narrowing yet: the chosen child still holds all of [t0, t_out]
   for (int depth = 0; depth < kMaxDepth; ++depth) {
     const DNode nd = nodes[i];
     const uint32_t ax = nd.meta >> 30;
@@ -305,12 +321,8 @@ __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const Ra
     } else if (pid == pid1) {  // the plane that produced t1: t_s == t1
       i = near_c;
     } else {
-      const float sf = (float)nd.split;
-      const float ts = fmaf(sf, B, sel3f(ax, rf.C[0], rf.C[1], rf.C[2])) +
-                       fmaf(sf, sel3f(ax, rf.Bl[0], rf.Bl[1], rf.Bl[2]),
-                            sel3f(ax, rf.Cl[0], rf.Cl[1], rf.Cl[2]));
-      const float es = ((rf.exact_axes >> ax) & 1) ? __int_as_float(0x7f800000)
-                                                   : ldexpf(fabsf(ts) + 1.0f, -22);
+      float es;
+      const float ts = plane_tau(rf, ax, nd.split, es);
       if (ts - tau1 > es + e1) {
         i = near_c;
       } else if (tau0 - ts > es + e0) {
@@ -333,6 +345,89 @@ __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const Ra
     if (pushing) start = i;
   }
   return -1;
+}
+
+__device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const RayArgs& A, int px,
+                                       int py, const RayF& rf, uint32_t& start, int pid0,
+                                       float tau0, float e0, int& pid1, float& tau1, float& e1,
+                                       int lod_min = kNoLod) {
+  return descend_from(nodes, A, px, py, rf, start, true, start, pid0, tau0, e0, pid1, tau1, e1,
+                      lod_min);
+}
+
+// Rope restart (neighbour links in the manner of Havran's ropes; the paper restarts every
+// segment by kd-restart).  The segment after leaf `prev`, which the ray left through its
+// face on plane pid0, begins in node N = the deepest node holding the level cell beyond
+// that face (second half of the face table).  A descent from N reaches the same leaf as one
+// from the root whenever the ray just after t0 lies in N's box; and the planes the root
+// descent would narrow (t1) to above N are N's ancestors' planes, of which only N's own
+// exit planes can be nearest, so these are applied first (the root's faces are t_out
+// already).  Both steps use the FP32 filter, narrowing falls back to the exact decision;
+// when containment is too close to call (the ray passes near an edge of N) this returns
+// false and the caller descends from the push-down start.  On the exit-face axis the ray
+// is inside N (N's lower side on that axis is the face or behind it); on an axis the ray
+// runs parallel to, its coordinate stays inside the face's extent, which N holds.
+__device__ __forceinline__ bool rope_start(const int32_t* __restrict__ face_node,
+                                           const int4* __restrict__ node_box, const RayArgs& R,
+                                           int px, int py, const RayF& rf, int prev, int pid0,
+                                           float tau0, float e0, uint32_t& node, int& pid1,
+                                           float& tau1, float& e1) {
+  const int a = pid0 & 3;
+  const bool up = sel3f(a, rf.B[0], rf.B[1], rf.B[2]) > 0.0f;
+  const uint32_t nd = (uint32_t)__ldg(face_node + 12 * prev + 6 + 2 * a + (up ? 1 : 0));
+  const int4 lo = __ldg(node_box + 2 * nd), hi = __ldg(node_box + 2 * nd + 1);
+  const int blo[3] = {lo.x, lo.y, lo.z}, bhi[3] = {hi.x, hi.y, hi.z};
+  int pid[3];
+  float ts[3], es[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    pid[b] = -1;
+    const float Bb = rf.B[b];
+    if (Bb == 0.0f) continue;
+    const bool fwd = Bb > 0.0f;
+    const int s_in = fwd ? blo[b] : bhi[b], s_out = fwd ? bhi[b] : blo[b];
+    if (b != a && s_in != (fwd ? R.root_f[b] : R.root_f[3 + b])) {
+      float e;
+      const float t = plane_tau(rf, b, s_in, e);
+      if (!(tau0 - t > e + e0)) return false;  // N entered at or after t0 on this axis
+    }
+    if (s_out != (fwd ? R.root_f[3 + b] : R.root_f[b])) {
+      ts[b] = plane_tau(rf, b, s_out, es[b]);
+      if (b != a && !(ts[b] - tau0 > es[b] + e0)) return false;  // N left by t0
+      pid[b] = s_out * 4 + b;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (pid[b] < 0 || ts[b] - tau1 > es[b] + e1) continue;  // certainly not before t1
+    const bool narrow = (tau1 - ts[b] > es[b] + e1 && ts[b] - tau0 > es[b] + e0) ||
+                        exact_decide(R, px, py, pid[b], pid0, pid1) == 2;
+    if (narrow) {
+      pid1 = pid[b];
+      tau1 = ts[b];
+      e1 = es[b];
+    }
+  }
+  node = nd;
+  return true;
+}
+
+// Leaf of the segment starting at (pid0, tau0) that follows leaf `prev` (-1 on the first
+// segment): by rope while pruning is off, else (or when the rope's filter cannot decide)
+// by the push-down descent.  The leaf and the exact t1 are the same either way; only the
+// plane id recorded for t1 may differ, between planes whose t1 is the same FP64 value.
+__device__ __forceinline__ int next_leaf(const DNode* __restrict__ nodes,
+                                         const int32_t* __restrict__ face_node,
+                                         const int4* __restrict__ node_box, const RayArgs& R,
+                                         int px, int py, const RayF& rf, uint32_t& start,
+                                         int prev, int pid0, float tau0, float e0, int& pid1,
+                                         float& tau1, float& e1, int lod_min = kNoLod) {
+  uint32_t nd;
+  if (prev >= 0 && !(R.lod_scale_f > 0.0f) &&
+      rope_start(face_node, node_box, R, px, py, rf, prev, pid0, tau0, e0, nd, pid1, tau1, e1))
+    return descend_from(nodes, R, px, py, rf, nd, false, start, pid0, tau0, e0, pid1, tau1, e1,
+                        lod_min);
+  return descend(nodes, R, px, py, rf, start, pid0, tau0, e0, pid1, tau1, e1, lod_min);
 }
 
 // Point location by integer finest-cell coordinates (left iff f_a < split), stopping at a
@@ -1085,7 +1180,7 @@ __device__ __forceinline__ float4 march_ray(const RenderArgs& A, const RayArgs& 
     int pid0 = kPidIn;
     float tau0 = 0.0f, e0 = 0.0f;
     uint32_t start = 0;
-    int seg = 0;
+    int seg = 0, prev = -1;
     while (pid0 != kPidOut) {
       if (seg >= A.max_segments) {
         status |= kStatusCapacity;
@@ -1095,11 +1190,13 @@ __device__ __forceinline__ float4 march_ray(const RenderArgs& A, const RayArgs& 
       int pid1 = kPidOut;
       float tau1 = rf.tau_out, e1 = exit_bound(rf);
       const int lmin = lod_min_level(R, A.lv, rf, i, j, pid0, tau0, e0);
-      const int lid = descend(A.nodes, R, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1, lmin);
+      const int lid = next_leaf(A.nodes, A.face_node, A.node_box, R, i, j, rf, start, prev, pid0,
+                                tau0, e0, pid1, tau1, e1, lmin);
       if (lid < 0) {
         status |= kStatusDevice;
         break;
       }
+      prev = lid;
       const DLeaf lf = A.leaves[lid];
       const DLevel& lv = A.lv[lf.level];
       int n = segment_count(R, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv);

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
   RayF rf;
   float Lx = 0.f, Ly = 0.f, Lz = 0.f;
   float C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
-  int pid0 = kPidOut, seg = 0;
+  int pid0 = kPidOut, seg = 0, prev = -1;
   float tau0 = 0.f, e0 = 0.f;
   uint32_t start = 0;
   SegSetup g;
@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
               e0 = 0.f;
               start = 0;
               seg = 0;
+              prev = -1;
               k = 0;
               g.s.n = 0;
               live = true;
@@ -132,13 +133,14 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
           int pid1 = kPidOut;
           float tau1 = rf.tau_out, e1 = exit_bound(rf);
           const int lmin = lod_min_level(R, A.lv, rf, i, R.row0 + jr, pid0, tau0, e0);
-          const int lid = descend(A.nodes, R, i, R.row0 + jr, rf, start, pid0, tau0, e0, pid1,
-                                  tau1, e1, lmin);
+          const int lid = next_leaf(A.nodes, A.face_node, A.node_box, R, i, R.row0 + jr, rf,
+                                    start, prev, pid0, tau0, e0, pid1, tau1, e1, lmin);
           if (lid < 0) {
             status |= kStatusDevice;
             finish();
             break;
           }
+          prev = lid;
           const DLeaf lf = A.leaves[lid];
           const DLevel& lv = A.lv[lf.level];
           int n = segment_count(R, i, R.row0 + jr, rf, pid0, tau0, e0, pid1, tau1, e1, lv);

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
   int pid0 = kPidIn;
   float tau0 = 0.0f, e0 = 0.0f;
   uint32_t start = 0;
-  int nseg = 0;
+  int nseg = 0, prev = -1;
   const float one_minus_eps = A.ert_thresh;  // include a sample while 1 - T < 1 - eps
 
   while (__any_sync(0xffffffffu, live)) {
@@ -111,11 +111,13 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
         ++nseg;
         int pid1 = kPidOut;
         float tau1 = rf.tau_out, e1 = exit_bound(rf);
-        const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1);
+        const int lid = next_leaf(A.nodes, A.face_node, A.node_box, A.ray, i, j, rf, start, prev,
+                                  pid0, tau0, e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;
           live = false;
         } else {
+          prev = lid;
           const DLeaf lf = A.leaves[lid];
           const DLevel& lv = A.lv[lf.level];
           n = segment_count(A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv);

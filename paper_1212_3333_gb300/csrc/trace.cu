@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
   int pid0 = kPidIn;
   float tau0 = 0.0f, e0 = 0.0f;
   uint32_t start = 0;
-  int n = 0;
+  int n = 0, prev = -1;
   unsigned long long status = 0;
   while (pid0 != kPidOut) {
     if (n >= A.max_segments) {
@@ -28,11 +28,13 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
     int pid1 = kPidOut;
     float tau1 = rf.tau_out, e1 = exit_bound(rf);
     const int lmin = lod_min_level(A.ray, A.lv, rf, i, j, pid0, tau0, e0);
-    const int lid = descend(A.nodes, A.ray, i, j, rf, start, pid0, tau0, e0, pid1, tau1, e1, lmin);
+    const int lid = next_leaf(A.nodes, A.face_node, A.node_box, A.ray, i, j, rf, start, prev, pid0,
+                              tau0, e0, pid1, tau1, e1, lmin);
     if (lid < 0) {
       status |= kStatusDevice;
       break;
     }
+    prev = lid;
     if (n < A.max_len) {
       const size_t q = p * (size_t)A.max_len + n;
       A.leaf_seq[q] = lid;
