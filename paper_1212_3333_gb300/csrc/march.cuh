@@ -776,6 +776,29 @@ __device__ __forceinline__ float neighbour_value(const RenderArgs& A, const RayA
                                     s.margin, bn[0], bn[1], bn[2], AX, (float)SG);
 }
 
+// neighbour_value with the axis and sign as run-time values (bn: the neighbour position).
+template <int ST, int INTERP>
+__device__ __forceinline__ float neighbour_at(const RenderArgs& A, const RayArgs& R,
+                                              const SegState& s, const float* bn, int k, int ax,
+                                              float sg) {
+  const float m = s.margin;
+  bool inside = true;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) inside = inside && (bn[q] >= s.bl[q] + m) && (bn[q] < s.bh[q] - m);
+  if (inside) {
+    if constexpr (INTERP == 1) {
+      return trilinear<ST>(A, s.brick, bn[0], bn[1], bn[2]);
+    } else {
+      const float fx = bn[0] + 0.5f, fy = bn[1] + 0.5f, fz = bn[2] + 0.5f;
+      const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
+      if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > m)
+        return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
+    }
+  }
+  return neighbour_slow<ST, INTERP>(A, R, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k, s.margin,
+                                    bn[0], bn[1], bn[2], ax, sg);
+}
+
 // Value at the sample itself (the segment's own leaf and level, Sec. 3.3).
 template <int ST, int INTERP>
 __device__ __forceinline__ float sample_value(const RenderArgs& A, const RayArgs& R,
@@ -921,12 +944,25 @@ __device__ __forceinline__ void gradient(const RenderArgs& A, const RayArgs& R, 
       return;
     }
   }
-  g[0] = (neighbour_value<ST, INTERP, 0, 1>(A, R, s, beta, k) -
-          neighbour_value<ST, INTERP, 0, -1>(A, R, s, beta, k)) * (0.5f * (float)lv.inv_h[0]);
-  g[1] = (neighbour_value<ST, INTERP, 1, 1>(A, R, s, beta, k) -
-          neighbour_value<ST, INTERP, 1, -1>(A, R, s, beta, k)) * (0.5f * (float)lv.inv_h[1]);
-  g[2] = (neighbour_value<ST, INTERP, 2, 1>(A, R, s, beta, k) -
-          neighbour_value<ST, INTERP, 2, -1>(A, R, s, beta, k)) * (0.5f * (float)lv.inv_h[2]);
+  // one rolled loop over the six neighbours (+x, -x, +y, -y, +z, -z) keeps a single copy
+  // of the lookup code in the kernel
+  float d[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 1
+  for (int q = 0; q < 6; ++q) {
+    const int ax = q >> 1;
+    const float sg = (q & 1) ? -1.0f : 1.0f;
+    float bn[3] = {beta[0], beta[1], beta[2]};
+    bn[0] += ax == 0 ? sg : 0.0f;
+    bn[1] += ax == 1 ? sg : 0.0f;
+    bn[2] += ax == 2 ? sg : 0.0f;
+    const float v = neighbour_at<ST, INTERP>(A, R, s, bn, k, ax, sg);
+    d[0] += ax == 0 ? sg * v : 0.0f;
+    d[1] += ax == 1 ? sg * v : 0.0f;
+    d[2] += ax == 2 ? sg * v : 0.0f;
+  }
+  g[0] = d[0] * (0.5f * (float)lv.inv_h[0]);
+  g[1] = d[1] * (0.5f * (float)lv.inv_h[1]);
+  g[2] = d[2] * (0.5f * (float)lv.inv_h[2]);
 }
 
 // A segment ready for sampling: its state, first sample position and step in brick
