@@ -6,11 +6,13 @@
 //                      cache line per few nodes serves to a whole warp (Sec. 3.2 stores the
 //                      second child at the next texel for the same reason).
 //   int4   node_box[2N] 32 B per node slot: its box (rope restarts).
-//   DLeaf  leaves[M]  48 B each, canonical (pre-order) leaf id order.
+//   DLeaf  leaves[M]  96 B each, canonical (pre-order) leaf id order, with the
+//                      addressing of the leaf's brick.
 //   DPatch patches[P] 48 B each: where a patch's brick lives and how to address it.
 //   bricks            one brick per patch with a one-cell halo (Sec. 4), float32, x fastest,
 //                      in the layout of the chosen storage strategy.
 #pragma once
+#include <stddef.h>
 #include <stdint.h>
 
 #include <cuda_runtime.h>
@@ -22,6 +24,7 @@ constexpr int kLeafAxis = 3;            // DNode axis value that marks a leaf
 constexpr uint32_t kIndexMask = 0x3fffffffu;
 constexpr int kMaxDepth = 256;          // descent bound (tree depth is checked at build)
 constexpr int kMaxSamplesPerSegment = 1 << 22;
+constexpr uint32_t kFaceLeaf = 0x80000000u;  // face-table entry names a leaf (id in bits 0..30)
 
 // device counters: [0] samples, [1] status bits, [2] exact descent decisions,
 // [3] exact sample counts, [4] exact neighbour / nearest positions
@@ -38,15 +41,26 @@ struct DNode {
   int32_t split;  // split plane, finest-level cell index
 };
 
-struct DLeaf {
+// A leaf with the addressing of its patch's brick: a segment start or a cross-leaf lookup
+// reads one record instead of a leaf and then its patch (one dependent load less).
+struct alignas(16) DLeaf {
+  long long base;        // brick (DPatch::base), the same for every leaf of a patch
+  long long gbase;       // gradient brick (DPatch::gbase)
   int32_t lo[3], hi[3];  // box, finest-level cells
   int32_t patch;
   int32_t level;
   float vmin, vmax;      // range of every value a sample of this leaf can interpolate
   int32_t faces;         // bit 2a (+1): the level cell beyond the lower (upper) face on axis
                          // a lies in the same patch and is not refined
+  int32_t sy, sz;        // brick strides (DPatch::sy, sz)
+  int32_t blo[3];        // brick: patch box lo (DPatch::lo)
+  int32_t dim[3];        // brick extent with halo (DPatch::dim)
   int32_t pad;
 };
+static_assert(sizeof(DLeaf) == 96, "DLeaf is six 16-byte words");
+// lo and hi fill the record's second 16-byte word and half its third (rope restarts read
+// them as two int4)
+static_assert(offsetof(DLeaf, lo) == 16 && offsetof(DLeaf, hi) == 28, "DLeaf box layout");
 
 struct DPatch {
   long long base;      // pointer table: device address of the brick; linear atlas: element
@@ -97,7 +111,8 @@ struct RenderArgs {
   const DLeaf* leaves;
   const int32_t* face_node;    // per leaf, 12: per face (2a + side) the node slot holding the
                                // leaf and the cell beyond the face, then the cell alone
-                               // (starts of neighbour lookups; the second half: ropes)
+                               // (starts of neighbour lookups; the second half: ropes);
+                               // an entry with kFaceLeaf set names a leaf id instead
   const int4* node_box;        // per node slot, 2: box lo (x, y, z, 0), hi (x, y, z, 0),
                                // finest cells (rope restarts)
   const DPatch* patches;
@@ -128,6 +143,7 @@ struct TraceArgs {
   RayArgs ray;
   DLevel lv[kMaxLevels];
   const DNode* nodes;
+  const DLeaf* leaves;
   const int32_t* face_node;
   const int4* node_box;
   int32_t* leaf_seq;

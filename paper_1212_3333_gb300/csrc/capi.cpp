@@ -789,6 +789,7 @@ amr_status amr_trace(amr_ctx* c, const amr_camera* cam, double lod_pixels, int32
   a.ray.lod_scale = lod_scale(cam, lod_pixels);
   a.ray.lod_scale_f = (float)a.ray.lod_scale;
   a.nodes = c->dev.nodes;
+  a.leaves = c->dev.leaves;
   a.face_node = c->dev.face_node;
   a.node_box = c->dev.node_box;
   a.leaf_seq = leaf_seq_dev;

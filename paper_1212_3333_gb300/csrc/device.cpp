@@ -236,7 +236,10 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   std::vector<int4> boxes;
   std::vector<DNode> nodes = layout_nodes(t, c->root, lodv, slot_of, boxes);
   std::vector<int32_t> face_slots(std::max<size_t>(1, t.face_node.size()), 0);
-  for (size_t k = 0; k < t.face_node.size(); ++k) face_slots[k] = slot_of[t.face_node[k]];
+  for (size_t k = 0; k < t.face_node.size(); ++k) {
+    const int32_t pre = t.face_node[k];
+    face_slots[k] = t.axis[pre] < 0 ? (int32_t)(kFaceLeaf | (uint32_t)t.leaf[pre]) : slot_of[pre];
+  }
   const size_t ML = t.lod_patch.size();
   if (M + ML >= ((size_t)1 << 26)) return fail(c, AMR_ERR_CAPACITY, "too many leaves");
   std::vector<DLeaf> leaves(M + ML);
@@ -316,6 +319,17 @@ amr_status upload(amr_ctx* c, void* stream_v) {
                      cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(d.node_box, boxes.data(), boxes.size() * sizeof(int4), cudaMemcpyHostToDevice,
                      stream));
+  for (DLeaf& l : leaves) {  // brick addressing, now that the bricks are placed
+    const DPatch& q = pt[(size_t)l.patch];
+    l.base = q.base;
+    l.gbase = q.gbase;
+    l.sy = q.sy;
+    l.sz = q.sz;
+    for (int a = 0; a < 3; ++a) {
+      l.blo[a] = q.lo[a];
+      l.dim[a] = q.dim[a];
+    }
+  }
   if (M + ML)
     CK(cudaMemcpyAsync(d.leaves, leaves.data(), (M + ML) * sizeof(DLeaf), cudaMemcpyHostToDevice,
                        stream));

@@ -358,25 +358,37 @@ __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const Ra
 // Rope restart (neighbour links in the manner of Havran's ropes; the paper restarts every
 // segment by kd-restart).  The segment after leaf `prev`, which the ray left through its
 // face on plane pid0, begins in node N = the deepest node holding the level cell beyond
-// that face (second half of the face table).  A descent from N reaches the same leaf as one
-// from the root whenever the ray just after t0 lies in N's box; and the planes the root
-// descent would narrow (t1) to above N are N's ancestors' planes, of which only N's own
-// exit planes can be nearest, so these are applied first (the root's faces are t_out
-// already).  Both steps use the FP32 filter, narrowing falls back to the exact decision;
-// when containment is too close to call (the ray passes near an edge of N) this returns
-// false and the caller descends from the push-down start.  On the exit-face axis the ray
-// is inside N (N's lower side on that axis is the face or behind it); on an axis the ray
-// runs parallel to, its coordinate stays inside the face's extent, which N holds.
-__device__ __forceinline__ bool rope_start(const int32_t* __restrict__ face_node,
-                                           const int4* __restrict__ node_box, const RayArgs& R,
-                                           int px, int py, const RayF& rf, int prev, int pid0,
-                                           float tau0, float e0, uint32_t& node, int& pid1,
-                                           float& tau1, float& e1) {
+// that face (second half of the face table; often a leaf, which the table then names).
+// A descent from N reaches the same leaf as one from the root whenever the ray just after
+// t0 lies in N's box; and the planes the root descent would narrow (t1) to above N are
+// N's ancestors' planes, of which only N's own exit planes can be nearest, so these are
+// applied first (the root's faces are t_out already).  Both steps use the FP32 filter,
+// narrowing falls back to the exact decision; when containment is too close to call (the
+// ray passes near an edge of N) the caller descends from the push-down start.  On the
+// exit-face axis the ray is inside N (N's lower side on that axis is the face or behind
+// it); on an axis the ray runs parallel to, its coordinate stays inside the face's extent,
+// which N holds.  Returns the leaf when N is one (nothing left to descend), -2 - N's slot
+// for an inner node, -1 for no rope.
+__device__ __forceinline__ int rope_start(const int32_t* __restrict__ face_node,
+                                          const int4* __restrict__ node_box,
+                                          const DLeaf* __restrict__ leaves, const RayArgs& R,
+                                          int px, int py, const RayF& rf, int prev, int pid0,
+                                          float tau0, float e0, int& pid1, float& tau1,
+                                          float& e1) {
   const int a = pid0 & 3;
   const bool up = sel3f(a, rf.B[0], rf.B[1], rf.B[2]) > 0.0f;
-  const uint32_t nd = (uint32_t)__ldg(face_node + 12 * prev + 6 + 2 * a + (up ? 1 : 0));
-  const int4 lo = __ldg(node_box + 2 * nd), hi = __ldg(node_box + 2 * nd + 1);
-  const int blo[3] = {lo.x, lo.y, lo.z}, bhi[3] = {hi.x, hi.y, hi.z};
+  const uint32_t ent = (uint32_t)__ldg(face_node + 12 * prev + 6 + 2 * a + (up ? 1 : 0));
+  int blo[3], bhi[3];
+  if (ent & kFaceLeaf) {
+    const int4* w = reinterpret_cast<const int4*>(leaves + (ent & ~kFaceLeaf));
+    const int4 w1 = __ldg(w + 1), w2 = __ldg(w + 2);  // lo[3], hi[0] | hi[1], hi[2], ...
+    blo[0] = w1.x, blo[1] = w1.y, blo[2] = w1.z;
+    bhi[0] = w1.w, bhi[1] = w2.x, bhi[2] = w2.y;
+  } else {
+    const int4 lo = __ldg(node_box + 2 * ent), hi = __ldg(node_box + 2 * ent + 1);
+    blo[0] = lo.x, blo[1] = lo.y, blo[2] = lo.z;
+    bhi[0] = hi.x, bhi[1] = hi.y, bhi[2] = hi.z;
+  }
   int pid[3];
   float ts[3], es[3];
 #pragma unroll
@@ -389,11 +401,11 @@ __device__ __forceinline__ bool rope_start(const int32_t* __restrict__ face_node
     if (b != a && s_in != (fwd ? R.root_f[b] : R.root_f[3 + b])) {
       float e;
       const float t = plane_tau(rf, b, s_in, e);
-      if (!(tau0 - t > e + e0)) return false;  // N entered at or after t0 on this axis
+      if (!(tau0 - t > e + e0)) return -1;  // N entered at or after t0 on this axis
     }
     if (s_out != (fwd ? R.root_f[3 + b] : R.root_f[b])) {
       ts[b] = plane_tau(rf, b, s_out, es[b]);
-      if (b != a && !(ts[b] - tau0 > es[b] + e0)) return false;  // N left by t0
+      if (b != a && !(ts[b] - tau0 > es[b] + e0)) return -1;  // N left by t0
       pid[b] = s_out * 4 + b;
     }
   }
@@ -408,8 +420,7 @@ __device__ __forceinline__ bool rope_start(const int32_t* __restrict__ face_node
       e1 = es[b];
     }
   }
-  node = nd;
-  return true;
+  return (ent & kFaceLeaf) ? (int)(ent & ~kFaceLeaf) : -2 - (int)ent;
 }
 
 // Leaf of the segment starting at (pid0, tau0) that follows leaf `prev` (-1 on the first
@@ -417,16 +428,20 @@ __device__ __forceinline__ bool rope_start(const int32_t* __restrict__ face_node
 // by the push-down descent.  The leaf and the exact t1 are the same either way; only the
 // plane id recorded for t1 may differ, between planes whose t1 is the same FP64 value.
 __device__ __forceinline__ int next_leaf(const DNode* __restrict__ nodes,
+                                         const DLeaf* __restrict__ leaves,
                                          const int32_t* __restrict__ face_node,
                                          const int4* __restrict__ node_box, const RayArgs& R,
                                          int px, int py, const RayF& rf, uint32_t& start,
                                          int prev, int pid0, float tau0, float e0, int& pid1,
                                          float& tau1, float& e1, int lod_min = kNoLod) {
-  uint32_t nd;
-  if (prev >= 0 && !(R.lod_scale_f > 0.0f) &&
-      rope_start(face_node, node_box, R, px, py, rf, prev, pid0, tau0, e0, nd, pid1, tau1, e1))
-    return descend_from(nodes, R, px, py, rf, nd, false, start, pid0, tau0, e0, pid1, tau1, e1,
-                        lod_min);
+  if (prev >= 0 && !(R.lod_scale_f > 0.0f)) {
+    const int r = rope_start(face_node, node_box, leaves, R, px, py, rf, prev, pid0, tau0, e0,
+                             pid1, tau1, e1);
+    if (r >= 0) return r;
+    if (r <= -2)
+      return descend_from(nodes, R, px, py, rf, (uint32_t)(-2 - r), false, start, pid0, tau0, e0,
+                          pid1, tau1, e1, lod_min);
+  }
   return descend(nodes, R, px, py, rf, start, pid0, tau0, e0, pid1, tau1, e1, lod_min);
 }
 
@@ -457,18 +472,19 @@ struct BrickRef {
   int org[3];
 };
 
-__device__ __forceinline__ BrickRef load_brick(const DPatch* __restrict__ pt, int p) {
-  const DPatch q = pt[p];
+// The brick of a leaf from its record (the 3D-atlas origin, used by that storage only,
+// from the patch table).
+__device__ __forceinline__ BrickRef leaf_brick(const DPatch* __restrict__ pt, const DLeaf& lf) {
   BrickRef b;
-  b.base = q.base;
-  b.gbase = q.gbase;
-  b.sy = q.sy;
-  b.sz = q.sz;
+  b.base = lf.base;
+  b.gbase = lf.gbase;
+  b.sy = lf.sy;
+  b.sz = lf.sz;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    b.dim[a] = q.dim[a];
-    b.lo[a] = q.lo[a];
-    b.org[a] = q.org[a];
+    b.dim[a] = lf.dim[a];
+    b.lo[a] = lf.blo[a];
+    b.org[a] = pt[lf.patch].org[a];
   }
   return b;
 }
@@ -634,37 +650,34 @@ __device__ __forceinline__ int nearest_index_exact(const RayArgs& A, const DLeve
 
 // Cross-leaf gradient neighbour x_k + sign h^l e_a: descend the tree on finest-cell
 // coordinates relative to the current leaf corner; a split within the error margin sends
-// the decision to FP64.  Takes scalars only, so the caller keeps its state in registers.
+// the decision to FP64.  Takes scalars only, so the caller keeps its state in registers,
+// and the current leaf's level and corner come from the caller, so the first load of the
+// lookup is the face table.  (x0, x1, x2): the neighbour in finest cells from the leaf
+// corner (lo0, lo1, lo2); mf: its error margin in finest cells; beyond: the point lies
+// clearly beyond the face (a, sign).
 template <int ST, int INTERP>
 __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs& R, int px, int py,
-                                             int leaf_lod,
-                                             int pid0, int pid1, int n, int k, float margin,
-                                             float bn0, float bn1, float bn2, int a, float sign) {
+                                             int leaf_lod, int level, int lo0, int lo1, int lo2,
+                                             int pid0, int pid1, int n, int k, float mf,
+                                             float x0, float x1, float x2, int a, float sign,
+                                             bool beyond) {
   const int leaf = leaf_of(leaf_lod), lod_min = lod_of(leaf_lod);
-  const DLeaf cl = A.leaves[leaf];
-  const DLevel& lv = A.lv[cl.level];
-  const BrickRef cb = load_brick(A.patches, cl.patch);
-  const float scf = (float)lv.sc;
-  const float mf = margin * scf;
-  const float bn[3] = {bn0, bn1, bn2};
-  float xr[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-    xr[q] = (bn[q] - ((float)(cl.lo[q] - cb.lo[q] * lv.sc) * lv.inv_sc + 0.5f)) * scf;
+  const DLevel& lv = A.lv[level];
+  const float xr[3] = {x0, x1, x2};
+  const int clo[3] = {lo0, lo1, lo2};
   bool amb = false;
   int lid = -1;
   const bool pruning = lod_min < kNoLod;
   // the neighbour lies in the leaf or in the level cell beyond its face (a, sign): start at
   // the deepest node holding both, or the cell alone when the point is clearly beyond the
-  // face (from the root under pruning, which may stop above them)
+  // face, which the face table names directly when it is a leaf (from the root under
+  // pruning, which may stop above them)
   uint32_t i = 0;
   if (!pruning) {
-    const float xa = sel3f(a, xr[0], xr[1], xr[2]);
-    const float ext = (float)(sel3i(a, cl.hi[0], cl.hi[1], cl.hi[2]) - sel3i(a, cl.lo[0], cl.lo[1], cl.lo[2]));
-    const bool beyond = sign > 0.0f ? xa >= ext + mf : xa < -mf;
     i = (uint32_t)__ldg(A.face_node + 12 * leaf + (beyond ? 6 : 0) + 2 * a + (sign > 0.0f ? 1 : 0));
+    if (i & kFaceLeaf) lid = (int)(i & ~kFaceLeaf);
   }
-  for (int depth = 0; depth < kMaxDepth; ++depth) {
+  for (int depth = 0; lid < 0 && depth < kMaxDepth; ++depth) {
     const DNode nd = A.nodes[i];
     const uint32_t ax = nd.meta >> 30;
     const uint32_t idx = nd.meta & kIndexMask;
@@ -679,8 +692,7 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs&
         break;
       }
     }
-    const float diff = sel3f(ax, xr[0], xr[1], xr[2]) -
-                       (float)(nd.split - sel3i(ax, cl.lo[0], cl.lo[1], cl.lo[2]));
+    const float diff = sel3f(ax, xr[0], xr[1], xr[2]) - (float)(nd.split - sel3i(ax, clo[0], clo[1], clo[2]));
     if (fabsf(diff) <= mf) {
       amb = true;
       break;
@@ -706,7 +718,7 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs&
   }
   if (lid < 0) return 0.0f;
   const DLeaf lf = A.leaves[lid];
-  const BrickRef nb = (lid == leaf) ? cb : load_brick(A.patches, lf.patch);
+  const BrickRef nb = leaf_brick(A.patches, lf);
   const DLevel& lw = A.lv[lf.level];
   float bq[3];
   if (amb) {
@@ -716,7 +728,7 @@ __device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs&
   } else {
 #pragma unroll
     for (int q = 0; q < 3; ++q)
-      bq[q] = fmaf(xr[q], lw.inv_sc, (float)(cl.lo[q] - nb.lo[q] * lw.sc) * lw.inv_sc + 0.5f);
+      bq[q] = fmaf(xr[q], lw.inv_sc, (float)(clo[q] - nb.lo[q] * lw.sc) * lw.inv_sc + 0.5f);
   }
   if constexpr (INTERP == 1) {
     return trilinear<ST>(A, nb, bq[0], bq[1], bq[2]);
@@ -742,45 +754,20 @@ __device__ __noinline__ float nearest_sample_exact(const RenderArgs& A, const Ra
                                                    int pid0, int pid1, int n, int k) {
   const DLeaf cl = A.leaves[leaf];
   const DLevel& lv = A.lv[cl.level];
-  const BrickRef b = load_brick(A.patches, cl.patch);
+  const BrickRef b = leaf_brick(A.patches, cl);
   const double3 x = sample_x_exact(R, px, py, pid0, pid1, n, k);
   return cell_at<ST>(A, b, nearest_index_exact(R, lv, x.x, 0, b.lo[0]),
                      nearest_index_exact(R, lv, x.y, 1, b.lo[1]),
                      nearest_index_exact(R, lv, x.z, 2, b.lo[2]));
 }
 
-// Value of the AMR field at the gradient neighbour x_k + SG h^l e_AX (Sec. 4: shading
+// Value of the AMR field at the gradient neighbour bn = x_k + sg h^l e_ax (Sec. 4: shading
 // reads across block boundaries).  Inside the current leaf (beyond the error margin) it is
 // the current brick; otherwise the slow path locates the finest leaf holding the point.
-template <int ST, int INTERP, int AX, int SG>
-__device__ __forceinline__ float neighbour_value(const RenderArgs& A, const RayArgs& R,
-                                                 const SegState& s,
-                                                 const float* beta, int k) {
-  float bn[3] = {beta[0], beta[1], beta[2]};
-  bn[AX] += (float)SG;
-  const float m = s.margin;
-  bool inside = true;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) inside = inside && (bn[q] >= s.bl[q] + m) && (bn[q] < s.bh[q] - m);
-  if (inside) {
-    if constexpr (INTERP == 1) {
-      return trilinear<ST>(A, s.brick, bn[0], bn[1], bn[2]);
-    } else {
-      const float fx = bn[0] + 0.5f, fy = bn[1] + 0.5f, fz = bn[2] + 0.5f;
-      const float rx = fx - floorf(fx), ry = fy - floorf(fy), rz = fz - floorf(fz);
-      if (fminf(fminf(fminf(rx, 1.0f - rx), fminf(ry, 1.0f - ry)), fminf(rz, 1.0f - rz)) > m)
-        return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
-    }
-  }
-  return neighbour_slow<ST, INTERP>(A, R, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k,
-                                    s.margin, bn[0], bn[1], bn[2], AX, (float)SG);
-}
-
-// neighbour_value with the axis and sign as run-time values (bn: the neighbour position).
 template <int ST, int INTERP>
 __device__ __forceinline__ float neighbour_at(const RenderArgs& A, const RayArgs& R,
-                                              const SegState& s, const float* bn, int k, int ax,
-                                              float sg) {
+                                              const SegState& s, const DLevel& lv,
+                                              const float* bn, int k, int ax, float sg) {
   const float m = s.margin;
   bool inside = true;
 #pragma unroll
@@ -795,8 +782,19 @@ __device__ __forceinline__ float neighbour_at(const RenderArgs& A, const RayArgs
         return cell_at<ST>(A, s.brick, (int)floorf(fx), (int)floorf(fy), (int)floorf(fz));
     }
   }
-  return neighbour_slow<ST, INTERP>(A, R, s.px, s.py, s.leaf, s.pid0, s.pid1, s.n, k, s.margin,
-                                    bn[0], bn[1], bn[2], ax, sg);
+  // finest cells from the leaf corner; beyond the face against the (possibly widened) leaf
+  // bound, which only ever errs towards the deeper start node
+  const float scf = (float)lv.sc;
+  float x[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    x[q] = (bn[q] - ((float)(s.leaf_lo[q] - s.brick.lo[q] * lv.sc) * lv.inv_sc + 0.5f)) * scf;
+  const float ba = sel3f(ax, bn[0], bn[1], bn[2]);
+  const bool beyond = sg > 0.0f ? ba >= sel3f(ax, s.bh[0], s.bh[1], s.bh[2]) + m
+                                : ba < sel3f(ax, s.bl[0], s.bl[1], s.bl[2]) - m;
+  return neighbour_slow<ST, INTERP>(A, R, s.px, s.py, s.leaf, s.level, s.leaf_lo[0],
+                                    s.leaf_lo[1], s.leaf_lo[2], s.pid0, s.pid1, s.n, k,
+                                    m * scf, x[0], x[1], x[2], ax, sg, beyond);
 }
 
 // Value at the sample itself (the segment's own leaf and level, Sec. 3.3).
@@ -955,7 +953,7 @@ __device__ __forceinline__ void gradient(const RenderArgs& A, const RayArgs& R, 
     bn[0] += ax == 0 ? sg : 0.0f;
     bn[1] += ax == 1 ? sg : 0.0f;
     bn[2] += ax == 2 ? sg : 0.0f;
-    const float v = neighbour_at<ST, INTERP>(A, R, s, bn, k, ax, sg);
+    const float v = neighbour_at<ST, INTERP>(A, R, s, lv, bn, k, ax, sg);
     d[0] += ax == 0 ? sg * v : 0.0f;
     d[1] += ax == 1 ? sg * v : 0.0f;
     d[2] += ax == 2 ? sg * v : 0.0f;
@@ -982,7 +980,7 @@ __device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& r
                                               int px, int py, SegSetup& g,
                                               int lod_min = kNoLod) {
   SegState& s = g.s;
-  s.brick = load_brick(A.patches, lf.patch);
+  s.brick = leaf_brick(A.patches, lf);
   s.level = lf.level;
   s.leaf = pack_leaf(lid, lod_min);
   s.pid0 = pid0;
@@ -1065,7 +1063,7 @@ __device__ __noinline__ float shadow_transmittance(const RenderArgs& A, const Ra
       leaf = locate_cell(A.nodes, R, kNoLod, f[0], f[1], f[2]);
       if (leaf < 0) return T;
       lf = A.leaves[leaf];
-      b = load_brick(A.patches, lf.patch);
+      b = leaf_brick(A.patches, lf);
       inv_sc = A.lv[lf.level].inv_sc;
     }
     const float v = trilinear<ST>(A, b, fmaf(P[0], inv_sc, 0.5f - (float)b.lo[0]),
@@ -1226,7 +1224,7 @@ __device__ __forceinline__ float4 march_ray(const RenderArgs& A, const RayArgs& 
       int pid1 = kPidOut;
       float tau1 = rf.tau_out, e1 = exit_bound(rf);
       const int lmin = lod_min_level(R, A.lv, rf, i, j, pid0, tau0, e0);
-      const int lid = next_leaf(A.nodes, A.face_node, A.node_box, R, i, j, rf, start, prev, pid0,
+      const int lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, R, i, j, rf, start, prev, pid0,
                                 tau0, e0, pid1, tau1, e1, lmin);
       if (lid < 0) {
         status |= kStatusDevice;

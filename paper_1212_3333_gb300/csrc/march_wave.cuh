@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
         ++nseg;
         int pid1 = kPidOut;
         float tau1 = rf.tau_out, e1 = exit_bound(rf);
-        const int lid = next_leaf(A.nodes, A.face_node, A.node_box, A.ray, i, j, rf, start, prev,
+        const int lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, A.ray, i, j, rf, start, prev,
                                   pid0, tau0, e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
           if (n > 0) {
             WaveSeg& ws = W->seg[lane];
             SegState& s = ws.s;
-            s.brick = load_brick(A.patches, lf.patch);
+            s.brick = leaf_brick(A.patches, lf);
             s.level = lf.level;
             s.leaf = pack_leaf(lid, kNoLod);
             s.pid0 = pid0;
