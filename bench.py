@@ -358,11 +358,12 @@ def shadow_eval(amr, ctx, vmin, vmax, args, size=512):
 
 
 def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5, lo=256, hi=2048,
-               tune_views=16):
+               tune_views=16, schedule=0):
     """Batched multi-view rendering: 64 seeded views with square sides uniform in
     256..2048 and four 256-entry transfer functions, rendered (a) as 64 separate
     amr_render launches, (b) as one persistent amr_render_batch launch with the autotuned
-    tile configuration, (c) as that launch replayed from a CUDA graph."""
+    tile configuration, (c) as that launch replayed from a CUDA graph.  schedule 3: the
+    batched launch marches with deferred shading (the separate renders stay per-ray)."""
     import torch
     import synth
 
@@ -371,7 +372,9 @@ def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5, lo=256, hi=
     cams = [synth.orbit_camera(5000 + v, int(sd), int(sd)) for v, sd in enumerate(sides)]
     tfi = [v % 4 for v in range(n_views)]
     tfs = torch.as_tensor(np.stack(synth.tf_variants()), device="cuda")
-    p = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
+    p0 = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
+    p = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
+                               schedule=schedule, samples_per_iter=16)
     views, offsets, total = amr.make_views(cams, tfi)
     out = torch.zeros((total,), dtype=torch.float32, device="cuda")
     ref = torch.zeros_like(out)
@@ -379,7 +382,7 @@ def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5, lo=256, hi=
 
     def separate(dst):
         for cam, t, off in zip(cams, tfi, offsets):
-            ctx.amr_render(cam, tfs[t], p, dst[off:off + 4 * cam.width * cam.height])
+            ctx.amr_render(cam, tfs[t], p0, dst[off:off + 4 * cam.width * cam.height])
 
     def timed(fn, reps=3):
         fn()
@@ -410,7 +413,8 @@ def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5, lo=256, hi=
     same = same and bool(torch.equal(out, ref))
     names = [f"{tw}x{th}/r{r}" for tw, th in ((8, 8), (16, 8), (16, 16)) for r in (1, 2, 4)]
     bps = BYTES_PER_SAMPLE[args.shade]
-    return {"views": n_views, "sides": [lo, hi], "pixels": int(sum(int(sd) ** 2 for sd in sides)),
+    return {"views": n_views, "sides": [lo, hi], "schedule": schedule,
+            "pixels": int(sum(int(sd) ** 2 for sd in sides)),
             "samples": samples, "identical_to_separate": same,
             "separate": {"ms": ms_sep, "gsamples_s": samples / ms_sep / 1e6},
             "batched": {"ms": ms_batch, "gsamples_s": samples / ms_batch / 1e6},
@@ -420,6 +424,41 @@ def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5, lo=256, hi=
             "autotune": {"best": f"{best.tile_w}x{best.tile_h}/r{best.rays_per_thread}",
                          "tuned_on_views": tune_views, "ms": dict(zip(names, table)),
                          "seconds": tune_s}}
+
+
+def schedules_eval(amr, ctx, vmin, vmax, tf, args, sizes=(2048, 1024, 512), spi=16):
+    """The frame march under the per-ray loop (schedule 0), persistent refill (2) and
+    deferred shading (3) at several image sizes (the C2 orbit view): Gsamples/s and
+    whether each image equals the per-ray one bit for bit."""
+    import torch
+    import synth
+
+    stream = torch.cuda.current_stream()
+    res = {}
+    for size in sizes:
+        cam = synth.orbit_camera(2, size, size)
+        ref = torch.empty((size, size, 4), dtype=torch.float32, device="cuda")
+        out = torch.empty_like(ref)
+        row = {}
+        for sched in (0, 2, 3):
+            p = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
+                                       schedule=sched, samples_per_iter=spi)
+            if sched == 3 and args.shade != 1:
+                continue
+            dst = ref if sched == 0 else out
+            n = ctx.amr_render(cam, tf, p, dst, count_samples=True)
+            ctx.amr_render(cam, tf, p, dst)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                ctx.amr_render(cam, tf, p, dst)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 3
+            row[str(sched)] = {"ms": ms, "gsamples_s": n / ms / 1e6,
+                               "identical_to_per_ray": bool(torch.equal(dst, ref))}
+        res[str(size)] = row
+    return {"samples_per_iter": spi, "by_size": res}
 
 
 def c3_eval(amr, args, peak):
@@ -486,6 +525,7 @@ def _config(hier, args, storage, size=SIZE):
                                   storage != "oracle" else ""),
             "cells": getattr(args, "dtype", "f32"),
             "image": [size, size], "shade": args.shade,
+            "schedule": getattr(args, "schedule", 0),
             "l2": "inputs larger than L2: 602 MB of bricks vs 129 MB L2, no flush"}
 
 
@@ -503,7 +543,11 @@ def main():
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e", type=int, default=1, help="also time the host-buffer entry point")
     ap.add_argument("--size", type=int, default=SIZE, help="image side (the metric is at 2048)")
-    ap.add_argument("--schedule", type=int, default=0, help="0 per-ray loop, 1 warp wavefront")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="0 per-ray loop, 1 warp wavefront, 2 refill, 3 deferred shading")
+    ap.add_argument("--spi", type=int, default=16, help="samples per step, schedules 2 and 3")
+    ap.add_argument("--schedules", type=int, default=1,
+                    help="time schedules 0 / 2 / 3 at 2048, 1024 and 512 pixels")
     ap.add_argument("--gradient", type=int, default=1, help="build gradient bricks")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"],
                     help="brick cell storage type (interpolation and compositing stay FP32)")
@@ -548,7 +592,7 @@ def main():
     build_s = time.perf_counter() - t0
     st = ctx.amr_get_stats()
     params = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
-                                    schedule=args.schedule)
+                                    schedule=args.schedule, samples_per_iter=args.spi)
     out = torch.empty((size, size, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -610,7 +654,8 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": _profiled_traffic(args.shade, variant, size),
             "peak_kind": peak_kind, "bytes_per_sample": bps,
-            "kernel": ("march_kernel" if args.schedule == 0 else "wave_kernel") +
+            "kernel": {0: "march_kernel", 1: "wave_kernel", 2: "persist_kernel",
+                       3: "deferred_kernel"}[args.schedule] +
                       f"<{variant}, trilinear, {'phong' if args.shade else 'plain'}>",
             "kernel_ms": kern_ms}
     extra = {"frames_per_s": fps, "samples_per_frame": samples, "build_s": build_s,
@@ -660,6 +705,11 @@ def main():
         extra["batch"] = batch_eval(amr, ctx, vmin, vmax, args, peak)
         extra["batch_small_views"] = batch_eval(amr, ctx, vmin, vmax, args, peak, lo=64, hi=256,
                                                 tune_views=64)
+        if args.shade == 1:
+            extra["batch_small_views_deferred"] = batch_eval(
+                amr, ctx, vmin, vmax, args, peak, lo=64, hi=256, tune_views=64, schedule=3)
+    if args.schedules and world == 1:
+        extra["schedules"] = schedules_eval(amr, ctx, vmin, vmax, tf, args)
     if args.c3 and world == 1:
         extra["c3"] = c3_eval(amr, args, peak)
     if args.learned and world == 1:

@@ -96,15 +96,17 @@ typedef struct {
   int32_t schedule;   /* 0: one loop per ray; 1: warp wavefront (the samples of a warp's
                          current segments spread over its lanes, shading on the compacted
                          opaque samples); 2: persistent warps that refill finished lanes
-                         with new rays and fetch segments in batches (trilinear only).
-                         All three give the same image. */
+                         with new rays and fetch segments in batches (trilinear only);
+                         3: warps march their rays in step and shade the opaque samples
+                         32 at a time (trilinear, shade = 1 only).  All give the same
+                         image. */
   int32_t learned;    /* learned segment proposal (needs amr_set_proposal; trilinear; ptr or
                          atlas_linear storage, FP32 cells): 0 off; 1 skip segments whose predicted
                          contribution is below tau; 2 sample them with a coarse_factor times
                          coarser step */
   double tau;         /* proposal threshold (default 1e-3) */
-  int32_t samples_per_iter; /* schedule 2: samples a lane takes between warp steps, 1..64
-                               (default 4) */
+  int32_t samples_per_iter; /* schedules 2 and 3: samples a lane takes between warp steps,
+                               1..64 (default 4) */
   int32_t coarse_factor;    /* learned mode 2: a segment predicted below tau takes
                                ceil(n / coarse_factor) samples, 2..64 (default 4) */
   double lod_pixels;        /* level-of-detail pruning (Sec. 3.1 type-(a) nodes, Sec. 3.3):
@@ -228,8 +230,9 @@ typedef struct {
  *   out_rgba_dev   device float32 [out_floats]; view v writes [H][W][4] at out_offset;
  *                  images must not overlap; buffers 16-byte aligned
  *   config         NULL: the context's last autotuned configuration (initially 16x8, 1)
- * Needs the ptr storage with FP32 cells, trilinear sampling, the per-ray schedule and no
- * learned proposal (else AMR_ERR_ARG).  Issues one cudaMemsetAsync and one kernel launch
+ * Needs the ptr storage with FP32 cells, trilinear sampling, schedule 0 (per-ray loop) or
+ * 3 (deferred shading, shade = 1), no learned proposal and no secondary rays (else
+ * AMR_ERR_ARG).  Issues one cudaMemsetAsync and one kernel launch
  * on cuda_stream and allocates nothing, so with samples_out NULL the call can be captured
  * in a CUDA graph; samples_out (nullable, host) synchronises and returns the total sample
  * count of all views (plus the device status check, as amr_render). */

@@ -4,7 +4,8 @@
 // a view).  Every block pops a tile with one atomic, builds that view's ray arguments in
 // shared memory and marches the tile's pixels with the same per-pixel code as the
 // single-view kernel, so each view's image is bit-identical to its own amr_render.  Up to
-// eight transfer functions are staged in shared memory once per block.  The view table
+// eight transfer functions are staged in shared memory once per block.  With schedule 3
+// each warp marches its rays with the deferred-shading loop instead of the per-ray loop.  The view table
 // travels in the kernel's parameter block, so a call is one memset and one launch and can
 // be captured in a CUDA graph.  The paper renders one view per pass; batching is an
 // addition for throughput over many small and large views.
@@ -12,12 +13,15 @@
 
 #include "ctx.h"
 #include "march.cuh"
+#include "march_deferred.cuh"
 
 namespace amr {
 
 namespace {
 
-template <int ST, int SHADE, int TW, int TH>
+// DEFER: the warp-synchronous march with deferred shading (schedule 3) instead of the
+// per-ray loop; each warp's queue area follows the transfer functions in shared memory.
+template <int ST, int SHADE, int TW, int TH, bool DEFER>
 __global__ void __launch_bounds__(TW * TH, (128 * kMinBlocks<SHADE>) / (TW * TH))
     batch_kernel(const __grid_constant__ BatchArgs B) {
   constexpr int NT = TW * TH;
@@ -96,8 +100,15 @@ __global__ void __launch_bounds__(TW * TH, (128 * kMinBlocks<SHADE>) / (TW * TH)
     float4* out = A.out + s_out;
     for (int r = 0; r < rpt; ++r) {
       const int j = (ty * rpt + r) * TH + (int)threadIdx.y;
-      if (i < W && j < H)
-      {
+      if constexpr (DEFER) {
+        // every lane of the warp takes part, with or without a pixel
+        const size_t nz_bytes = (size_t)B.n_tf * (tf_n + 1) * sizeof(int);
+        const size_t area = ((size_t)B.n_tf * tf_n * sizeof(float4) + nz_bytes + 15) & ~(size_t)15;
+        DeferArea& Q = reinterpret_cast<DeferArea*>(reinterpret_cast<char*>(smem) + area)[tid >> 5];
+        const bool act = i < W && j < H;
+        const float4 c = march_deferred<ST, SHADE>(A, s_ray, i, j, act, tf, nz, Q, nsamp, status);
+        if (act) out[(size_t)j * W + i] = c;
+      } else if (i < W && j < H) {
         RayF rf;
         out[(size_t)j * W + i] = march_ray<ST, 1, SHADE>(A, s_ray, i, j, tf, nz, rf, nsamp, status);
       }
@@ -109,11 +120,12 @@ __global__ void __launch_bounds__(TW * TH, (128 * kMinBlocks<SHADE>) / (TW * TH)
   if (status) atomicOr(A.counters + 1, status);
 }
 
-template <int ST, int SHADE, int TW, int TH>
+template <int ST, int SHADE, int TW, int TH, bool DEFER>
 amr_status launch_shape(amr_ctx* c, const BatchArgs& b, int blocks_per_sm, cudaStream_t s) {
-  auto k = batch_kernel<ST, SHADE, TW, TH>;
-  const size_t smem = (size_t)b.n_tf * b.A.tf_n * (sizeof(float4) + sizeof(int)) +
-                      (size_t)b.n_tf * sizeof(int);
+  auto k = batch_kernel<ST, SHADE, TW, TH, DEFER>;
+  size_t smem = (size_t)b.n_tf * b.A.tf_n * (sizeof(float4) + sizeof(int)) +
+                (size_t)b.n_tf * sizeof(int);
+  if (DEFER) smem = ((smem + 15) & ~(size_t)15) + (TW * TH / 32) * sizeof(DeferArea);
   cudaError_t e = cudaSuccess;
   if (smem > 48 * 1024)
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -130,24 +142,31 @@ amr_status launch_shape(amr_ctx* c, const BatchArgs& b, int blocks_per_sm, cudaS
   return AMR_OK;
 }
 
-template <int ST, int SHADE>
+template <int ST, int SHADE, bool DEFER>
 amr_status launch_st(amr_ctx* c, const BatchArgs& b, const amr_batch_config& cfg, cudaStream_t s) {
-  if (cfg.tile_w == 8 && cfg.tile_h == 8) return launch_shape<ST, SHADE, 8, 8>(c, b, cfg.blocks_per_sm, s);
-  if (cfg.tile_w == 16 && cfg.tile_h == 8) return launch_shape<ST, SHADE, 16, 8>(c, b, cfg.blocks_per_sm, s);
+  if (cfg.tile_w == 8 && cfg.tile_h == 8)
+    return launch_shape<ST, SHADE, 8, 8, DEFER>(c, b, cfg.blocks_per_sm, s);
+  if (cfg.tile_w == 16 && cfg.tile_h == 8)
+    return launch_shape<ST, SHADE, 16, 8, DEFER>(c, b, cfg.blocks_per_sm, s);
   if (cfg.tile_w == 16 && cfg.tile_h == 16)
-    return launch_shape<ST, SHADE, 16, 16>(c, b, cfg.blocks_per_sm, s);
+    return launch_shape<ST, SHADE, 16, 16, DEFER>(c, b, cfg.blocks_per_sm, s);
   return fail(c, AMR_ERR_ARG, "batch tile must be 8x8, 16x8 or 16x16");
 }
 
 }  // namespace
 
-amr_status launch_batch(amr_ctx* c, const BatchArgs& b, int storage, int shade,
+amr_status launch_batch(amr_ctx* c, const BatchArgs& b, int storage, int shade, int schedule,
                         const amr_batch_config& cfg, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (storage != ST_PTR) return fail(c, AMR_ERR_ARG, "batched rendering needs the ptr storage (FP32)");
-  if (shade == 0) return launch_st<ST_PTR, 0>(c, b, cfg, s);
-  if (shade == 1) return launch_st<ST_PTR, 1>(c, b, cfg, s);
-  return launch_st<ST_PTR, 2>(c, b, cfg, s);
+  if (schedule == 3) {
+    if (shade == 1) return launch_st<ST_PTR, 1, true>(c, b, cfg, s);
+    if (shade == 2) return launch_st<ST_PTR, 2, true>(c, b, cfg, s);
+    return fail(c, AMR_ERR_ARG, "deferred shading renders with shade = 1");
+  }
+  if (shade == 0) return launch_st<ST_PTR, 0, false>(c, b, cfg, s);
+  if (shade == 1) return launch_st<ST_PTR, 1, false>(c, b, cfg, s);
+  return launch_st<ST_PTR, 2, false>(c, b, cfg, s);
 }
 
 }  // namespace amr

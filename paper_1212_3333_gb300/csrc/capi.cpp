@@ -291,15 +291,17 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   if (!(p->kappa >= 0.0)) return fail(c, AMR_ERR_ARG, "kappa must be non-negative");
   if (p->interp != 0 && p->interp != 1) return fail(c, AMR_ERR_ARG, "unknown interp");
   if (p->shade != 0 && p->shade != 1) return fail(c, AMR_ERR_ARG, "unknown shade");
-  if (p->schedule < 0 || p->schedule > 2) return fail(c, AMR_ERR_ARG, "unknown schedule");
-  if (p->schedule == 2 && (p->samples_per_iter < 1 || p->samples_per_iter > 64))
+  if (p->schedule < 0 || p->schedule > 3) return fail(c, AMR_ERR_ARG, "unknown schedule");
+  if (p->schedule == 3 && (p->interp != AMR_INTERP_TRILINEAR || p->shade != 1 || p->learned != 0))
+    return fail(c, AMR_ERR_ARG, "deferred shading renders trilinear with shade = 1, no proposal");
+  if (p->schedule >= 2 && (p->samples_per_iter < 1 || p->samples_per_iter > 64))
     return fail(c, AMR_ERR_ARG, "samples_per_iter must be in [1, 64]");
   if (p->schedule == 2 && p->interp != AMR_INTERP_TRILINEAR)
     return fail(c, AMR_ERR_ARG, "the refill schedule renders trilinear");
   if (!(p->lod_pixels >= 0.0) || !std::isfinite(p->lod_pixels))
     return fail(c, AMR_ERR_ARG, "lod_pixels must be finite and non-negative");
   if (p->lod_pixels > 0.0 && (p->schedule == 1 || p->learned != 0))
-    return fail(c, AMR_ERR_ARG, "level-of-detail pruning needs schedule 0 or 2 without the proposal");
+    return fail(c, AMR_ERR_ARG, "level-of-detail pruning needs schedule 0, 2 or 3 without the proposal");
   if (p->shadow != 0 && p->shadow != 1) return fail(c, AMR_ERR_ARG, "shadow must be 0 or 1");
   if (p->shadow) {
     for (int a = 0; a < 3; ++a)
@@ -354,7 +356,7 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->light_ambient = (float)p->light_ambient;
   a->coarse_factor = p->coarse_factor;
   if (c->dtype != AMR_F32 && (p->interp != AMR_INTERP_TRILINEAR || p->schedule == 1))
-    return fail(c, AMR_ERR_ARG, "16-bit cells render trilinear with schedule 0 or 2");
+    return fail(c, AMR_ERR_ARG, "16-bit cells render trilinear with schedule 0, 2 or 3");
   if (p->learned != 0) {
     if (p->learned != 1 && p->learned != 2) return fail(c, AMR_ERR_ARG, "unknown learned mode");
     if (p->learned == 2 && (p->coarse_factor < 2 || p->coarse_factor > 64))
@@ -482,9 +484,11 @@ amr_status prepare_batch(amr_ctx* c, const amr_view* views, int32_t n_views, con
     return fail(c, AMR_ERR_ARG, "need 1 <= n_tf <= 8 and n_tf * tf_n <= 2048");
   if (p->row0 != 0 || p->rows > 0)
     return fail(c, AMR_ERR_ARG, "batched views render whole images (row0 = 0, rows <= 0)");
-  if (p->interp != AMR_INTERP_TRILINEAR || p->schedule != 0 || p->learned != 0 || p->shadow)
+  if (p->interp != AMR_INTERP_TRILINEAR || (p->schedule != 0 && p->schedule != 3) ||
+      p->learned != 0 || p->shadow)
     return fail(c, AMR_ERR_ARG,
-                "batched rendering is trilinear, per-ray, without the proposal or secondary rays");
+                "batched rendering is trilinear, schedule 0 or 3, without the proposal or "
+                "secondary rays");
   if (cfg.rays_per_thread < 1 || cfg.rays_per_thread > 8 || cfg.blocks_per_sm < 0)
     return fail(c, AMR_ERR_ARG, "batch config: rays_per_thread in [1, 8], blocks_per_sm >= 0");
   if (!((cfg.tile_w == 8 && cfg.tile_h == 8) || (cfg.tile_w == 16 && cfg.tile_h == 8) ||
@@ -560,7 +564,8 @@ amr_status amr_render_batch(amr_ctx* c, const amr_view* views, int32_t n_views,
   if (s != AMR_OK) return s;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   CK(cudaMemsetAsync(c->dev.counters, 0, kNumCounters * sizeof(unsigned long long), st));
-  s = launch_batch(c, *b, kernel_storage(c), kernel_shade(c, params), cfg, cuda_stream);
+  s = launch_batch(c, *b, kernel_storage(c), kernel_shade(c, params), params->schedule, cfg,
+                   cuda_stream);
   if (s != AMR_OK) return s;
   return finish_render(c, st, samples_out);
 }
@@ -599,7 +604,7 @@ amr_status amr_batch_autotune(amr_ctx* c, const amr_view* views, int32_t n_views
       if (cudaMemsetAsync(c->dev.counters, 0, kNumCounters * sizeof(unsigned long long), st) !=
           cudaSuccess)
         return done(fail(c, AMR_ERR_CUDA, "cudaMemsetAsync"));
-      s = launch_batch(c, *b, kernel_storage(c), shade, cfg, cuda_stream);
+      s = launch_batch(c, *b, kernel_storage(c), shade, params->schedule, cfg, cuda_stream);
       if (s != AMR_OK) return done(s);
     }
     if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

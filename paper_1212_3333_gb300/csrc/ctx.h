@@ -112,7 +112,7 @@ amr_status launch_render(amr_ctx* c, const RenderArgs& a, int storage, int inter
                          int schedule, void* stream);
 amr_status launch_trace(amr_ctx* c, const TraceArgs& a, void* stream);
 amr_status launch_learned(amr_ctx* c, const RenderArgs& a, int storage, int shade, void* stream);
-amr_status launch_batch(amr_ctx* c, const BatchArgs& b, int storage, int shade,
+amr_status launch_batch(amr_ctx* c, const BatchArgs& b, int storage, int shade, int schedule,
                         const amr_batch_config& cfg, void* stream);
 amr_status launch_log(amr_ctx* c, const RenderArgs& a, int storage, float* features,
                       float* targets, long long cap, unsigned long long* count, float keep_prob,

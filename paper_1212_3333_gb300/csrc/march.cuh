@@ -971,6 +971,25 @@ struct SegSetup {
   float delta;
 };
 
+// The leaf's corner and its box in brick coordinates, the region whose gradient neighbours
+// read the leaf's own brick.
+__device__ __forceinline__ void leaf_bounds(const DLeaf& lf, const DLevel& lv, const BrickRef& b,
+                                            int lod_min, int* leaf_lo, float* bl, float* bh) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    leaf_lo[a] = lf.lo[a];
+    bl[a] = (float)(lf.lo[a] - b.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
+    bh[a] = (float)(lf.hi[a] - b.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
+    // a same-patch face widens the region whose neighbours read this brick by one cell.
+    // Under pruning only when the bound is finer than this leaf's level: then no node the
+    // pruned descent could stop at overlaps the (level-l) cells beyond the face
+    if (lod_min > lf.level) {
+      if ((lf.faces >> (2 * a)) & 1) bl[a] -= 1.0f;
+      if ((lf.faces >> (2 * a + 1)) & 1) bh[a] += 1.0f;
+    }
+  }
+}
+
 // Sample parameters of segment (pid0, pid1) of leaf `lid` with n midpoint samples, and the
 // bound on their FP32 error: the tau ends within max(e0, e1), a few roundings of the tau
 // arithmetic, then the position and brick-space roundings.
@@ -994,22 +1013,13 @@ __device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& r
   const float taum = fmaf(0.5f, dtau, tau0);
   const float etau = fmaxf(e0, e1) + ldexpf(tau1 + 1.0f, -21);
   float ex = 0.0f, bmax = 0.0f;
+  leaf_bounds(lf, lv, s.brick, lod_min, s.leaf_lo, s.bl, s.bh);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float xm = fmaf(taum, rf.Dd[a], rf.Xe[a]);  // finest units
     const float lo05 = 0.5f - (float)s.brick.lo[a];
     g.b0[a] = fmaf(xm, lv.inv_sc, lo05);
     g.db[a] = dtau * rf.Dd[a] * lv.inv_sc;
-    s.leaf_lo[a] = lf.lo[a];
-    s.bl[a] = (float)(lf.lo[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
-    s.bh[a] = (float)(lf.hi[a] - s.brick.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
-    // a same-patch face widens the region whose neighbours read this brick by one cell.
-    // Under pruning only when the bound is finer than this leaf's level: then no node the
-    // pruned descent could stop at overlaps the (level-l) cells beyond the face
-    if (lod_min > lf.level) {
-      if ((lf.faces >> (2 * a)) & 1) s.bl[a] -= 1.0f;
-      if ((lf.faces >> (2 * a + 1)) & 1) s.bh[a] += 1.0f;
-    }
     const float ea = fabsf(rf.Dd[a]) * etau +
                      ldexpf(fabsf(rf.Xe[a]) + fabsf(xm) + nfl * fabsf(dtau * rf.Dd[a]) + 1.0f, -21);
     ex = fmaxf(ex, ea);
@@ -1076,6 +1086,23 @@ __device__ __noinline__ float shadow_transmittance(const RenderArgs& A, const Ra
   return T;
 }
 
+// Headlight Phong factor of gradient gr (normal g / max(|g|, gamma (vmax - vmin) / h^l))
+// applied to the transfer-function colour (cr, cg, cb), clamped to [0, 1].
+__device__ __forceinline__ void phong(const RenderArgs& A, const DLevel& lv, const float* gr,
+                                      float Lx, float Ly, float Lz, float& cr, float& cg,
+                                      float& cb) {
+  const float gn = sqrtf(fmaf(gr[0], gr[0], fmaf(gr[1], gr[1], gr[2] * gr[2])));
+  const float gf = A.gfloor_num / lv.hmin;
+  const float den = fmaxf(gn, gf);
+  const float inv = den > 0.0f ? 1.0f / den : 0.0f;
+  const float ndl = fabsf((gr[0] * Lx + gr[1] * Ly + gr[2] * Lz) * inv);
+  const float spec = A.ks * __powf(ndl, A.shininess);
+  const float diff = fmaf(A.kd, ndl, A.ka);
+  cr = fminf(fmaxf(fmaf(cr, diff, spec), 0.0f), 1.0f);
+  cg = fminf(fmaxf(fmaf(cg, diff, spec), 0.0f), 1.0f);
+  cb = fminf(fmaxf(fmaf(cb, diff, spec), 0.0f), 1.0f);
+}
+
 // Sample k of a segment (Sec. 3: emission-absorption compositing; Sec. 4: gradient
 // shading), composited front to back into (C, Acc).  Returns true when early ray
 // termination stops the ray at this sample.
@@ -1094,16 +1121,7 @@ __device__ __forceinline__ bool composite_sample(const RenderArgs& A, const RayA
   if constexpr ((SHADE & 3) >= 1) {
     float gr[3];
     gradient<ST, INTERP, ((SHADE & 3) == 2)>(A, R, s, beta, k, lv, gr);
-    const float gn = sqrtf(fmaf(gr[0], gr[0], fmaf(gr[1], gr[1], gr[2] * gr[2])));
-    const float gf = A.gfloor_num / lv.hmin;
-    const float den = fmaxf(gn, gf);
-    const float inv = den > 0.0f ? 1.0f / den : 0.0f;
-    const float ndl = fabsf((gr[0] * Lx + gr[1] * Ly + gr[2] * Lz) * inv);
-    const float spec = A.ks * __powf(ndl, A.shininess);
-    const float diff = fmaf(A.kd, ndl, A.ka);
-    cr = fminf(fmaxf(fmaf(cr, diff, spec), 0.0f), 1.0f);
-    cg = fminf(fmaxf(fmaf(cg, diff, spec), 0.0f), 1.0f);
-    cb = fminf(fmaxf(fmaf(cb, diff, spec), 0.0f), 1.0f);
+    phong(A, lv, gr, Lx, Ly, Lz, cr, cg, cb);
   }
   if constexpr ((SHADE & kShadeShadow) != 0) {
     // the sample in finest-cell units: beta = X / sc - lo + 0.5

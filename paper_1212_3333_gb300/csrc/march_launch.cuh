@@ -4,6 +4,7 @@
 
 #include "ctx.h"
 #include "march.cuh"
+#include "march_deferred.cuh"
 #include "march_persist.cuh"
 #include "march_wave.cuh"
 
@@ -60,6 +61,13 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
     } else {
       return fail(c, AMR_ERR_ARG, "secondary rays need the ptr or atlas_linear storage, FP32 cells");
     }
+  } else if (schedule == 3) {
+    // warp-synchronous march with deferred shading (trilinear, Phong)
+    if (interp != 1 || (shade != 1 && shade != 2))
+      return fail(c, AMR_ERR_ARG, "deferred shading renders trilinear with shade = 1");
+    const size_t smem = ((tf_bytes + 15) & ~(size_t)15) + 4 * sizeof(DeferArea);
+    if (shade == 1) e = launch_one(deferred_kernel<ST, 1>, grid, block, smem, s, a);
+    else e = launch_one(deferred_kernel<ST, 2>, grid, block, smem, s, a);
   } else if (schedule == 2) {
     // persistent warps with ray refill (trilinear)
     if (interp != 1) return fail(c, AMR_ERR_ARG, "the refill schedule renders trilinear");
@@ -70,7 +78,7 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
   } else if constexpr (ST >= ST_PTR_F16) {
     // 16-bit cells: trilinear, per-ray schedule
     if (interp != 1 || schedule != 0)
-      return fail(c, AMR_ERR_ARG, "16-bit storage renders trilinear with schedule 0 or 2");
+      return fail(c, AMR_ERR_ARG, "16-bit storage renders trilinear with schedule 0, 2 or 3");
     const size_t smem = tf_bytes;
     if (shade == 0) e = launch_one(march_kernel<ST, 1, 0>, grid, block, smem, s, a);
     else if (shade == 1) e = launch_one(march_kernel<ST, 1, 1>, grid, block, smem, s, a);

@@ -1,7 +1,8 @@
 """GPU checks of batched multi-view rendering: every view of a persistent batched launch
 equals its own single-view render bit for bit (same per-pixel arithmetic), for every tile
-shape and rays-per-thread setting; a CUDA-graph replay of the call gives the same images;
-the autotuner's choice is kept; malformed batches are rejected before any launch."""
+shape and rays-per-thread setting, with the per-ray loop or deferred shading; a CUDA-graph
+replay of the call gives the same images; the autotuner's choice is kept; malformed
+batches are rejected before any launch."""
 import numpy as np
 import pytest
 
@@ -52,8 +53,8 @@ def _split(out, cams, offsets):
 
 
 @pytest.mark.parametrize("gradient", [False, True])
-@pytest.mark.parametrize("shade", [0, 1])
-def test_batch_equals_single_view_renders(amr, c1, gradient, shade):
+@pytest.mark.parametrize("shade,schedule", [(0, 0), (1, 0), (1, 3)])
+def test_batch_equals_single_view_renders(amr, c1, gradient, shade, schedule):
     import torch
 
     w = c1
@@ -63,12 +64,14 @@ def test_batch_equals_single_view_renders(amr, c1, gradient, shade):
     tfs = torch.as_tensor(np.stack(tfs_h), device="cuda")
     cams, tfi = _views(11, 5 + shade)
     p, _ = params_pair(amr, w["vmin"], w["vmax"], shade=shade)
+    # schedule 3 (deferred shading) gives the per-ray loop's images bit for bit
+    pb, _ = params_pair(amr, w["vmin"], w["vmax"], shade=shade, schedule=schedule)
     want, n_want = _singles(amr, ctx, cams, tfi, tfs_h, p)
     views, offsets, total = amr.make_views(cams, tfi)
     for tw, th in SHAPES:
         for rpt in (1, 2, 4):
             out = torch.full((total + 8,), float("nan"), device="cuda")
-            n = ctx.amr_render_batch(views, tfs, p, out, config=amr.batch_config(tw, th, rpt),
+            n = ctx.amr_render_batch(views, tfs, pb, out, config=amr.batch_config(tw, th, rpt),
                                      count_samples=True)
             assert n == n_want, (tw, th, rpt)
             for v, img in enumerate(_split(out, cams, offsets)):
