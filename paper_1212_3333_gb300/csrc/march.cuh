@@ -1291,38 +1291,56 @@ __device__ __forceinline__ void stage_tf(const float4* __restrict__ tf, int n, f
   __syncthreads();
 }
 
+// The frame march (schedule 0): one thread per pixel, persistent warps.  Each warp takes
+// 8x4-pixel tiles from a global queue (counters[kQueueCounter], zeroed before the launch)
+// until none is left, so a warp that finishes its rays starts on new ones at once instead
+// of idling until the slowest warp of its block is done (measured on C2 at 2048^2: Phong
+// 50.0 -> 52.9 Gsamples/s against one block per 8x16 tile); the grid holds only as many
+// blocks as are resident at once.
 template <int ST, int INTERP, int SHADE>
-__global__ void __launch_bounds__(128, kMinBlocks<SHADE>) march_kernel(const __grid_constant__ RenderArgs A) {
+__global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
+    march_kernel(const __grid_constant__ RenderArgs A) {
   extern __shared__ float4 smem[];
   float4* s_tf = smem;
   int* s_nz = reinterpret_cast<int*>(smem + A.tf_n);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   stage_tf(A.tf, A.tf_n, s_tf, s_nz, tid, blockDim.x * blockDim.y);
-
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int jr = blockIdx.y * blockDim.y + threadIdx.y;
-  const int j = A.ray.row0 + jr;
-  const bool active = i < A.ray.width && jr < A.ray.rows && j < A.ray.height;
+  const int lane = tid & 31;
+  const RayArgs& R = A.ray;
+  const int tiles_x = (R.width + 7) / 8;
+  const int n_tiles = tiles_x * ((R.rows + 3) / 4);
   unsigned nsamp = 0;
   unsigned long long status = 0;
-  if (active) {
-    if constexpr (SHADE == 0) {
-      // unshaded: the ray frame lives in shared memory (read once per segment), leaving the
-      // registers to the sample loop (measured 6 % faster on C2 at 2048^2; with shading
-      // the extra shared-memory reads cost more than the spills they save).  One padding
-      // word keeps the odd-sized slots free of bank conflicts.
-      __shared__ RayFSlot s_rf[128];
-      A.out[(size_t)jr * A.ray.width + i] =
-          march_ray<ST, INTERP, SHADE>(A, A.ray, i, j, s_tf, s_nz, s_rf[tid].f, nsamp, status);
-    } else {
-      RayF rf;
-      A.out[(size_t)jr * A.ray.width + i] =
-          march_ray<ST, INTERP, SHADE>(A, A.ray, i, j, s_tf, s_nz, rf, nsamp, status);
+  // each pass takes one tile, and the queue hands out every tile once
+  for (;;) {
+    int t = 0;
+    if (lane == 0) {
+      const unsigned long long q = atomicAdd(A.counters + kQueueCounter, 1ull);
+      t = q < (unsigned long long)n_tiles ? (int)q : n_tiles;
+    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_tiles) break;
+    const int i = (t % tiles_x) * 8 + (lane & 7);
+    const int jr = (t / tiles_x) * 4 + (lane >> 3);
+    const int j = R.row0 + jr;
+    if (i < R.width && jr < R.rows && j < R.height) {
+      if constexpr (SHADE == 0) {
+        // unshaded: the ray frame lives in shared memory (read once per segment), leaving
+        // the registers to the sample loop (measured 6 % faster on C2 at 2048^2; with
+        // shading the extra shared-memory reads cost more than the spills they save).  One
+        // padding word keeps the odd-sized slots free of bank conflicts.
+        __shared__ RayFSlot s_rf[128];
+        A.out[(size_t)jr * R.width + i] =
+            march_ray<ST, INTERP, SHADE>(A, R, i, j, s_tf, s_nz, s_rf[tid].f, nsamp, status);
+      } else {
+        RayF rf;
+        A.out[(size_t)jr * R.width + i] =
+            march_ray<ST, INTERP, SHADE>(A, R, i, j, s_tf, s_nz, rf, nsamp, status);
+      }
     }
   }
-  // exact sample count: one atomic per warp
   const unsigned total = __reduce_add_sync(0xffffffffu, nsamp);
-  if ((tid & 31) == 0 && total) atomicAdd(A.counters, (unsigned long long)total);
+  if (lane == 0 && total) atomicAdd(A.counters, (unsigned long long)total);
   if (status) atomicOr(A.counters + 1, status);
 }
 

@@ -229,6 +229,8 @@ __device__ __forceinline__ float4 march_deferred(const RenderArgs& A, const RayA
   return make_float4(C0, C1, C2, Acc);
 }
 
+// Schedule 3: persistent warps taking 8x4-pixel tiles from the global queue (as
+// march_kernel does for the per-ray loop), each marching its tile with deferred shading.
 template <int ST, int SHADE>
 __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS_DEFERRED)
     deferred_kernel(const __grid_constant__ RenderArgs A) {
@@ -240,16 +242,30 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS_DEFERRED)
   DeferArea& Q = reinterpret_cast<DeferArea*>(reinterpret_cast<char*>(smem) +
                                               ((tf_bytes + 15) & ~(size_t)15))[tid >> 5];
   stage_tf(A.tf, A.tf_n, s_tf, s_nz, tid, blockDim.x * blockDim.y);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int jr = blockIdx.y * blockDim.y + threadIdx.y;
-  const int j = A.ray.row0 + jr;
-  const bool active = i < A.ray.width && jr < A.ray.rows && j < A.ray.height;
+  const int lane = tid & 31;
+  const RayArgs& R = A.ray;
+  const int tiles_x = (R.width + 7) / 8;
+  const int n_tiles = tiles_x * ((R.rows + 3) / 4);
   unsigned nsamp = 0;
   unsigned long long status = 0;
-  const float4 c = march_deferred<ST, SHADE>(A, A.ray, i, j, active, s_tf, s_nz, Q, nsamp, status);
-  if (active) A.out[(size_t)jr * A.ray.width + i] = c;
+  // each pass takes one tile, and the queue hands out every tile once
+  for (;;) {
+    int t = 0;
+    if (lane == 0) {
+      const unsigned long long q = atomicAdd(A.counters + kQueueCounter, 1ull);
+      t = q < (unsigned long long)n_tiles ? (int)q : n_tiles;
+    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_tiles) break;
+    const int i = (t % tiles_x) * 8 + (lane & 7);
+    const int jr = (t / tiles_x) * 4 + (lane >> 3);
+    const int j = R.row0 + jr;
+    const bool active = i < R.width && jr < R.rows && j < R.height;
+    const float4 c = march_deferred<ST, SHADE>(A, R, i, j, active, s_tf, s_nz, Q, nsamp, status);
+    if (active) A.out[(size_t)jr * R.width + i] = c;
+  }
   const unsigned total = __reduce_add_sync(0xffffffffu, nsamp);
-  if ((tid & 31) == 0 && total) atomicAdd(A.counters, (unsigned long long)total);
+  if (lane == 0 && total) atomicAdd(A.counters, (unsigned long long)total);
   if (status) atomicOr(A.counters + 1, status);
 }
 

@@ -22,12 +22,12 @@ cudaError_t launch_one(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_
   return cudaGetLastError();
 }
 
-// Persistent launch of the refill schedule: as many blocks as fit on the device, at most
-// one warp per 8x4 pixel tile.
+// Persistent launch of the refill schedule: the queue head is zeroed, then as many blocks
+// as fit on the device start, at most one warp per 8x4 pixel tile.
 template <typename K>
 cudaError_t launch_persist(K kernel, size_t smem, cudaStream_t s, const RenderArgs& a) {
-  cudaError_t e = cudaSuccess;
-  if (smem > 48 * 1024)
+  cudaError_t e = cudaMemsetAsync(a.counters + kQueueCounter, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess && smem > 48 * 1024)
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, sms = 0, occ = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -37,6 +37,26 @@ cudaError_t launch_persist(K kernel, size_t smem, cudaStream_t s, const RenderAr
   const long long tiles = (long long)((a.ray.width + 7) / 8) * ((a.ray.rows + 3) / 4);
   const long long grid = std::max(1LL, std::min((long long)sms * std::max(occ, 1), (tiles + 3) / 4));
   kernel<<<(unsigned)grid, dim3(8, 16), smem, s>>>(a, a.samples_per_iter);
+  return cudaGetLastError();
+}
+
+// Persistent launch of the tile-queue kernels (march_kernel, deferred_kernel): the queue
+// head is zeroed (every launch owns its queue, also when a caller renders a frame in
+// several bands on one set of counters), then as many 128-thread blocks as are resident at
+// once start, at most one warp per 8x4 tile.
+template <typename K>
+cudaError_t launch_tiles(K kernel, size_t smem, cudaStream_t s, const RenderArgs& a) {
+  cudaError_t e = cudaMemsetAsync(a.counters + kQueueCounter, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess && smem > 48 * 1024)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 0, occ = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, smem);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (long long)((a.ray.width + 7) / 8) * ((a.ray.rows + 3) / 4);
+  const long long grid = std::max(1LL, std::min((long long)sms * std::max(occ, 1), (tiles + 3) / 4));
+  kernel<<<(unsigned)grid, dim3(8, 16), smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -55,9 +75,9 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
         return fail(c, AMR_ERR_ARG, "secondary rays render trilinear with schedule 0");
       const size_t smem = tf_bytes;
       const int base = shade & 3;
-      if (base == 0) e = launch_one(march_kernel<ST, 1, kShadeShadow>, grid, block, smem, s, a);
-      else if (base == 1) e = launch_one(march_kernel<ST, 1, 1 | kShadeShadow>, grid, block, smem, s, a);
-      else e = launch_one(march_kernel<ST, 1, 2 | kShadeShadow>, grid, block, smem, s, a);
+      if (base == 0) e = launch_tiles(march_kernel<ST, 1, kShadeShadow>, smem, s, a);
+      else if (base == 1) e = launch_tiles(march_kernel<ST, 1, 1 | kShadeShadow>, smem, s, a);
+      else e = launch_tiles(march_kernel<ST, 1, 2 | kShadeShadow>, smem, s, a);
     } else {
       return fail(c, AMR_ERR_ARG, "secondary rays need the ptr or atlas_linear storage, FP32 cells");
     }
@@ -66,8 +86,8 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
     if (interp != 1 || (shade != 1 && shade != 2))
       return fail(c, AMR_ERR_ARG, "deferred shading renders trilinear with shade = 1");
     const size_t smem = ((tf_bytes + 15) & ~(size_t)15) + 4 * sizeof(DeferArea);
-    if (shade == 1) e = launch_one(deferred_kernel<ST, 1>, grid, block, smem, s, a);
-    else e = launch_one(deferred_kernel<ST, 2>, grid, block, smem, s, a);
+    if (shade == 1) e = launch_tiles(deferred_kernel<ST, 1>, smem, s, a);
+    else e = launch_tiles(deferred_kernel<ST, 2>, smem, s, a);
   } else if (schedule == 2) {
     // persistent warps with ray refill (trilinear)
     if (interp != 1) return fail(c, AMR_ERR_ARG, "the refill schedule renders trilinear");
@@ -80,16 +100,16 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
     if (interp != 1 || schedule != 0)
       return fail(c, AMR_ERR_ARG, "16-bit storage renders trilinear with schedule 0, 2 or 3");
     const size_t smem = tf_bytes;
-    if (shade == 0) e = launch_one(march_kernel<ST, 1, 0>, grid, block, smem, s, a);
-    else if (shade == 1) e = launch_one(march_kernel<ST, 1, 1>, grid, block, smem, s, a);
-    else e = launch_one(march_kernel<ST, 1, 2>, grid, block, smem, s, a);
+    if (shade == 0) e = launch_tiles(march_kernel<ST, 1, 0>, smem, s, a);
+    else if (shade == 1) e = launch_tiles(march_kernel<ST, 1, 1>, smem, s, a);
+    else e = launch_tiles(march_kernel<ST, 1, 2>, smem, s, a);
   } else if (schedule == 0) {
     const size_t smem = tf_bytes;
-    if (interp == 1 && shade == 0) e = launch_one(march_kernel<ST, 1, 0>, grid, block, smem, s, a);
-    else if (interp == 1 && shade == 1) e = launch_one(march_kernel<ST, 1, 1>, grid, block, smem, s, a);
-    else if (interp == 1 && shade == 2) e = launch_one(march_kernel<ST, 1, 2>, grid, block, smem, s, a);
-    else if (interp == 0 && shade == 0) e = launch_one(march_kernel<ST, 0, 0>, grid, block, smem, s, a);
-    else e = launch_one(march_kernel<ST, 0, 1>, grid, block, smem, s, a);
+    if (interp == 1 && shade == 0) e = launch_tiles(march_kernel<ST, 1, 0>, smem, s, a);
+    else if (interp == 1 && shade == 1) e = launch_tiles(march_kernel<ST, 1, 1>, smem, s, a);
+    else if (interp == 1 && shade == 2) e = launch_tiles(march_kernel<ST, 1, 2>, smem, s, a);
+    else if (interp == 0 && shade == 0) e = launch_tiles(march_kernel<ST, 0, 0>, smem, s, a);
+    else e = launch_tiles(march_kernel<ST, 0, 1>, smem, s, a);
   } else {
     const size_t smem = ((tf_bytes + 15) & ~(size_t)15) + 4 * sizeof(WarpArea);
     if (interp == 1 && shade == 0) e = launch_one(wave_kernel<ST, 1, 0>, grid, block, smem, s, a);

@@ -37,7 +37,7 @@ def _noalloc(lib, ctx, cam_s, tf, p, out):
     return st, int(n.value)
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3])
 def test_noalloc_matches_render_host_on_two_calls(setup, schedule):
     amr, _lib, w, ctx, cam = setup
     lib = _lib.load()
