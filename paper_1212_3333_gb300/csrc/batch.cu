@@ -22,7 +22,9 @@ namespace {
 // DEFER: the warp-synchronous march with deferred shading (schedule 3) instead of the
 // per-ray loop; each warp's queue area follows the transfer functions in shared memory.
 template <int ST, int SHADE, int TW, int TH, bool DEFER>
-__global__ void __launch_bounds__(TW * TH, (128 * kMinBlocks<SHADE>) / (TW * TH))
+__global__ void __launch_bounds__(TW * TH,
+                                  (128 * (DEFER ? AMR_MIN_BLOCKS_DEFERRED : kMinBlocks<SHADE>)) /
+                                      (TW * TH))
     batch_kernel(const __grid_constant__ BatchArgs B) {
   constexpr int NT = TW * TH;
   const RenderArgs& A = B.A;

@@ -650,13 +650,15 @@ __device__ __forceinline__ int nearest_index_exact(const RayArgs& A, const DLeve
 
 // Cross-leaf gradient neighbour x_k + sign h^l e_a: descend the tree on finest-cell
 // coordinates relative to the current leaf corner; a split within the error margin sends
-// the decision to FP64.  Takes scalars only, so the caller keeps its state in registers,
-// and the current leaf's level and corner come from the caller, so the first load of the
-// lookup is the face table.  (x0, x1, x2): the neighbour in finest cells from the leaf
-// corner (lo0, lo1, lo2); mf: its error margin in finest cells; beyond: the point lies
-// clearly beyond the face (a, sign).
+// the decision to FP64.  The current leaf's level and corner come from the caller, so the
+// first load of the lookup is the face table.  (x0, x1, x2): the neighbour in finest cells
+// from the leaf corner (lo0, lo1, lo2); mf: its error margin in finest cells; beyond: the
+// point lies clearly beyond the face (a, sign).  Inlined at its one call site (the rolled
+// neighbour loop): as a call, saving and restoring the caller's live registers around
+// 18.5 M lookups per C2 2048^2 frame cost more than the lookups (measured 52.8 -> 61.6
+// Gsamples/s).
 template <int ST, int INTERP>
-__device__ __noinline__ float neighbour_slow(const RenderArgs& A, const RayArgs& R, int px, int py,
+__device__ __forceinline__ float neighbour_slow(const RenderArgs& A, const RayArgs& R, int px, int py,
                                              int leaf_lod, int level, int lo0, int lo1, int lo2,
                                              int pid0, int pid1, int n, int k, float mf,
                                              float x0, float x1, float x2, int a, float sign,
@@ -1198,8 +1200,9 @@ __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const RayArg
 }
 
 // Resident 128-thread blocks per SM the compiler must allow for, i.e. a register budget of
-// 65536 / (128 x this) per thread.  Measured on C2 at 2048^2 (Gsamples/s, Phong / unshaded):
-// 3 blocks 30.8 / 119.3, 4 blocks 34.1 / 119.4, 5 blocks 36.1 / 119.7, 6 blocks 33.2 / 126.0.
+// 65536 / (128 x this) per thread.  Measured on C2 at 2048^2 (Gsamples/s): Phong 3 / 4 / 5
+// blocks 59.8 / 64.9 / 61.6 (cross-leaf lookups inlined); unshaded 3 / 4 / 5 / 6 blocks
+// 119.3 / 119.4 / 119.7 / 126.0 (before persistent warps).
 // The learned march keeps the MLP fragments live beside the ray state: 3 blocks (168
 // registers) measured fastest there (coarse16@0.01 on C2 at 2048^2: 2.25x the plain march
 // at 3 blocks, 1.90x at 4, 1.57x at 5).
@@ -1207,7 +1210,7 @@ __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const RayArg
 #define AMR_MIN_BLOCKS 3
 #endif
 #ifndef AMR_MIN_BLOCKS_SHADED
-#define AMR_MIN_BLOCKS_SHADED 5
+#define AMR_MIN_BLOCKS_SHADED 4
 #endif
 #ifndef AMR_MIN_BLOCKS_PLAIN
 #define AMR_MIN_BLOCKS_PLAIN 6

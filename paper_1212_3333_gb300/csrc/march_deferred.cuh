@@ -39,8 +39,10 @@ struct DeferArea {
   float3 col[32];
 };
 
+// resident blocks per SM the register budget allows for (measured on C2, Phong, 2048^2 /
+// 1024^2 / 512^2 Gsamples/s: 3 blocks 61.3 / 46.1 / 28.9, 4 blocks 55.9 / 41.9 / 24.9)
 #ifndef AMR_MIN_BLOCKS_DEFERRED
-#define AMR_MIN_BLOCKS_DEFERRED 5
+#define AMR_MIN_BLOCKS_DEFERRED 3
 #endif
 
 // Colour of queued sample t (what composite_sample computes for an opaque sample).
