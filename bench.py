@@ -706,6 +706,7 @@ def main():
         extra["batch_small_views"] = batch_eval(amr, ctx, vmin, vmax, args, peak, lo=64, hi=256,
                                                 tune_views=64)
         if args.shade == 1:
+            extra["batch_deferred"] = batch_eval(amr, ctx, vmin, vmax, args, peak, schedule=3)
             extra["batch_small_views_deferred"] = batch_eval(
                 amr, ctx, vmin, vmax, args, peak, lo=64, hi=256, tune_views=64, schedule=3)
     if args.schedules and world == 1:
