@@ -1299,8 +1299,11 @@ __device__ __forceinline__ void stage_tf(const float4* __restrict__ tf, int n, f
 // until none is left, so a warp that finishes its rays starts on new ones at once instead
 // of idling until the slowest warp of its block is done (measured on C2 at 2048^2: Phong
 // 50.0 -> 52.9 Gsamples/s against one block per 8x16 tile); the grid holds only as many
-// blocks as are resident at once.
-template <int ST, int INTERP, int SHADE>
+// blocks as are resident at once.  QUEUE = false: one block per 8x16 tile, each warp
+// marching its own 8x4 tile once - used for the per-patch texture storage, whose fetches
+// need more registers than the queue loop leaves (C2 2048^2 unshaded: 44.5 against 9.3
+// Gsamples/s with the queue).
+template <int ST, int INTERP, int SHADE, bool QUEUE = true>
 __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
     march_kernel(const __grid_constant__ RenderArgs A) {
   extern __shared__ float4 smem[];
@@ -1310,21 +1313,9 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
   stage_tf(A.tf, A.tf_n, s_tf, s_nz, tid, blockDim.x * blockDim.y);
   const int lane = tid & 31;
   const RayArgs& R = A.ray;
-  const int tiles_x = (R.width + 7) / 8;
-  const int n_tiles = tiles_x * ((R.rows + 3) / 4);
   unsigned nsamp = 0;
   unsigned long long status = 0;
-  // each pass takes one tile, and the queue hands out every tile once
-  for (;;) {
-    int t = 0;
-    if (lane == 0) {
-      const unsigned long long q = atomicAdd(A.counters + kQueueCounter, 1ull);
-      t = q < (unsigned long long)n_tiles ? (int)q : n_tiles;
-    }
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= n_tiles) break;
-    const int i = (t % tiles_x) * 8 + (lane & 7);
-    const int jr = (t / tiles_x) * 4 + (lane >> 3);
+  auto march_pixel = [&](int i, int jr) {
     const int j = R.row0 + jr;
     if (i < R.width && jr < R.rows && j < R.height) {
       if constexpr (SHADE == 0) {
@@ -1341,6 +1332,23 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
             march_ray<ST, INTERP, SHADE>(A, R, i, j, s_tf, s_nz, rf, nsamp, status);
       }
     }
+  };
+  if constexpr (QUEUE) {
+    const int tiles_x = (R.width + 7) / 8;
+    const int n_tiles = tiles_x * ((R.rows + 3) / 4);
+    // each pass takes one tile, and the queue hands out every tile once
+    for (;;) {
+      int t = 0;
+      if (lane == 0) {
+        const unsigned long long q = atomicAdd(A.counters + kQueueCounter, 1ull);
+        t = q < (unsigned long long)n_tiles ? (int)q : n_tiles;
+      }
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t >= n_tiles) break;
+      march_pixel((t % tiles_x) * 8 + (lane & 7), (t / tiles_x) * 4 + (lane >> 3));
+    }
+  } else {
+    march_pixel(blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
   }
   const unsigned total = __reduce_add_sync(0xffffffffu, nsamp);
   if (lane == 0 && total) atomicAdd(A.counters, (unsigned long long)total);

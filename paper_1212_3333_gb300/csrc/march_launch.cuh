@@ -103,6 +103,14 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
     if (shade == 0) e = launch_tiles(march_kernel<ST, 1, 0>, smem, s, a);
     else if (shade == 1) e = launch_tiles(march_kernel<ST, 1, 1>, smem, s, a);
     else e = launch_tiles(march_kernel<ST, 1, 2>, smem, s, a);
+  } else if (schedule == 0 && ST == ST_TEXOBJ) {
+    // per-patch textures: one block per 8x16 tile (see march_kernel)
+    const size_t smem = tf_bytes;
+    if (interp == 1 && shade == 0) e = launch_one(march_kernel<ST, 1, 0, false>, grid, block, smem, s, a);
+    else if (interp == 1 && shade == 1) e = launch_one(march_kernel<ST, 1, 1, false>, grid, block, smem, s, a);
+    else if (interp == 1 && shade == 2) e = launch_one(march_kernel<ST, 1, 2, false>, grid, block, smem, s, a);
+    else if (interp == 0 && shade == 0) e = launch_one(march_kernel<ST, 0, 0, false>, grid, block, smem, s, a);
+    else e = launch_one(march_kernel<ST, 0, 1, false>, grid, block, smem, s, a);
   } else if (schedule == 0) {
     const size_t smem = tf_bytes;
     if (interp == 1 && shade == 0) e = launch_tiles(march_kernel<ST, 1, 0>, smem, s, a);
