@@ -5,7 +5,8 @@
 //                      c + 1), so the top of the tree is a contiguous prefix that one
 //                      cache line per few nodes serves to a whole warp (Sec. 3.2 stores the
 //                      second child at the next texel for the same reason).
-//   int4   node_box[2N] 32 B per node slot: its box (rope restarts).
+//   int4   node_box[2N] 32 B per node slot: its box and the highest label level of
+//                      a type-(a) node above it (rope restarts).
 //   DLeaf  leaves[M]  96 B each, canonical (pre-order) leaf id order, with the
 //                      addressing of the leaf's brick.
 //   DPatch patches[P] 48 B each: where a patch's brick lives and how to address it.
@@ -47,20 +48,22 @@ struct alignas(16) DLeaf {
   long long base;        // brick (DPatch::base), the same for every leaf of a patch
   long long gbase;       // gradient brick (DPatch::gbase)
   int32_t lo[3], hi[3];  // box, finest-level cells
-  int32_t patch;
+  int32_t lod_anc;       // highest label level of a type-(a) node above this leaf, -1: none
   int32_t level;
+  int32_t patch;
   float vmin, vmax;      // range of every value a sample of this leaf can interpolate
   int32_t faces;         // bit 2a (+1): the level cell beyond the lower (upper) face on axis
                          // a lies in the same patch and is not refined
   int32_t sy, sz;        // brick strides (DPatch::sy, sz)
   int32_t blo[3];        // brick: patch box lo (DPatch::lo)
   int32_t dim[3];        // brick extent with halo (DPatch::dim)
-  int32_t pad;
 };
 static_assert(sizeof(DLeaf) == 96, "DLeaf is six 16-byte words");
-// lo and hi fill the record's second 16-byte word and half its third (rope restarts read
+// lo, hi and lod_anc fill the record's second and third 16-byte words (rope restarts read
 // them as two int4)
-static_assert(offsetof(DLeaf, lo) == 16 && offsetof(DLeaf, hi) == 28, "DLeaf box layout");
+static_assert(offsetof(DLeaf, lo) == 16 && offsetof(DLeaf, hi) == 28 &&
+                  offsetof(DLeaf, lod_anc) == 40,
+              "DLeaf box layout");
 
 struct DPatch {
   long long base;      // pointer table: device address of the brick; linear atlas: element
@@ -102,6 +105,7 @@ struct RayArgs {
   int32_t levels;       // 1 + the finest level of a type-(a) node (0: none)
   double lod_scale;
   float lod_scale_f;
+  int32_t n_leaves;     // leaves of the unpruned tree (ids at or above are pruned leaves)
 };
 
 struct RenderArgs {
@@ -113,8 +117,9 @@ struct RenderArgs {
                                // leaf and the cell beyond the face, then the cell alone
                                // (starts of neighbour lookups; the second half: ropes);
                                // an entry with kFaceLeaf set names a leaf id instead
-  const int4* node_box;        // per node slot, 2: box lo (x, y, z, 0), hi (x, y, z, 0),
-                               // finest cells (rope restarts)
+  const int4* node_box;        // per node slot, 2: box lo (x, y, z, highest label level of
+                               // a type-(a) node above it or -1), hi (x, y, z, 0), finest
+                               // cells (rope restarts)
   const DPatch* patches;
   const void* pool;            // linear atlas base (element type of the storage)
   const float4* gpool;         // linear atlas of gradient bricks (float4 per cell)

@@ -59,6 +59,7 @@ void fill_ray(const amr_ctx* c, const amr_camera* cam, int row0, int rows, RayAr
     ra->root_f[a] = (int32_t)c->root[a];
     ra->root_f[3 + a] = (int32_t)c->root[3 + a];
   }
+  ra->n_leaves = (int32_t)c->tree.leaf_patch.size();
   ra->tan_half_fov_y = cam->tan_half_fov_y;
   ra->width = cam->width;
   ra->height = cam->height;

@@ -20,20 +20,24 @@ namespace {
 
 // breadth-first re-layout: children of a node are adjacent, the top levels contiguous;
 // lod receives each slot's pruned-leaf entry (id << 5 | level) or -1, box each slot's box
-// (lo, hi as two int4, finest cells) starting from the root box
+// (lo, hi as two int4, finest cells) starting from the root box with the highest label
+// level of a type-(a) node above the slot in lo.w, leaf_anc that level per leaf
 std::vector<DNode> layout_nodes(const Tree& t, const int64_t* root, std::vector<int32_t>& lod,
-                                std::vector<int32_t>& slot_of, std::vector<int4>& box) {
+                                std::vector<int32_t>& slot_of, std::vector<int4>& box,
+                                std::vector<int32_t>& leaf_anc) {
   const size_t n = t.axis.size();
   std::vector<DNode> out(n);
   lod.assign(n, -1);
   slot_of.assign(n, 0);
   box.assign(2 * std::max<size_t>(n, 1), make_int4(0, 0, 0, 0));
+  leaf_anc.assign(t.leaf_patch.size(), -1);
   struct Item {
     int pre, slot;
     int32_t b[6];
+    int32_t anc;  // highest label level of a type-(a) node above this one, -1: none
   };
   std::deque<Item> q;
-  Item r{0, 0, {}};
+  Item r{0, 0, {}, -1};
   for (int k = 0; k < 6; ++k) r.b[k] = (int32_t)root[k];
   q.push_back(r);
   int next = 1;
@@ -42,19 +46,24 @@ std::vector<DNode> layout_nodes(const Tree& t, const int64_t* root, std::vector<
     q.pop_front();
     const int pre = it.pre, slot = it.slot;
     slot_of[pre] = slot;
-    box[2 * (size_t)slot] = make_int4(it.b[0], it.b[1], it.b[2], 0);
+    box[2 * (size_t)slot] = make_int4(it.b[0], it.b[1], it.b[2], it.anc);
     box[2 * (size_t)slot + 1] = make_int4(it.b[3], it.b[4], it.b[5], 0);
+    const int32_t lq = t.node_lod.empty() ? -1 : t.node_lod[pre];
+    const int32_t lvl = lq >= 0 ? t.lod_level[(size_t)lq - t.leaf_patch.size()] : -1;
+    if (lq >= 0) lod[slot] = (lq << 5) | lvl;
     DNode d;
     if (t.axis[pre] < 0) {
       d.meta = ((uint32_t)kLeafAxis << 30) | ((uint32_t)t.leaf[pre] & kIndexMask);
       d.split = 0;
+      leaf_anc[(size_t)t.leaf[pre]] = it.anc;
     } else {
       int first = next;
       next += 2;
       const int ax = t.axis[pre];
       d.meta = ((uint32_t)ax << 30) | ((uint32_t)first & kIndexMask);
       d.split = t.split[pre];
-      Item lc{t.left[pre], first, {}}, rc{t.right[pre], first + 1, {}};
+      const int32_t anc = std::max(it.anc, lvl);
+      Item lc{t.left[pre], first, {}, anc}, rc{t.right[pre], first + 1, {}, anc};
       std::memcpy(lc.b, it.b, sizeof lc.b);
       std::memcpy(rc.b, it.b, sizeof rc.b);
       lc.b[3 + ax] = t.split[pre];
@@ -63,11 +72,6 @@ std::vector<DNode> layout_nodes(const Tree& t, const int64_t* root, std::vector<
       q.push_back(rc);
     }
     out[slot] = d;
-    const int32_t q = t.node_lod.empty() ? -1 : t.node_lod[pre];
-    if (q >= 0) {
-      const int32_t lvl = t.lod_level[(size_t)q - t.leaf_patch.size()];
-      lod[slot] = (q << 5) | lvl;
-    }
   }
   return out;
 }
@@ -234,7 +238,8 @@ amr_status upload(amr_ctx* c, void* stream_v) {
     return fail(c, AMR_ERR_CAPACITY, "tree too large for 30-bit node indices");
   std::vector<int32_t> lodv, slot_of;
   std::vector<int4> boxes;
-  std::vector<DNode> nodes = layout_nodes(t, c->root, lodv, slot_of, boxes);
+  std::vector<int32_t> leaf_anc;
+  std::vector<DNode> nodes = layout_nodes(t, c->root, lodv, slot_of, boxes, leaf_anc);
   std::vector<int32_t> face_slots(std::max<size_t>(1, t.face_node.size()), 0);
   for (size_t k = 0; k < t.face_node.size(); ++k) {
     const int32_t pre = t.face_node[k];
@@ -252,6 +257,7 @@ amr_status upload(amr_ctx* c, void* stream_v) {
     l.patch = lod ? t.lod_patch[m - M] : t.leaf_patch[m];
     l.level = lod ? t.lod_level[m - M] : t.leaf_level[m];
     l.faces = (lod || t.leaf_faces.empty()) ? 0 : t.leaf_faces[m];
+    l.lod_anc = lod ? -1 : leaf_anc[m];
     // the range of the cells as stored; rounding is monotone, so the rounded extremes
     // bound every rounded cell and empty-space skipping stays exact
     l.vmin = storage_round(c->dtype, c->leaf_vmin[m]);

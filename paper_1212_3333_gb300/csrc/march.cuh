@@ -367,28 +367,33 @@ __device__ __forceinline__ int descend(const DNode* __restrict__ nodes, const Ra
 // ray passes near an edge of N) the caller descends from the push-down start.  On the
 // exit-face axis the ray is inside N (N's lower side on that axis is the face or behind
 // it); on an axis the ray runs parallel to, its coordinate stays inside the face's extent,
-// which N holds.  Returns the leaf when N is one (nothing left to descend), -2 - N's slot
-// for an inner node, -1 for no rope.
+// which N holds.  Under level-of-detail pruning the root descent stops at the first
+// type-(a) node whose label level reaches lod_min; the rope is taken only when no node
+// above N does (N and its subtree the descent from N checks itself).  Returns the leaf when
+// N is one (nothing left to descend), -2 - N's slot for an inner node, -1 for no rope.
 __device__ __forceinline__ int rope_start(const int32_t* __restrict__ face_node,
                                           const int4* __restrict__ node_box,
                                           const DLeaf* __restrict__ leaves, const RayArgs& R,
                                           int px, int py, const RayF& rf, int prev, int pid0,
                                           float tau0, float e0, int& pid1, float& tau1,
-                                          float& e1) {
+                                          float& e1, int lod_min) {
   const int a = pid0 & 3;
   const bool up = sel3f(a, rf.B[0], rf.B[1], rf.B[2]) > 0.0f;
   const uint32_t ent = (uint32_t)__ldg(face_node + 12 * prev + 6 + 2 * a + (up ? 1 : 0));
-  int blo[3], bhi[3];
+  int blo[3], bhi[3], anc;
   if (ent & kFaceLeaf) {
     const int4* w = reinterpret_cast<const int4*>(leaves + (ent & ~kFaceLeaf));
-    const int4 w1 = __ldg(w + 1), w2 = __ldg(w + 2);  // lo[3], hi[0] | hi[1], hi[2], ...
+    const int4 w1 = __ldg(w + 1), w2 = __ldg(w + 2);  // lo[3], hi[0] | hi[1], hi[2], lod_anc
     blo[0] = w1.x, blo[1] = w1.y, blo[2] = w1.z;
     bhi[0] = w1.w, bhi[1] = w2.x, bhi[2] = w2.y;
+    anc = w2.z;
   } else {
     const int4 lo = __ldg(node_box + 2 * ent), hi = __ldg(node_box + 2 * ent + 1);
     blo[0] = lo.x, blo[1] = lo.y, blo[2] = lo.z;
     bhi[0] = hi.x, bhi[1] = hi.y, bhi[2] = hi.z;
+    anc = lo.w;
   }
+  if (anc >= lod_min) return -1;  // a node above N may stop the pruned descent
   int pid[3];
   float ts[3], es[3];
 #pragma unroll
@@ -424,8 +429,9 @@ __device__ __forceinline__ int rope_start(const int32_t* __restrict__ face_node,
 }
 
 // Leaf of the segment starting at (pid0, tau0) that follows leaf `prev` (-1 on the first
-// segment): by rope while pruning is off, else (or when the rope's filter cannot decide)
-// by the push-down descent.  The leaf and the exact t1 are the same either way; only the
+// segment): by rope when prev is a leaf of the unpruned tree, else (or when the rope's
+// filter cannot decide, or a node above the rope's target may stop the pruned descent) by
+// the push-down descent.  The leaf and the exact t1 are the same either way; only the
 // plane id recorded for t1 may differ, between planes whose t1 is the same FP64 value.
 __device__ __forceinline__ int next_leaf(const DNode* __restrict__ nodes,
                                          const DLeaf* __restrict__ leaves,
@@ -434,9 +440,9 @@ __device__ __forceinline__ int next_leaf(const DNode* __restrict__ nodes,
                                          int px, int py, const RayF& rf, uint32_t& start,
                                          int prev, int pid0, float tau0, float e0, int& pid1,
                                          float& tau1, float& e1, int lod_min = kNoLod) {
-  if (prev >= 0 && !(R.lod_scale_f > 0.0f)) {
+  if (prev >= 0 && prev < R.n_leaves) {
     const int r = rope_start(face_node, node_box, leaves, R, px, py, rf, prev, pid0, tau0, e0,
-                             pid1, tau1, e1);
+                             pid1, tau1, e1, lod_min);
     if (r >= 0) return r;
     if (r <= -2)
       return descend_from(nodes, R, px, py, rf, (uint32_t)(-2 - r), false, start, pid0, tau0, e0,
@@ -672,12 +678,23 @@ __device__ __forceinline__ float neighbour_slow(const RenderArgs& A, const RayAr
   const bool pruning = lod_min < kNoLod;
   // the neighbour lies in the leaf or in the level cell beyond its face (a, sign): start at
   // the deepest node holding both, or the cell alone when the point is clearly beyond the
-  // face, which the face table names directly when it is a leaf (from the root under
-  // pruning, which may stop above them)
+  // face, which the face table names directly when it is a leaf.  Under pruning only when
+  // no type-(a) node above that start reaches the bound (else from the root), and never
+  // from a pruned leaf (the table covers the unpruned leaves)
   uint32_t i = 0;
-  if (!pruning) {
-    i = (uint32_t)__ldg(A.face_node + 12 * leaf + (beyond ? 6 : 0) + 2 * a + (sign > 0.0f ? 1 : 0));
-    if (i & kFaceLeaf) lid = (int)(i & ~kFaceLeaf);
+  if (leaf < R.n_leaves) {
+    const uint32_t ent =
+        (uint32_t)__ldg(A.face_node + 12 * leaf + (beyond ? 6 : 0) + 2 * a + (sign > 0.0f ? 1 : 0));
+    bool ok = true;
+    if (pruning) {
+      const int anc = (ent & kFaceLeaf) ? __ldg(&A.leaves[ent & ~kFaceLeaf].lod_anc)
+                                        : __ldg(&A.node_box[2 * ent].w);
+      ok = anc < lod_min;
+    }
+    if (ok) {
+      if (ent & kFaceLeaf) lid = (int)(ent & ~kFaceLeaf);
+      else i = ent;
+    }
   }
   for (int depth = 0; lid < 0 && depth < kMaxDepth; ++depth) {
     const DNode nd = A.nodes[i];
