@@ -1,8 +1,8 @@
 // Device side of the single-pass AMR raycaster (Sec. 3.3 of Kaehler & Abel).
 //
-// One thread per pixel; a 128-thread block covers an 8x16 pixel tile and each warp an 8x4
-// sub-tile, so the rays of a warp traverse nearly the same leaves and read nearly the same
-// brick cache lines.
+// One thread per pixel; each warp marches 8x4-pixel tiles (taken from a queue by
+// persistent warps), so the rays of a warp traverse nearly the same leaves and read nearly
+// the same brick cache lines.
 //
 // Exactness without FP64 throughput.  The reference semantics are FP64: ray parameters of
 // split planes t_s = (plane - o) / d decide the kd-restart descent, and the per-segment
@@ -871,9 +871,10 @@ __device__ __forceinline__ int segment_count(const RayArgs& R, int px, int py, c
 
 // Central-difference gradient g_a = (F(x + h e_a) - F(x - h e_a)) / 2h at sample beta.
 // When all six neighbours lie inside the current leaf (beyond the error margin), they are
-// trilinear values of the same brick and share one 32-cell stencil: the differences along
-// an axis are lerps of the two outer cell pairs, combined bilinearly in the other axes.
-// Otherwise each neighbour goes through neighbour_value (cross-leaf lookups).
+// trilinear values of the same brick: one interpolation of the gradient brick's per-cell
+// differences, or one 32-cell stencil (the differences along an axis are lerps of the two
+// outer cell pairs, combined bilinearly in the other axes).  Otherwise each neighbour goes
+// through neighbour_at (cross-leaf lookups), in one rolled loop.
 template <int ST, int INTERP, int GB>
 __device__ __forceinline__ void gradient(const RenderArgs& A, const RayArgs& R, const SegState& s,
                                          const float* beta,
