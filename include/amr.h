@@ -106,7 +106,7 @@ typedef struct {
                          coarser step */
   double tau;         /* proposal threshold (default 1e-3) */
   int32_t samples_per_iter; /* schedules 2 and 3: samples a lane takes between warp steps,
-                               1..64 (default 4) */
+                               1..64 (default 16) */
   int32_t coarse_factor;    /* learned mode 2: a segment predicted below tau takes
                                ceil(n / coarse_factor) samples, 2..64 (default 4) */
   double lod_pixels;        /* level-of-detail pruning (Sec. 3.1 type-(a) nodes, Sec. 3.3):

@@ -123,7 +123,7 @@ void amr_default_params(amr_render_params* p) {
   p->schedule = 0;
   p->learned = 0;
   p->tau = 1e-3;
-  p->samples_per_iter = 4;
+  p->samples_per_iter = 16;  // measured best for schedule 3 on C2 at 512^2 .. 2048^2
   p->coarse_factor = 4;
   p->light_ambient = 0.2;
 }
