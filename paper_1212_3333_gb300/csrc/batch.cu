@@ -5,9 +5,9 @@
 // shared memory and marches the tile's pixels with the same per-pixel code as the
 // single-view kernel, so each view's image is bit-identical to its own amr_render.  Up to
 // eight transfer functions are staged in shared memory once per block.  With schedule 3
-// each warp marches its rays with the deferred-shading loop instead of the per-ray loop.  The view table
-// travels in the kernel's parameter block, so a call is one memset and one launch and can
-// be captured in a CUDA graph.  The paper renders one view per pass; batching is an
+// each warp marches its rays with the deferred-shading loop instead of the per-ray loop.
+// The view table travels in the kernel's parameter block, so a call is one memset and one
+// launch and can be captured in a CUDA graph.  The paper renders one view per pass; batching is an
 // addition for throughput over many small and large views.
 #include <cuda_runtime.h>
 

@@ -302,7 +302,8 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   if (!(p->lod_pixels >= 0.0) || !std::isfinite(p->lod_pixels))
     return fail(c, AMR_ERR_ARG, "lod_pixels must be finite and non-negative");
   if (p->lod_pixels > 0.0 && (p->schedule == 1 || p->learned != 0))
-    return fail(c, AMR_ERR_ARG, "level-of-detail pruning needs schedule 0, 2 or 3 without the proposal");
+    return fail(c, AMR_ERR_ARG,
+                "level-of-detail pruning needs schedule 0, 2 or 3 without the proposal");
   if (p->shadow != 0 && p->shadow != 1) return fail(c, AMR_ERR_ARG, "shadow must be 0 or 1");
   if (p->shadow) {
     for (int a = 0; a < 3; ++a)

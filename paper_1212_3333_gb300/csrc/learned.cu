@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(128) log_kernel(const __grid_constant__ Render
   for (int seg = 0; pid0 != kPidOut && seg < A.max_segments; ++seg) {
     int pid1 = kPidOut;
     float tau1 = rf.tau_out, e1 = exit_bound(rf);
-    const int lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, A.ray, i, j, rf, start, prev, pid0,
-                              tau0, e0, pid1, tau1, e1);
+    const int lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, A.ray, i, j, rf, start,
+                              prev, pid0, tau0, e0, pid1, tau1, e1);
     if (lid < 0) break;
     prev = lid;
     const DLeaf lf = A.leaves[lid];
@@ -172,8 +172,8 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
         ++nseg;
         tau1 = rf.tau_out;
         e1 = exit_bound(rf);
-        lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, A.ray, i, j, rf, start, prev, pid0, tau0,
-                        e0, pid1, tau1, e1);
+        lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, A.ray, i, j, rf, start, prev,
+                        pid0, tau0, e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;
           live = false;

@@ -133,8 +133,8 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
           int pid1 = kPidOut;
           float tau1 = rf.tau_out, e1 = exit_bound(rf);
           const int lmin = lod_min_level(R, A.lv, rf, i, R.row0 + jr, pid0, tau0, e0);
-          const int lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, R, i, R.row0 + jr, rf,
-                                    start, prev, pid0, tau0, e0, pid1, tau1, e1, lmin);
+          const int lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, R, i, R.row0 + jr,
+                                    rf, start, prev, pid0, tau0, e0, pid1, tau1, e1, lmin);
           if (lid < 0) {
             status |= kStatusDevice;
             finish();

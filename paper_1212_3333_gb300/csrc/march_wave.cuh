@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(128) wave_kernel(const __grid_constant__ Rende
         ++nseg;
         int pid1 = kPidOut;
         float tau1 = rf.tau_out, e1 = exit_bound(rf);
-        const int lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, A.ray, i, j, rf, start, prev,
-                                  pid0, tau0, e0, pid1, tau1, e1);
+        const int lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, A.ray, i, j, rf,
+                                  start, prev, pid0, tau0, e0, pid1, tau1, e1);
         if (lid < 0) {
           status |= kStatusDevice;
           live = false;

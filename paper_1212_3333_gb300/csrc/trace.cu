@@ -28,8 +28,8 @@ __global__ void __launch_bounds__(128) trace_kernel(const __grid_constant__ Trac
     int pid1 = kPidOut;
     float tau1 = rf.tau_out, e1 = exit_bound(rf);
     const int lmin = lod_min_level(A.ray, A.lv, rf, i, j, pid0, tau0, e0);
-    const int lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, A.ray, i, j, rf, start, prev, pid0,
-                              tau0, e0, pid1, tau1, e1, lmin);
+    const int lid = next_leaf(A.nodes, A.leaves, A.face_node, A.node_box, A.ray, i, j, rf, start,
+                              prev, pid0, tau0, e0, pid1, tau1, e1, lmin);
     if (lid < 0) {
       status |= kStatusDevice;
       break;
