@@ -103,6 +103,30 @@ def test_atlas_packing_is_valid():
     assert 0.0 < st.atlas_efficiency <= st.atlas_efficiency_halo <= 1.0
 
 
+@pytest.mark.parametrize("seed", [3, 5])
+def test_brick_bytes_and_packing_efficiency_follow_their_definitions(seed):
+    """Memory statistics (the quantities of the paper's Table 2): one FP32 value per cell,
+    bricks carrying a one-cell halo (Sec. 4), packing efficiency = data cells / atlas cells
+    (Sec. 4.1), with and without the halos."""
+    h = random_hierarchy(seed, n0=8, num_levels=3, patches_per_level=8, max_size=12, tiles=5)
+    n = (h.patch_box[:, 3:] - h.patch_box[:, :3]).astype(np.int64)
+    cells = int(np.prod(n, axis=1).sum())
+    halo_cells = int(np.prod(n + 2, axis=1).sum())
+    for storage in ("ptr", "atlas_linear"):
+        ctx = amr.from_hierarchy(h)
+        ctx.amr_build_host(storage)
+        st = ctx.amr_get_stats()
+        assert st.num_patches == h.num_patches
+        assert st.num_cells == cells
+        assert st.brick_bytes == 4 * halo_cells
+        if storage == "atlas_linear":
+            vol = int(np.prod(np.array(st.atlas_dims[:], dtype=np.int64)))
+            assert vol >= halo_cells  # bricks are disjoint inside the atlas box
+            assert st.atlas_efficiency == pytest.approx(cells / vol, rel=1e-12)
+            assert st.atlas_efficiency_halo == pytest.approx(halo_cells / vol, rel=1e-12)
+        ctx.amr_destroy()
+
+
 @pytest.mark.parametrize("boxes,levels,code", [
     ([[0, 0, 0, 4, 4, 4], [2, 0, 0, 4, 4, 4]], [0, 0], _lib.AMR_ERR_OVERLAP),
     ([[0, 0, 0, 2, 2, 2], [2, 2, 2, 4, 4, 4]], [0, 0], _lib.AMR_ERR_NOT_TILED),
