@@ -13,6 +13,13 @@
  *   - Every call returns an amr_status; nothing aborts or exits.  amr_last_error() gives
  *     a message for the last failing call on a context (per context, not thread-safe:
  *     use one context per thread at a time).
+ *   - Every device loop is bounded; a kernel that meets a bound (segments per ray, samples
+ *     per segment, descent depth) sets a status word instead of trapping, and the call
+ *     that synchronises reports AMR_ERR_CAPACITY or AMR_ERR_DEVICE.
+ *   - Fault injection for tests (host side only): the environment variable AMR_FAULT =
+ *     bad_alloc makes the host build fail with AMR_ERR_OOM, oom the device upload's first
+ *     allocation (AMR_ERR_OOM), corrupt_node uploads a root node that names itself as a
+ *     child (indices stay in range; renders report AMR_ERR_DEVICE).  Unset: no effect.
  *   - Level l has spacing h^l = h^0 / r^l per axis (Sec. 2).  Patch boxes are int64[6]
  *     {lo_x, lo_y, lo_z, hi_x, hi_y, hi_z}, half-open, in level-l cell indices.  Level 0
  *     must tile its bounding box (the kD root, Sec. 3.1); same-level patches must be

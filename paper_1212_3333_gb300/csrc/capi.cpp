@@ -224,6 +224,7 @@ amr_status amr_build_host(amr_ctx* c, amr_storage storage_flags) {
     return fail(c, AMR_ERR_ARG, "16-bit cells need the ptr or atlas_linear storage");
   auto t0 = std::chrono::steady_clock::now();
   try {
+    if (fault_injected("bad_alloc")) throw std::bad_alloc();
     if (!c->host_built) {
       amr_status s = validate_hierarchy(c);
       if (s != AMR_OK) return s;

@@ -3,6 +3,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <cstdlib>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -10,6 +12,18 @@
 #include "amr_device.h"
 
 namespace amr {
+
+// Host-side fault injection for tests of the error paths (no GPU fault is ever provoked):
+// the environment variable AMR_FAULT names one failure to simulate -
+//   bad_alloc     the host build runs out of memory            -> AMR_ERR_OOM
+//   oom           the device upload's first allocation fails   -> AMR_ERR_OOM
+//   corrupt_node  the uploaded root node names itself as a child (every index stays in
+//                 range), so descents loop until their depth bound -> AMR_ERR_DEVICE
+// Unset or any other value: no effect.
+inline bool fault_injected(const char* what) {
+  const char* v = std::getenv("AMR_FAULT");
+  return v && std::strcmp(v, what) == 0;
+}
 
 struct Patch {
   int level;

@@ -240,6 +240,9 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   std::vector<int4> boxes;
   std::vector<int32_t> leaf_anc;
   std::vector<DNode> nodes = layout_nodes(t, c->root, lodv, slot_of, boxes, leaf_anc);
+  if (fault_injected("corrupt_node") && nodes.size() > 1 &&
+      (nodes[0].meta >> 30) != (uint32_t)kLeafAxis)
+    nodes[0].meta &= ~kIndexMask;  // the root's children become slots 0 (itself) and 1
   std::vector<int32_t> face_slots(std::max<size_t>(1, t.face_node.size()), 0);
   for (size_t k = 0; k < t.face_node.size(); ++k) {
     const int32_t pre = t.face_node[k];
@@ -271,6 +274,7 @@ amr_status upload(amr_ctx* c, void* stream_v) {
       pt[p].dim[a] = (int32_t)(c->patches[p].n[a] + 2);
     }
   }
+  if (fault_injected("oom")) return fail(c, AMR_ERR_OOM, "injected device allocation failure");
   CK(cudaMalloc(&d.nodes, nodes.size() * sizeof(DNode)));
   CK(cudaMalloc(&d.lod, lodv.size() * sizeof(int32_t)));
   CK(cudaMalloc(&d.face_node, face_slots.size() * sizeof(int32_t)));

@@ -172,3 +172,16 @@ def test_render_before_build_is_a_state_error():
     assert lib.amr_render(ctx._h, C.byref(cam), C.c_void_p(16), 256, C.byref(p), C.c_void_p(16),
                           None, None) == _lib.AMR_ERR_STATE
     assert lib.amr_destroy(None) == _lib.AMR_OK
+
+
+def test_injected_host_allocation_failure(monkeypatch):
+    """AMR_FAULT=bad_alloc: the host build reports AMR_ERR_OOM with a message and leaves
+    the context usable; without the variable the same context builds."""
+    ctx = amr.from_hierarchy(synth.make_c1())
+    lib = _lib.load()
+    monkeypatch.setenv("AMR_FAULT", "bad_alloc")
+    assert lib.amr_build_host(ctx._h, _lib.AMR_STORE_PTR) == _lib.AMR_ERR_OOM
+    assert b"memory" in lib.amr_last_error(ctx._h)
+    monkeypatch.setenv("AMR_FAULT", "none")
+    ctx.amr_build_host("ptr")
+    assert ctx.amr_get_stats().num_leaves > 0
