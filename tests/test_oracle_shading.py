@@ -72,15 +72,18 @@ def test_linear_field_shading_across_levels_is_phong_of_the_true_normal():
                                rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("interp", [1, 0])
 @pytest.mark.parametrize("gamma", [0.5, 2.0])
-def test_gradient_floor_scales_the_normal(gamma):
-    n = 16  # one level, h = 1/16: g = (0, 0, 1), floor gamma * 1 / h = 16 gamma > 1
+def test_gradient_floor_scales_the_normal(gamma, interp):
+    # one level, h = 1/16: g = (0, 0, 1) also under nearest sampling (the neighbours' cells
+    # are the sample's cell +- one, whose centres differ by 2h); floor gamma * 1 / h = 16 gamma
+    n = 16
     h = make_uniform(n, lambda X, Y, Z: Z)
     o = oracle.Oracle(h)
     tf = _box_tf(0.3, 0.7)
     cam = look_camera((0.4, 0.2, -1.0), (0.5, 0.55, 0.5), (0, 1, 0), 30.0, 9, 8)
     pr = oracle.OracleParams(vmin=0.0, vmax=1.0, kappa=6.0, ert_eps=0.0, shade=1,
-                             gamma=gamma)
+                             gamma=gamma, interp=interp)
     img, _ = o.render(cam, tf, pr)
     floor = gamma * 1.0 * n
     hit = _check(img, cam, lambda d: abs(d[2]) / (floor * np.linalg.norm(d)))
