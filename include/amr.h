@@ -196,9 +196,13 @@ amr_status amr_render_host(amr_ctx* ctx, const amr_camera* cam, const float* tf_
  * equal amr_render_host's; limits: 2 <= tf_n <= 2048, image width <= 16384
  * (AMR_ERR_ARG beyond them).  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) for that device; make that first call before any stream
- * capture.  Every call reuses the array (the counters are cleared per call); calls that
- * overlap on the GPU race, so serialise them.  Synchronises the stream before returning;
- * samples_out (nullable) receives the sample count. */
+ * capture.  Under CUDA's lazy module loading that first call is also when the array is
+ * committed on the device, so a caller whose footprint must be fixed before rendering
+ * makes one call at start-up.  The current device must be the one the context was built
+ * on (else AMR_ERR_STATE).  Every call reuses the array (the counters are cleared per
+ * call); calls that overlap on the GPU race, so serialise them.  Synchronises the stream
+ * before returning, on errors too once work was queued; samples_out (nullable) receives
+ * the sample count. */
 amr_status amr_render_host_noalloc(amr_ctx* ctx, const amr_camera* cam,
                                    const float* tf_rgba_host, int32_t tf_n,
                                    const amr_render_params* params, float* out_rgba_host,

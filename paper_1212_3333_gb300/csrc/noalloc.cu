@@ -16,6 +16,12 @@
 // band is copied to the caller's host image, so the image size is not limited; one row must
 // fit (width <= 16384 pixels).  Calls that overlap on the GPU (several streams or threads at
 // once) share the array and race; serialise them.
+//
+// With CUDA's lazy module loading the array is committed when this file's module is first
+// used on a device, i.e. by the first call there (the address lookup); a caller whose
+// footprint must be fixed before rendering makes one call at start-up.  The looked-up
+// address is cached per device ordinal; cudaDeviceReset invalidates it, as it does every
+// context's device memory (such contexts must be destroyed, not rendered).
 #include <cstring>
 #include <mutex>
 
@@ -38,12 +44,16 @@ constexpr int kMaxDevices = 256;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of g_scratch on the current device (the host-side symbol is only a
-// stand-in, never a device address).  Looked up once per device.
+// stand-in, never a device address).  Looked up once per device.  The current device must
+// be the one the context was uploaded to: the kernel reads the context's tree and bricks
+// there, so scratch on another device would be a foreign address.
 amr_status scratch_address(amr_ctx* c, void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(c, AMR_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(c, AMR_ERR_CUDA, "device ordinal out of range");
+  if (dev != c->dev.device)
+    return fail(c, AMR_ERR_STATE, "the current device is not the one the context was built on");
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
@@ -90,11 +100,17 @@ extern "C" amr_status amr_render_host_noalloc(amr_ctx* c, const amr_camera* cam,
       params->rows <= 0 ? cam->height - first : std::min(params->rows, cam->height - first);
   const int band_rows =
       (int)(kBandBytes / ((size_t)cam->width * sizeof(float4)) / kTileRows) * kTileRows;
-#define CKN(call)                                                                    \
-  do {                                                                               \
-    cudaError_t e_ = (call);                                                         \
-    if (e_ != cudaSuccess)                                                           \
-      return fail(c, AMR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  // once work is queued, an error return first waits for it: the queued copies write the
+  // caller's host image, which the caller may free as soon as the call returns
+  auto drain = [&](amr_status r) {
+    cudaStreamSynchronize(st);
+    return r;
+  };
+#define CKN(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return drain(fail(c, AMR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
   } while (0)
   // the array keeps the previous call's contents: start the counters from zero
   CKN(cudaMemsetAsync(counters, 0, kCounterBytes, st));
@@ -106,13 +122,13 @@ extern "C" amr_status amr_render_host_noalloc(amr_ctx* c, const amr_camera* cam,
     p.rows = std::min(band_rows, total - r);
     RenderArgs a;
     s = prepare_render_args(c, cam, tf_n, &p, &a);
-    if (s != AMR_OK) return s;
+    if (s != AMR_OK) return drain(s);
     a.tf = tf_dev;
     a.out = band;
     a.counters = counters;
     a.ray.counters = counters;
     s = launch_render_args(c, a, &p, cuda_stream);
-    if (s != AMR_OK) return s;
+    if (s != AMR_OK) return drain(s);
     CKN(cudaMemcpyAsync(out_rgba_host + (size_t)r * cam->width * 4, band,
                         (size_t)p.rows * cam->width * sizeof(float4), cudaMemcpyDeviceToHost, st));
   }

@@ -69,3 +69,30 @@ def test_noalloc_rejects_sizes_beyond_its_staging(setup):
     tf = np.ascontiguousarray(w["tf"], dtype=np.float32)
     st, _ = _noalloc(lib, ctx, amr.make_camera(wide), tf, p, out)
     assert st == _lib.AMR_ERR_ARG and b"16384" in lib.amr_last_error(ctx._h)
+
+
+def test_noalloc_leaves_device_free_memory_unchanged(setup):
+    """The property the entry point exists for: on a warmed context, calls allocate no
+    device memory - not for a repeat of the same frame, and not for a wider image with a
+    longer transfer function, which would make amr_render_host grow its staging buffers."""
+    import torch
+
+    amr, _lib, w, ctx, cam = setup
+    lib = _lib.load()
+    p = amr.amr_default_params(vmin=w["vmin"], vmax=w["vmax"], shade=1)
+    tf = np.ascontiguousarray(w["tf"], dtype=np.float32)
+    tf_long = np.ascontiguousarray(np.repeat(tf, 4, axis=0), dtype=np.float32)  # 1024 entries
+    wide = synth.orbit_camera(1, 6000, 40, fov_y_deg=12.0)
+    outs = {}
+    for c in (cam, wide):
+        outs[c.width] = np.zeros((c.height, c.width, 4), dtype=np.float32)
+    # warm-up: the first call on the device looks up (and commits) the staging array
+    st, _ = _noalloc(lib, ctx, amr.make_camera(cam), tf, p, outs[cam.width])
+    assert st == _lib.AMR_OK, lib.amr_last_error(ctx._h)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for c, t in ((cam, tf), (wide, tf_long), (cam, tf), (wide, tf_long)):
+        st, n = _noalloc(lib, ctx, amr.make_camera(c), t, p, outs[c.width])
+        assert st == _lib.AMR_OK, lib.amr_last_error(ctx._h)
+        assert n > 0
+        assert torch.cuda.mem_get_info()[0] == free0, "the no-alloc call changed free device memory"
