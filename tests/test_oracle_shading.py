@@ -88,3 +88,49 @@ def test_gradient_floor_scales_the_normal(gamma, interp):
     floor = gamma * 1.0 * n
     hit = _check(img, cam, lambda d: abs(d[2]) / (floor * np.linalg.norm(d)))
     assert hit > 30
+
+
+def test_gradient_floor_takes_the_segment_level_across_levels():
+    # two levels: level 0 is 16^3 (h = 1/16), a level-1 slab x in [0.375, 0.625) covers all
+    # of y and z (h = 1/32).  With gamma 0.5 the floor is 8 in coarse leaves and 16 in fine
+    # ones, both above |g| = 1, so |n.L| = |d_z| / (floor_l |d|) with l the level of the
+    # sample's own leaf.  Rays run nearly along +z; a pixel is checked when all of its
+    # opaque samples (z in [0.3, 0.7]) lie in one region: coarse, the slab's interior, or
+    # the slab's outer fine cells, whose x-neighbours at +-1/32 lie in a coarse leaf (where
+    # a floor taken from a neighbour's level instead of the segment's would be 8, not 16)
+    h = make_hierarchy_from_boxes(2, 2, (16, 16, 16),
+                                  [[0, 0, 0, 16, 16, 16], [12, 0, 0, 20, 32, 32]], [0, 1],
+                                  lambda X, Y, Z: Z)
+    o = oracle.Oracle(h)
+    tf = _box_tf(0.3, 0.7)
+    W, H = 61, 5
+    dist = 40.0
+    # horizontal half-width 0.36 at the volume's centre: pixels span x in [0.14, 0.86]
+    fov_y = 2.0 * np.degrees(np.arctan(0.36 / (dist + 0.5) * H / W))
+    cam = look_camera((0.5, 0.5, -dist), (0.5, 0.5, 0.5), (0, 1, 0), fov_y, W, H)
+    gamma = 0.5
+    pr = oracle.OracleParams(vmin=0.0, vmax=1.0, kappa=6.0, ert_eps=0.0, shade=1, gamma=gamma)
+    img, _ = o.render(cam, tf, pr)
+    lo_f, hi_f, hf = 0.375, 0.625, 1.0 / 32
+    seen = {"coarse": 0, "fine": 0, "fine_edge": 0}
+    for j in range(H):
+        for i in range(W):
+            o_, d = ray_of_pixel(cam, i, j)
+            xs = [o_[0] + (z - o_[2]) / d[2] * d[0] for z in (0.29, 0.71)]
+            x0, x1 = min(xs), max(xs)
+            if x1 < lo_f - 1e-3 or x0 >= hi_f + 1e-3:
+                region, floor = "coarse", gamma * 16
+            elif x0 >= lo_f + hf + 1e-3 and x1 < hi_f - hf - 1e-3:
+                region, floor = "fine", gamma * 32
+            elif (x0 >= lo_f + 1e-3 and x1 < lo_f + hf - 1e-3) or \
+                    (x0 >= hi_f - hf + 1e-3 and x1 < hi_f - 1e-3):
+                region, floor = "fine_edge", gamma * 32
+            else:
+                continue
+            A = img[j, i, 3]
+            assert A > 1e-3, (i, j)
+            want = _phong(abs(d[2]) / (floor * np.linalg.norm(d)))
+            np.testing.assert_allclose(img[j, i, :3] / A, want, rtol=0, atol=1e-9,
+                                       err_msg=f"pixel {(i, j)} ({region})")
+            seen[region] += 1
+    assert seen["coarse"] >= 20 and seen["fine"] >= 10 and seen["fine_edge"] >= 5, seen
