@@ -498,6 +498,15 @@ def make_c3(seed: int = 3, device=None, use_cache: bool = False,
                           use_cache=use_cache, cell_budget=cell_budget)
 
 
+def make_deep(seed: int = 3, device=None, use_cache: bool = True,
+              cell_budget: int = 12_000_000) -> Hierarchy:
+    """The deep configuration's shape at a size that generates in seconds: the C3 generator
+    (8 levels, finest spacing 1/16384, threshold 4x the mean on every level) with each
+    refined level capped at `cell_budget` cells (about 1e8 cells in all instead of 1e9)."""
+    return make_lognormal(seed=seed, num_levels=8, level_growth=1.0, device=device,
+                          name="deep", use_cache=use_cache, cell_budget=cell_budget)
+
+
 def percentile_range(hier: Hierarchy, q: float = 99.9):
     allv = np.concatenate([d.ravel() for d in hier.data])
     return float(allv.min()), float(np.percentile(allv, q))

@@ -262,3 +262,17 @@ def test_c2_trace_sampled(amr, c2):
         assert np.array_equal(tseq[q, :len(leaf), 0], t0)
         assert np.array_equal(tseq[q, :len(leaf), 1], t1)
     del torch
+
+
+def test_c2_exact_sample_total_1024_without_ert(amr, c2):
+    # the bench hierarchy at 1024²: with early termination off the sample total is fixed by
+    # the traversal and the per-segment counts alone, so GPU and FP64 oracle agree exactly
+    h, vmin, vmax, o = c2
+    ctx = amr.from_hierarchy(h)
+    ctx.amr_build_kdtree("ptr")
+    cam = synth.orbit_camera(2, 1024, 1024)
+    tf = synth.ramp_tf()
+    p, op = params_pair(amr, vmin, vmax, shade=0, ert_eps=0.0)
+    _, n = gpu_render(ctx, cam, tf, p)
+    _, smp = o.render(cam, tf, op)
+    assert n == int(smp.sum()) and n > 10 ** 8
