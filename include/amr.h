@@ -73,7 +73,14 @@ typedef enum {
    * three central differences of the cell values, 4x the brick bytes).  Shaded trilinear
    * renders then read one float4 stencil per opaque sample instead of 32 cells whenever
    * all six gradient neighbours lie in the sample's leaf; results are unchanged. */
-  AMR_STORE_GRADIENT = 0x100
+  AMR_STORE_GRADIENT = 0x100,
+  /* flag: bricks carry a two-cell halo (the paper's bricks, Sec. 4, need one), and a leaf
+   * face whose far side - the slab of one cell of the leaf's level - lies only in leaves
+   * of that same level (any patch) lets the gradient neighbours there read the leaf's own
+   * brick, as a face onto the same unrefined patch does with one cell.  The halo cells
+   * hold V_l like the first layer.  Not in the paper; results agree with the one-cell
+   * layout to FP32 rounding. */
+  AMR_STORE_HALO2 = 0x200
 } amr_storage;
 
 /* Pinhole camera.  Pixel (i, j), row 0 at the top, has the ray o = eye,
@@ -86,6 +93,13 @@ typedef struct {
 } amr_camera;
 
 typedef enum { AMR_INTERP_NEAREST = 0, AMR_INTERP_TRILINEAR = 1 } amr_interp;
+
+/* amr_render_params.schedule value that lets the library choose (the default): deferred
+ * shading (3) where it applies (Phong, trilinear, no learned proposal) for images of fewer
+ * than 3,000,000 pixels, for batches of views and with secondary rays; the per-ray loop
+ * (0) otherwise.  Not in the paper; every schedule renders the same image bit for bit
+ * (with secondary rays: to rounding, see shadow). */
+#define AMR_SCHEDULE_AUTO (-1)
 
 typedef struct {
   double step_factor; /* sample step = step_factor * h^l of the leaf's level (Sec. 3.3) */
@@ -106,7 +120,7 @@ typedef struct {
                          with new rays and fetch segments in batches (trilinear only);
                          3: warps march their rays in step and shade the opaque samples
                          32 at a time (trilinear, shade = 1 only).  All give the same
-                         image. */
+                         image.  AMR_SCHEDULE_AUTO (-1, the default) picks one per call. */
   int32_t learned;    /* learned segment proposal (needs amr_set_proposal; trilinear; ptr or
                          atlas_linear storage, FP32 cells): 0 off; 1 skip segments whose predicted
                          contribution is below tau; 2 sample them with a coarse_factor times
@@ -121,23 +135,32 @@ typedef struct {
                                level l once min_a h^l_a <= lod_pixels * (2 tan_half_fov_y / H)
                                * t0 (t0 the segment's entry parameter, a unit fwd assumed),
                                and samples it at level l; gradients then read the same pruned
-                               tree.  0 (default) renders every level.  Schedules 0 and 2,
-                               no learned proposal. */
+                               tree.  0 (default) renders every level.  Schedules 0, 2 and
+                               3, no learned proposal. */
   int32_t shadow;           /* 1: secondary rays to a point light (the global-illumination
                                example of Sec. 5): an opaque sample at x is lit by
                                I = light_ambient + (1 - light_ambient) T, T the transmittance
                                of the part of x -> light inside the root box, marched with
                                n = max(1, ceil(len / light_step)) midpoint samples of the AMR
                                field (T = prod exp(-kappa a_TF len / n), 0 once <= 1e-4);
-                               its colour is multiplied by I.  Trilinear; not schedule 1. */
+                               its colour is multiplied by I.  Trilinear; schedule 0 (each
+                               lane marches its samples' light rays) or 3 with shade = 1
+                               (a warp marches each light ray 32 samples at a time; T then
+                               differs from schedule 0's by rounding only). */
   double light[3];          /* light position (world) */
   double light_step;        /* world step along secondary rays (> 0 with shadow) */
   double light_ambient;     /* in [0, 1] (default 0.2) */
+  int32_t learned_min_samples; /* learned modes: the proposal is consulted only for segments
+                                  of at least this many samples (shorter ones are sampled as
+                                  the plain march samples them), 1..2^22 (default 1: every
+                                  segment; skipping short segments is where the proposal
+                                  saves most, measured on the 5-level hierarchy) */
+  int32_t reserved;
 } amr_render_params;
 
 /* Fills p with the defaults: step 0.5, kappa 8, ert_eps 1e-4, vmin 0, vmax 1, ka 0.3,
  * kd 0.6, ks 0.3, shininess 32, gamma 1e-3, trilinear, unshaded, all rows, no skip,
- * per-ray schedule. */
+ * schedule AMR_SCHEDULE_AUTO, samples_per_iter 16. */
 void amr_default_params(amr_render_params* p);
 
 /* Create a context from an AMR hierarchy (Sec. 2: h^l = h^0 / r^l, patches Gamma^l_m).
@@ -155,7 +178,9 @@ amr_status amr_create(int32_t num_levels, int32_t refine_ratio, const double dom
 /* Build the kD-tree (Sec. 3.1: min-crossing planes, balanced tie-break, level-by-level
  * refinement), the per-patch bricks with a one-cell halo (Sec. 4: one brick per subgrid),
  * the chosen storage (Sec. 4.1 packing / 4.2 handle table) and upload everything on
- * `cuda_stream`.  `storage` is an amr_storage strategy, optionally OR AMR_STORE_GRADIENT.
+ * `cuda_stream`.  `storage` is an amr_storage strategy, optionally OR AMR_STORE_GRADIENT
+ * and / or AMR_STORE_HALO2 (a different halo than the context's first build rebuilds the
+ * host data).
  * The call returns after the uploads complete.  With AMR_F16 / AMR_BF16 cells: only
  * AMR_STORE_PTR and AMR_STORE_ATLAS_LINEAR (else AMR_ERR_ARG); gradient bricks hold the
  * value and the FP32 central differences, each rounded to the 16-bit type; AMR_F16 returns
@@ -213,7 +238,8 @@ amr_status amr_render_host_noalloc(amr_ctx* ctx, const amr_camera* cam,
 /* ---------------------------------------------------------------------------------- */
 
 #define AMR_MAX_BATCH_VIEWS 128
-#define AMR_BATCH_CANDIDATES 9   /* tiles 8x8, 16x8, 16x16  x  rays per thread 1, 2, 4 */
+#define AMR_BATCH_CANDIDATES 13  /* tiles 8x8, 16x8, 16x16  x  rays per thread 1, 2, 4;
+                                    then samples per iteration 4, 8, 16, 32 */
 
 /* One view of a batch: its camera, which transfer function it uses, and where its image
  * starts in the shared output buffer (in floats; a multiple of 4). */
@@ -227,9 +253,11 @@ typedef struct {
 /* Work decomposition of a batched render: pixel tiles of tile_w x tile_h threads (8x8,
  * 16x8 or 16x16), each thread marching rays_per_thread (1..8) pixels of a column of its
  * tile, so a queue item covers tile_w x (tile_h * rays_per_thread) pixels; blocks_per_sm
- * caps the persistent grid per SM (0: as many as fit). */
+ * caps the persistent grid per SM (0: as many as fit); samples_per_iter (0: the params'
+ * value, else 1..64) is the deferred schedule's samples per lane between warp steps. */
 typedef struct {
   int32_t tile_w, tile_h, rays_per_thread, blocks_per_sm;
+  int32_t samples_per_iter;
 } amr_batch_config;
 
 /* Render n_views (1..AMR_MAX_BATCH_VIEWS) views of the context's dataset in one persistent
@@ -240,7 +268,8 @@ typedef struct {
  *   tfs_rgba_dev   device float32 [n_tf][tf_n][4], 1 <= n_tf <= 8, n_tf * tf_n <= 2048
  *   out_rgba_dev   device float32 [out_floats]; view v writes [H][W][4] at out_offset;
  *                  images must not overlap; buffers 16-byte aligned
- *   config         NULL: the context's last autotuned configuration (initially 16x8, 1)
+ *   config         NULL: the context's last autotuned configuration (initially 16x8, 1,
+ *                  the params' samples_per_iter)
  * Needs the ptr storage with FP32 cells, trilinear sampling, schedule 0 (per-ray loop) or
  * 3 (deferred shading, shade = 1), no learned proposal and no secondary rays (else
  * AMR_ERR_ARG).  Issues one cudaMemsetAsync and one kernel launch
@@ -253,12 +282,15 @@ amr_status amr_render_batch(amr_ctx* ctx, const amr_view* views, int32_t n_views
                             int64_t out_floats, const amr_batch_config* config,
                             void* cuda_stream, uint64_t* samples_out);
 
-/* Time every candidate configuration (tile 8x8 / 16x8 / 16x16 x rays per thread 1 / 2 / 4,
- * blocks_per_sm 0) on this batch: one warm-up and `reps` (1..1000) timed renders each,
- * CUDA events on cuda_stream.  ms_out (nullable) receives the mean milliseconds of the
- * AMR_BATCH_CANDIDATES candidates in that order (tile-major); best_out (nullable) the
- * fastest, which the context also keeps for amr_render_batch calls without a config.
- * Synchronises; arguments as amr_render_batch. */
+/* Time candidate configurations on this batch, one warm-up and `reps` (1..1000) timed
+ * renders each, CUDA events on cuda_stream: first the 9 tiles 8x8 / 16x8 / 16x16 x rays
+ * per thread 1 / 2 / 4 (blocks_per_sm 0, the params' samples_per_iter), then - for deferred
+ * shading (schedule 3, also as AMR_SCHEDULE_AUTO picks it for batches) - the best of those
+ * with samples_per_iter 4, 8, 16 and 32.  ms_out (nullable) receives the mean milliseconds
+ * of the AMR_BATCH_CANDIDATES candidates in that order (tile-major; -1 for the last four
+ * under the per-ray schedule, which has no samples-per-iteration knob); best_out
+ * (nullable) the fastest, which the context also keeps for amr_render_batch calls without
+ * a config.  Synchronises; arguments as amr_render_batch. */
 amr_status amr_batch_autotune(amr_ctx* ctx, const amr_view* views, int32_t n_views,
                               const float* tfs_rgba_dev, int32_t n_tf, int32_t tf_n,
                               const amr_render_params* params, float* out_rgba_dev,

@@ -74,16 +74,19 @@ class AmrContext:
 
     # ----------------------------------------------------------------- lifecycle
     @staticmethod
-    def _storage_code(storage, gradient: bool) -> int:
+    def _storage_code(storage, gradient: bool, halo: int = 1) -> int:
         st = STORAGES[storage] if isinstance(storage, str) else int(storage)
-        return st | (AMR_STORE_GRADIENT if gradient else 0)
+        if halo not in (1, 2):
+            raise ValueError("halo must be 1 or 2")
+        return st | (AMR_STORE_GRADIENT if gradient else 0) | (_lib.AMR_STORE_HALO2 if halo == 2 else 0)
 
-    def amr_build_kdtree(self, storage="ptr", stream=None, gradient: bool = False) -> None:
-        st = self._storage_code(storage, gradient)
+    def amr_build_kdtree(self, storage="ptr", stream=None, gradient: bool = False,
+                         halo: int = 1) -> None:
+        st = self._storage_code(storage, gradient, halo)
         _check(self._lib.amr_build_kdtree(self._h, st, C.c_void_p(_stream_ptr(stream))), self._h)
 
-    def amr_build_host(self, storage="ptr", gradient: bool = False) -> None:
-        st = self._storage_code(storage, gradient)
+    def amr_build_host(self, storage="ptr", gradient: bool = False, halo: int = 1) -> None:
+        st = self._storage_code(storage, gradient, halo)
         _check(self._lib.amr_build_host(self._h, st), self._h)
 
     def amr_destroy(self) -> None:
@@ -188,7 +191,7 @@ class AmrContext:
         return box, arrs[0], arrs[1], arrs[2]
 
     def amr_get_leaf_faces(self):
-        """Per leaf: same-patch face bits and the 12 neighbour-lookup start nodes."""
+        """Per leaf: face bits (DLeaf.faces) and the 12 neighbour-lookup start nodes."""
         n = C.c_int64(0)
         self._lib.amr_get_leaf_faces(self._h, None, None, 0, C.byref(n))
         m = n.value
@@ -256,8 +259,9 @@ def make_views(cameras, tf_index):
 
 
 def batch_config(tile_w: int = 16, tile_h: int = 8, rays_per_thread: int = 1,
-                 blocks_per_sm: int = 0):
-    return _lib.amr_batch_config(tile_w, tile_h, rays_per_thread, blocks_per_sm)
+                 blocks_per_sm: int = 0, samples_per_iter: int = 0):
+    return _lib.amr_batch_config(tile_w, tile_h, rays_per_thread, blocks_per_sm,
+                                 samples_per_iter)
 
 
 def from_hierarchy(hier, dtype=AMR_F32) -> AmrContext:

@@ -22,6 +22,7 @@ AMR_F32, AMR_F16, AMR_BF16 = 0, 1, 2
 DTYPES = {"f32": AMR_F32, "f16": AMR_F16, "bf16": AMR_BF16}
 AMR_STORE_PTR, AMR_STORE_TEXOBJ, AMR_STORE_ATLAS_LINEAR, AMR_STORE_ATLAS_TEX3D = 0, 1, 2, 3
 AMR_STORE_GRADIENT = 0x100
+AMR_STORE_HALO2 = 0x200
 AMR_MLP_FEATURES, AMR_MLP_PARAMS, AMR_MLP_PACKED_BYTES = 12, 9217, 23440
 STORAGES = {"ptr": AMR_STORE_PTR, "texobj": AMR_STORE_TEXOBJ,
             "atlas_linear": AMR_STORE_ATLAS_LINEAR, "atlas_tex3d": AMR_STORE_ATLAS_TEX3D}
@@ -43,7 +44,8 @@ class amr_render_params(C.Structure):
                 ("learned", C.c_int32), ("tau", C.c_double), ("samples_per_iter", C.c_int32),
                 ("coarse_factor", C.c_int32), ("lod_pixels", C.c_double),
                 ("shadow", C.c_int32), ("light", C.c_double * 3), ("light_step", C.c_double),
-                ("light_ambient", C.c_double)]
+                ("light_ambient", C.c_double), ("learned_min_samples", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class amr_stats(C.Structure):
@@ -57,7 +59,8 @@ class amr_stats(C.Structure):
 
 
 AMR_MAX_BATCH_VIEWS = 128
-AMR_BATCH_CANDIDATES = 9
+AMR_SCHEDULE_AUTO = -1
+AMR_BATCH_CANDIDATES = 13
 
 
 class amr_view(C.Structure):
@@ -67,7 +70,7 @@ class amr_view(C.Structure):
 
 class amr_batch_config(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("rays_per_thread", C.c_int32),
-                ("blocks_per_sm", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("samples_per_iter", C.c_int32)]
 
 
 # every symbol include/amr.h declares, with its ctypes signature

@@ -10,7 +10,7 @@
 //   DLeaf  leaves[M]  96 B each, canonical (pre-order) leaf id order, with the
 //                      addressing of the leaf's brick.
 //   DPatch patches[P] 48 B each: where a patch's brick lives and how to address it.
-//   bricks            one brick per patch with a one-cell halo (Sec. 4), float32, x fastest,
+//   bricks            one brick per patch with a one- or two-cell halo (Sec. 4), x fastest,
 //                      in the layout of the chosen storage strategy.
 #pragma once
 #include <stddef.h>
@@ -53,9 +53,11 @@ struct alignas(16) DLeaf {
   int32_t patch;
   float vmin, vmax;      // range of every value a sample of this leaf can interpolate
   int32_t faces;         // bit 2a (+1): the level cell beyond the lower (upper) face on axis
-                         // a lies in the same patch and is not refined
+                         // a lies in the same patch and is not refined (one-cell halo), or
+                         // only in leaves of this leaf's level (two-cell halo): gradient
+                         // neighbours there read this leaf's brick
   int32_t sy, sz;        // brick strides (DPatch::sy, sz)
-  int32_t blo[3];        // brick: patch box lo (DPatch::lo)
+  int32_t blo[3];        // brick origin (DPatch::lo)
   int32_t dim[3];        // brick extent with halo (DPatch::dim)
 };
 static_assert(sizeof(DLeaf) == 96, "DLeaf is six 16-byte words");
@@ -70,8 +72,9 @@ struct DPatch {
                        // offset; texture table: cudaTextureObject_t; 3D atlas: unused
   long long gbase;     // the same for the gradient brick (float4 per cell), 0 if absent
   int32_t sy, sz;      // element strides of y and z (linear storages)
-  int32_t lo[3];       // patch box lo, level cells (brick index = cell - lo + 1)
-  int32_t dim[3];      // brick extent with halo: nx+2, ny+2, nz+2
+  int32_t lo[3];       // brick index = cell - lo + 1: the patch box lo, less one with a
+                       // two-cell halo (level cells)
+  int32_t dim[3];      // brick extent with halo: n + 2 (one-cell halo) or n + 4 per axis
   int32_t org[3];      // 3D atlas: texel origin of the brick
   int32_t pad[3];
 };
@@ -142,6 +145,7 @@ struct RenderArgs {
   float light_step, light_ambient;
   int32_t samples_per_iter;      // refill schedule: samples per lane between warp steps
   int32_t coarse_factor;         // learned mode 2: step multiplier below tau
+  int32_t learned_min_samples;   // learned modes: segments shorter than this skip the MLP
 };
 
 struct TraceArgs {

@@ -1,8 +1,10 @@
 // Bricks, halos and the packed atlas (Sec. 4 of Kaehler & Abel).
 //
 // One brick per patch (Sec. 4: fewer interfaces and less fragmentation than one brick per
-// kD node), holding the patch cells plus a one-cell halo so that trilinear interpolation
-// anywhere inside the patch box reads only its own brick.  A halo cell c of a level-l
+// kD node), holding the patch cells plus a halo of H = c->halo cells (one, or two so that
+// gradient neighbours up to one cell beyond a leaf face onto the same level also read the
+// brick) so that trilinear interpolation anywhere inside the patch box reads only its own
+// brick.  Brick index = cell - patch lo + H.  A halo cell c of a level-l
 // patch holds the level-l value V_l(c): c is first clamped into the domain; if some
 // level-l patch holds c, its stored value; otherwise the trilinear value, at the centre
 // of c, of the finest coarser level whose patch holds that centre.  This is the
@@ -81,7 +83,7 @@ amr_status build_bricks(amr_ctx* c) {
     BrickView bv;
     bv.v = c->bricks[p].data();
     for (int k = 0; k < 3; ++k) {
-      bv.d[k] = c->patches[p].n[k] + 2;
+      bv.d[k] = c->patches[p].n[k] + 2 * c->halo;
       bv.lo[k] = c->patches[p].box[k];
     }
     return bv;
@@ -93,7 +95,7 @@ amr_status build_bricks(amr_ctx* c) {
     int64_t i0[3];
     for (int a = 0; a < 3; ++a) {
       double hl = c->h0[a] / (double)c->rpow[lc];
-      double beta = (x[a] - c->dlo[a]) / hl + 0.5 - (double)bv.lo[a];
+      double beta = (x[a] - c->dlo[a]) / hl - 0.5 - (double)bv.lo[a] + (double)c->halo;
       double f = std::floor(beta);
       int64_t i = (int64_t)f;
       double wa = beta - f;
@@ -128,7 +130,8 @@ amr_status build_bricks(amr_ctx* c) {
     const Patch& pt = c->patches[p];
     const int l = pt.level;
     const int64_t sc = c->rpow[L - 1 - l];
-    const int64_t d0 = pt.n[0] + 2, d1 = pt.n[1] + 2, d2 = pt.n[2] + 2;
+    const int64_t H = c->halo;
+    const int64_t d0 = pt.n[0] + 2 * H, d1 = pt.n[1] + 2 * H, d2 = pt.n[2] + 2 * H;
     std::vector<float>& br = c->bricks[p];
     br.assign((size_t)(d0 * d1 * d2), 0.0f);
     int64_t rlo[3], rhi[3];
@@ -138,7 +141,7 @@ amr_status build_bricks(amr_ctx* c) {
     }
     // V_l at a cell outside the patch (halo): clamp, same-level patch, else coarse value
     auto halo_value = [&](int64_t bi, int64_t bj, int64_t bk, float* out) -> bool {
-      int64_t cc[3] = {pt.box[0] + bi - 1, pt.box[1] + bj - 1, pt.box[2] + bk - 1};
+      int64_t cc[3] = {pt.box[0] + bi - H, pt.box[1] + bj - H, pt.box[2] + bk - H};
       for (int a = 0; a < 3; ++a) cc[a] = std::min(std::max(cc[a], rlo[a]), rhi[a] - 1);
       int q = index[l].find(c->patches, cc[0], cc[1], cc[2]);
       if (q >= 0) {
@@ -164,14 +167,15 @@ amr_status build_bricks(amr_ctx* c) {
     for (int64_t bk = 0; bk < d2; ++bk)
       for (int64_t bj = 0; bj < d1; ++bj) {
         float* row = br.data() + (size_t)(d0 * (bj + d1 * bk));
-        bool interior_row = bj >= 1 && bj <= pt.n[1] && bk >= 1 && bk <= pt.n[2];
+        bool interior_row = bj >= H && bj < pt.n[1] + H && bk >= H && bk < pt.n[2] + H;
         if (interior_row) {
-          std::memcpy(row + 1, pt.data.data() + (size_t)(pt.n[0] * ((bj - 1) + pt.n[1] * (bk - 1))),
+          std::memcpy(row + H, pt.data.data() + (size_t)(pt.n[0] * ((bj - H) + pt.n[1] * (bk - H))),
                       sizeof(float) * (size_t)pt.n[0]);
-          if (!halo_value(0, bj, bk, row) || !halo_value(d0 - 1, bj, bk, row + d0 - 1)) {
+          for (int64_t e = 0; e < H; ++e)
+            if (!halo_value(e, bj, bk, row + e) || !halo_value(d0 - 1 - e, bj, bk, row + d0 - 1 - e)) {
 #pragma omp atomic write
-            uncovered = true;
-          }
+              uncovered = true;
+            }
         } else {
           for (int64_t bi = 0; bi < d0; ++bi)
             if (!halo_value(bi, bj, bk, row + bi)) {
@@ -202,9 +206,10 @@ amr_status build_bricks(amr_ctx* c) {
     BrickView bv = view(p);
     int64_t lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
-      // leaf extent in brick coordinates: beta = X - lo + 0.5 with X = finest / sc
-      double bmin = (double)box[a] / (double)sc - (double)pt.box[a] + 0.5;
-      double bmax = (double)box[3 + a] / (double)sc - (double)pt.box[a] + 0.5;
+      // leaf extent in brick coordinates: beta = X - lo + H - 0.5 with X = finest / sc
+      const double sh = (double)c->halo - 0.5;
+      double bmin = (double)box[a] / (double)sc - (double)pt.box[a] + sh;
+      double bmax = (double)box[3 + a] / (double)sc - (double)pt.box[a] + sh;
       lo[a] = std::max<int64_t>(0, (int64_t)std::floor(bmin));
       hi[a] = std::min<int64_t>(bv.d[a] - 1, (int64_t)std::floor(bmax) + 1);
     }
@@ -233,8 +238,9 @@ amr_status build_gradient_bricks(amr_ctx* c) {
 #pragma omp parallel for schedule(dynamic, 4)
   for (long long pi = 0; pi < (long long)P; ++pi) {
     const size_t p = (size_t)pi;
-    const int64_t d0 = c->patches[p].n[0] + 2, d1 = c->patches[p].n[1] + 2,
-                  d2 = c->patches[p].n[2] + 2;
+    const int64_t H = c->halo;
+    const int64_t d0 = c->patches[p].n[0] + 2 * H, d1 = c->patches[p].n[1] + 2 * H,
+                  d2 = c->patches[p].n[2] + 2 * H;
     const std::vector<float>& v = c->bricks[p];
     std::vector<float4>& g = c->gbricks[p];
     g.resize(v.size());
@@ -287,7 +293,7 @@ amr_status pack_atlas(amr_ctx* c) {
   std::vector<std::array<int64_t, 3>> ext(P);
   int64_t mx = 0;
   for (size_t p = 0; p < P; ++p) {
-    for (int a = 0; a < 3; ++a) ext[p][a] = c->patches[p].n[a] + 2;
+    for (int a = 0; a < 3; ++a) ext[p][a] = c->patches[p].n[a] + 2 * c->halo;
     mx = std::max(mx, std::max(ext[p][0], ext[p][1]));
   }
   std::vector<int> order(P);

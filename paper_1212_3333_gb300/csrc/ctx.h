@@ -96,6 +96,8 @@ struct amr_ctx {
   amr::Tree tree;
   std::vector<std::vector<float>> bricks;  // per patch, with halo
   bool want_gradient = false;              // build gradient bricks too
+  int halo = 1;                            // brick halo width in cells (1, or 2 with
+                                           // AMR_STORE_HALO2: faces onto the same level)
   std::vector<std::vector<float4>> gbricks; // per patch: value and central differences
   std::vector<float> leaf_vmin, leaf_vmax;
   amr::Packing packing;
@@ -105,7 +107,7 @@ struct amr_ctx {
   bool device_built = false;
   double build_seconds = 0.0;
   amr::DeviceState dev;
-  amr_batch_config batch_cfg = {16, 8, 1, 0};  // used when a batch call passes no config
+  amr_batch_config batch_cfg = {16, 8, 1, 0, 0};  // used when a batch call passes no config
   std::string err;
 };
 
@@ -143,5 +145,7 @@ amr_status prepare_render_args(amr_ctx* c, const amr_camera* cam, int32_t tf_n,
                                const amr_render_params* p, RenderArgs* a);
 amr_status launch_render_args(amr_ctx* c, const RenderArgs& a, const amr_render_params* p,
                               void* stream);
+// params with AMR_SCHEDULE_AUTO replaced by the schedule a single-view call would use
+amr_render_params resolve_render_schedule(const amr_camera* cam, const amr_render_params& p);
 
 }  // namespace amr

@@ -270,8 +270,9 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   for (size_t p = 0; p < P; ++p) {
     std::memset(&pt[p], 0, sizeof(DPatch));
     for (int a = 0; a < 3; ++a) {
-      pt[p].lo[a] = (int32_t)c->patches[p].box[a];
-      pt[p].dim[a] = (int32_t)(c->patches[p].n[a] + 2);
+      // brick index = cell - lo + 1 in every kernel: a halo of H cells shifts lo by H - 1
+      pt[p].lo[a] = (int32_t)(c->patches[p].box[a] - (c->halo - 1));
+      pt[p].dim[a] = (int32_t)(c->patches[p].n[a] + 2 * c->halo);
     }
   }
   if (fault_injected("oom")) return fail(c, AMR_ERR_OOM, "injected device allocation failure");

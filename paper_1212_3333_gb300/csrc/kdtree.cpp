@@ -139,6 +139,12 @@ class Builder {
     if (nodes_[i].axis < 0) return nodes_[i].patch == p;
     return same_patch(nodes_[i].left, q, p) && same_patch(nodes_[i].right, q, p);
   }
+  // every leaf overlapping box q is of level l
+  bool same_level(int i, const int64_t* q, int l) const {
+    if (!intersect(nodes_[i].box, q, nullptr)) return true;
+    if (nodes_[i].axis < 0) return nodes_[i].level == l;
+    return same_level(nodes_[i].left, q, l) && same_level(nodes_[i].right, q, l);
+  }
 
   static void offer(Candidate& best, int64_t cost, int64_t bal, int axis, int64_t s) {
     if (!best.valid || cost < best.cost || (cost == best.cost && bal < best.bal)) {
@@ -288,9 +294,9 @@ class Builder {
         t.right[k] = pre[b.right];
       }
     }
-    // same-patch faces: the slab of one level cell beyond a leaf face that lies inside the
-    // leaf's patch and overlaps only leaves of that patch (so gradient neighbours there read
-    // the leaf's own brick)
+    // face bits: the slab of one level cell beyond a leaf face lies inside the leaf's patch
+    // and overlaps only leaves of that patch (one-cell halo), or overlaps only leaves of the
+    // leaf's level (two-cell halo), so gradient neighbours there read the leaf's own brick
     t.leaf_faces.assign(t.leaf_patch.size(), 0);
     t.face_node.assign(12 * t.leaf_patch.size(), 0);
     std::vector<int> node2pre(n);
@@ -337,6 +343,15 @@ class Builder {
               }
             }
             t.face_node[12 * (size_t)t.leaf[k] + 6 * only_slab + 2 * a + side] = node2pre[i];
+          }
+          if (c_->halo >= 2) {
+            // two-cell halo: the slab may lie in any patch of the leaf's level (the brick's
+            // halo holds V_l there, and the stencils of points up to one cell beyond the
+            // face reach two cells beyond it); it must lie inside the root
+            if ((side == 0 && q[a] < c_->root[a]) || (side == 1 && q[3 + a] > c_->root[3 + a]))
+              continue;
+            if (same_level(0, q, b.level)) f |= (uint8_t)(1u << (2 * a + side));
+            continue;
           }
           if ((side == 0 && q[a] < pt.fbox[a]) || (side == 1 && q[3 + a] > pt.fbox[3 + a]))
             continue;

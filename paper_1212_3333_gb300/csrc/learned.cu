@@ -3,10 +3,11 @@
 //
 // learned_kernel works in rounds so that a warp is converged at segment boundaries: every
 // live lane descends to its ray's next segment, drops it if exact min/max skipping proves
-// it transparent, and stages its 12 features; the warp evaluates the MLP for all 32 lanes
-// on the tensor cores (mlp_forward_warp); a segment whose predicted opacity contribution is
-// below tau is skipped (mode 1) or sampled with a coarse_factor times coarser step (mode 2); otherwise it is
-// sampled exactly as the plain march samples it.
+// it transparent, and stages its 12 features; when some lane's segment has at least
+// learned_min_samples samples the warp evaluates the MLP for all 32 lanes on the tensor
+// cores (mlp_forward_warp); such a segment whose predicted opacity contribution is below tau
+// is skipped (mode 1) or sampled with a coarse_factor times coarser step (mode 2); every
+// other segment is sampled exactly as the plain march samples it.
 //
 // log_kernel is the plain march (no early termination) that records, per segment kept by a
 // seeded hash, the same 12 features and the target A_out - A_in = (1 - A_in) alpha_seg.
@@ -190,15 +191,17 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
         }
       }
     }
-    // stage the warp's features and evaluate the proposal on the tensor cores (only when
-    // some lane has a segment to decide)
-    if (__any_sync(0xffffffffu, n > 0)) {
+    // stage the warp's features and evaluate the proposal on the tensor cores, only when
+    // some lane has a segment long enough (learned_min_samples) for a skip or a coarser
+    // step to save more than the evaluation costs; shorter segments are sampled as is
+    const bool ask = n >= A.learned_min_samples;
+    if (__any_sync(0xffffffffu, ask)) {
 #pragma unroll
       for (int k = 0; k < kMlpInPad; ++k)
         xs[lane * kStride1 + k] = __float2bfloat16_rn(k < kMlpIn ? f[k] : 0.0f);
       __syncwarp();
       const float predicted = mlp_forward_warp(wsm, xs, ys, lane);
-      if (n > 0 && predicted < A.tau)
+      if (ask && predicted < A.tau)
         n = A.learned == 1 ? 0 : (n + A.coarse_factor - 1) / A.coarse_factor;
     }
     if (n > 0) {

@@ -468,6 +468,20 @@ __device__ __forceinline__ int locate_cell(const DNode* __restrict__ nodes, cons
   return -1;
 }
 
+// Point location from node `start` (which must hold the point), unpruned tree.
+__device__ __forceinline__ int locate_cell_from(const DNode* __restrict__ nodes, uint32_t start,
+                                                int f0, int f1, int f2) {
+  uint32_t i = start;
+  for (int depth = 0; depth < kMaxDepth; ++depth) {
+    const DNode nd = nodes[i];
+    const uint32_t ax = nd.meta >> 30;
+    const uint32_t idx = nd.meta & kIndexMask;
+    if (ax == kLeafAxis) return (int)idx;
+    i = idx + (sel3i(ax, f0, f1, f2) < nd.split ? 0u : 1u);
+  }
+  return -1;
+}
+
 // Brick of one patch as held in registers while a segment is sampled.
 struct BrickRef {
   long long base;  // pointer / element offset / texture object
@@ -1000,7 +1014,8 @@ __device__ __forceinline__ void leaf_bounds(const DLeaf& lf, const DLevel& lv, c
     leaf_lo[a] = lf.lo[a];
     bl[a] = (float)(lf.lo[a] - b.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
     bh[a] = (float)(lf.hi[a] - b.lo[a] * lv.sc) * lv.inv_sc + 0.5f;
-    // a same-patch face widens the region whose neighbours read this brick by one cell.
+    // a face bit (the far side is the same unrefined patch, or with a two-cell halo any
+    // patch of this level) widens the region whose neighbours read this brick by one cell.
     // Under pruning only when the bound is finer than this leaf's level: then no node the
     // pruned descent could stop at overlaps the (level-l) cells beyond the face
     if (lod_min > lf.level) {
@@ -1052,41 +1067,77 @@ __device__ __forceinline__ void setup_segment(const RenderArgs& A, const RayF& r
 // Sec. 5): transmittance of the part of the segment X -> light inside the root box, marched
 // with n = max(1, ceil(len / light_step)) midpoint samples of the AMR field (the finest
 // leaf holding each point, trilinear in its brick), stopping with 0 once T <= 1e-4.
-// X in finest-cell units.  Consecutive samples usually stay in one leaf, which is reused.
+// X in finest-cell units.  LightRay holds what both marchers below share.
+struct LightRay {
+  float X[3], D[3];  // start and light - start, finest-cell units
+  float s_out;       // the path inside the root ends at X + s_out D
+  float delta;       // world length of one light step
+  int n;             // light samples
+};
+
+__device__ __forceinline__ LightRay light_ray(const RenderArgs& A, const RayArgs& R, float x0,
+                                              float x1, float x2) {
+  LightRay L;
+  L.X[0] = x0;
+  L.X[1] = x1;
+  L.X[2] = x2;
+  float s_out = 1.0f, len2 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    L.D[a] = A.light_f[a] - L.X[a];
+    if (L.D[a] != 0.0f) {
+      const float bound = (float)(L.D[a] > 0.0f ? R.root_f[3 + a] : R.root_f[a]);
+      s_out = fminf(s_out, (bound - L.X[a]) / L.D[a]);
+    }
+    const float w = L.D[a] * (float)R.hf[a];
+    len2 = fmaf(w, w, len2);
+  }
+  L.s_out = fmaxf(s_out, 0.0f);
+  const float len = L.s_out * sqrtf(len2);
+  L.n = (int)fminf(fmaxf(ceilf(len / A.light_step), 1.0f), 65536.0f);
+  L.delta = len / (float)L.n;
+  return L;
+}
+
+// Point k of the light ray (finest-cell units) and its finest cell, clamped into the root.
+__device__ __forceinline__ void light_point(const RayArgs& R, const LightRay& L, int k, float* P,
+                                            int* f) {
+  const float sk = ((float)k + 0.5f) / (float)L.n * L.s_out;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    P[a] = fmaf(sk, L.D[a], L.X[a]);
+    f[a] = min(max((int)floorf(P[a]), R.root_f[a]), R.root_f[3 + a] - 1);
+  }
+}
+
+// The prefix counts of the transfer function's non-transparent entries, which the frame
+// kernels stage right after the transfer function in shared memory (stage_tf).
+__device__ __forceinline__ const int* tf_nonzero_prefix(const RenderArgs& A, const float4* s_tf) {
+  return reinterpret_cast<const int*>(s_tf + A.tf_n);
+}
+
+// Light samples in a leaf whose value range the transfer function maps to zero opacity
+// multiply T by exp(-kappa * 0 * delta) = 1 exactly, so both marchers skip them: the same
+// T bit for bit, without their stencils.
+
+// One lane marches the whole light ray, sample by sample (the per-ray schedule).
+// Consecutive samples usually stay in one leaf, which is reused.
 template <int ST>
 __device__ __noinline__ float shadow_transmittance(const RenderArgs& A, const RayArgs& R,
                                                    const float4* s_tf, float x0, float x1,
                                                    float x2) {
-  const float X[3] = {x0, x1, x2};
-  float D[3], s_out = 1.0f, len2 = 0.0f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    D[a] = A.light_f[a] - X[a];
-    if (D[a] != 0.0f) {
-      const float bound = (float)(D[a] > 0.0f ? R.root_f[3 + a] : R.root_f[a]);
-      s_out = fminf(s_out, (bound - X[a]) / D[a]);
-    }
-    const float w = D[a] * (float)R.hf[a];
-    len2 = fmaf(w, w, len2);
-  }
-  s_out = fmaxf(s_out, 0.0f);
-  const float len = s_out * sqrtf(len2);
-  const int n = (int)fminf(fmaxf(ceilf(len / A.light_step), 1.0f), 65536.0f);
-  const float delta = len / (float)n;
+  const LightRay L = light_ray(A, R, x0, x1, x2);
+  const int* s_nz = tf_nonzero_prefix(A, s_tf);
   float T = 1.0f;
   int leaf = -1;
   DLeaf lf;
   BrickRef b;
   float inv_sc = 1.0f;
-  for (int k = 0; k < n; ++k) {
-    const float sk = ((float)k + 0.5f) / (float)n * s_out;
+  bool clear = false;  // the current leaf is fully transparent
+  for (int k = 0; k < L.n; ++k) {
     float P[3];
     int f[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      P[a] = fmaf(sk, D[a], X[a]);
-      f[a] = min(max((int)floorf(P[a]), R.root_f[a]), R.root_f[3 + a] - 1);
-    }
+    light_point(R, L, k, P, f);
     const bool inside = leaf >= 0 && f[0] >= lf.lo[0] && f[0] < lf.hi[0] && f[1] >= lf.lo[1] &&
                         f[1] < lf.hi[1] && f[2] >= lf.lo[2] && f[2] < lf.hi[2];
     if (!inside) {
@@ -1095,13 +1146,92 @@ __device__ __noinline__ float shadow_transmittance(const RenderArgs& A, const Ra
       lf = A.leaves[leaf];
       b = leaf_brick(A.patches, lf);
       inv_sc = A.lv[lf.level].inv_sc;
+      clear = tf_transparent(s_nz, A.tf_n, lf.vmin, lf.vmax, A.vmin, A.inv_range);
     }
+    if (clear) continue;
     const float v = trilinear<ST>(A, b, fmaf(P[0], inv_sc, 0.5f - (float)b.lo[0]),
                                   fmaf(P[1], inv_sc, 0.5f - (float)b.lo[1]),
                                   fmaf(P[2], inv_sc, 0.5f - (float)b.lo[2]));
     const float a_tf = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range).w;
-    T *= expf(-A.kappa * a_tf * delta);
+    T *= expf(-A.kappa * a_tf * L.delta);
     if (T <= 1e-4f) return 0.0f;
+  }
+  return T;
+}
+
+// The same transmittance, marched by all 32 lanes of a warp together (the deferred
+// schedule; every lane must call it with the same start point).  Round r takes the 32
+// consecutive samples 32 r .. 32 r + 31, one per lane: neighbouring lanes read
+// neighbouring cells.  A lane keeps the leaf of its last point, tries the leaf of the last
+// point of the previous round next, and otherwise locates its point from the root; the
+// lanes that need it descend together, so a round pays one descent's latency however
+// many leaves its points span.  The round's factors exp(-kappa a delta) are multiplied in
+// a fixed tree order into T, so T is the same in every lane and differs from the per-lane
+// product only by rounding; T <= 1e-4 after a round gives 0 (T only falls, so this is the
+// per-sample rule).
+template <int ST>
+__device__ __forceinline__ float warp_shadow_transmittance(const RenderArgs& A, const RayArgs& R,
+                                                           const float4* s_tf, float x0,
+                                                           float x1, float x2) {
+  const unsigned FULL = 0xffffffffu;
+  const LightRay L = light_ray(A, R, x0, x1, x2);
+  const int* s_nz = tf_nonzero_prefix(A, s_tf);
+  float T = 1.0f;
+  int leaf = -1;                 // this lane's current leaf
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  BrickRef b;
+  float inv_sc = 1.0f;
+  bool clear = false;            // this lane's leaf is fully transparent
+  int last = -1;                 // warp-uniform: the leaf of the last sample of the last round
+  bool bad = false;              // malformed tree met
+  for (int k0 = 0; k0 < L.n; k0 += 32) {
+    const int k = k0 + (int)(threadIdx.x + blockDim.x * threadIdx.y) % 32;
+    const bool valid = k < L.n;
+    float P[3];
+    int f[3];
+    light_point(R, L, valid ? k : L.n - 1, P, f);
+    bool have = valid && leaf >= 0 && f[0] >= lo[0] && f[0] < hi[0] && f[1] >= lo[1] &&
+                f[1] < hi[1] && f[2] >= lo[2] && f[2] < hi[2];
+    if (valid && !have) {
+      int lid = -1;
+      if (last >= 0) {
+        const int4* w = reinterpret_cast<const int4*>(A.leaves + last);
+        const int4 w1 = __ldg(w + 1), w2 = __ldg(w + 2);  // lo[3], hi[0] | hi[1], hi[2], ...
+        if (f[0] >= w1.x && f[0] < w1.w && f[1] >= w1.y && f[1] < w2.x && f[2] >= w1.z &&
+            f[2] < w2.y)
+          lid = last;
+      }
+      if (lid < 0) lid = locate_cell_from(A.nodes, 0u, f[0], f[1], f[2]);
+      if (lid < 0) {
+        bad = true;
+      } else {
+        const DLeaf lf = A.leaves[lid];
+        leaf = lid;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = lf.lo[a];
+          hi[a] = lf.hi[a];
+        }
+        b = leaf_brick(A.patches, lf);
+        inv_sc = A.lv[lf.level].inv_sc;
+        clear = tf_transparent(s_nz, A.tf_n, lf.vmin, lf.vmax, A.vmin, A.inv_range);
+        have = true;
+      }
+    }
+    if (__any_sync(FULL, bad)) return T;  // malformed tree: the per-lane march stops too
+    float term = 1.0f;
+    if (valid && !clear) {
+      const float v = trilinear<ST>(A, b, fmaf(P[0], inv_sc, 0.5f - (float)b.lo[0]),
+                                    fmaf(P[1], inv_sc, 0.5f - (float)b.lo[1]),
+                                    fmaf(P[2], inv_sc, 0.5f - (float)b.lo[2]));
+      const float a_tf = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range).w;
+      term = expf(-A.kappa * a_tf * L.delta);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) term *= __shfl_down_sync(FULL, term, off);
+    T *= __shfl_sync(FULL, term, 0);
+    if (T <= 1e-4f) return 0.0f;
+    last = __shfl_sync(FULL, leaf, 31);
   }
   return T;
 }

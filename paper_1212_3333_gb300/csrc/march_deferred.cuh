@@ -10,11 +10,13 @@
 //            function, opacity and the accumulated alpha (so early ray termination is
 //            decided at once); an opaque sample is queued with what its shading needs;
 //   shade  - once 32 samples are queued (and at the end), each lane shades one of them
-//            (gradient, Phong) and every lane then adds its own samples' colours in sample
-//            order.
+//            (gradient, Phong; with secondary rays the warp first marches each queued
+//            sample's light ray together) and every lane then adds its own samples'
+//            colours in sample order.
 // The colour sum of a pixel sees the same terms in the same order as in the per-ray loop,
 // so the image is bit-identical to it; only the moments at which the sums are taken
-// change.
+// change.  (With secondary rays each light ray's transmittance is a product taken in
+// another order - 32 samples per round - so those images agree to rounding, not bits.)
 #pragma once
 #include "march.cuh"
 
@@ -37,6 +39,7 @@ struct ShadeTask {
 struct DeferArea {
   ShadeTask task[32];
   float3 col[32];
+  float T[32];    // secondary rays: transmittance from each task's sample to the light
 };
 
 // resident blocks per SM the register budget allows for (measured on C2, Phong, 2048^2 /
@@ -45,10 +48,20 @@ struct DeferArea {
 #define AMR_MIN_BLOCKS_DEFERRED 3
 #endif
 
-// Colour of queued sample t (what composite_sample computes for an opaque sample).
-template <int ST, int GB>
+// The sample of task t in finest-cell units (as composite_sample computes it).
+__device__ __forceinline__ float3 task_point(const RenderArgs& A, const ShadeTask& t) {
+  const DLeaf& lf = A.leaves[leaf_of(t.leaf)];
+  const float sc = (float)A.lv[lf.level].sc;
+  return make_float3((t.beta[0] - 0.5f + (float)lf.blo[0]) * sc,
+                     (t.beta[1] - 0.5f + (float)lf.blo[1]) * sc,
+                     (t.beta[2] - 0.5f + (float)lf.blo[2]) * sc);
+}
+
+// Colour of queued sample t (what composite_sample computes for an opaque sample); T is
+// its transmittance to the light when SHADOW is set.
+template <int ST, int GB, bool SHADOW = false>
 __device__ __forceinline__ float3 shade_task(const RenderArgs& A, const RayArgs& R,
-                                             const ShadeTask& t) {
+                                             const ShadeTask& t, float T = 1.0f) {
   const DLeaf lf = A.leaves[leaf_of(t.leaf)];
   const DLevel& lv = A.lv[lf.level];
   SegState s;
@@ -67,6 +80,12 @@ __device__ __forceinline__ float3 shade_task(const RenderArgs& A, const RayArgs&
   gradient<ST, 1, GB>(A, R, s, beta, t.k, lv, gr);
   float cr = t.cr, cg = t.cg, cb = t.cb;
   phong(A, lv, gr, t.Lx, t.Ly, t.Lz, cr, cg, cb);
+  if constexpr (SHADOW) {
+    const float I = fmaf(1.0f - A.light_ambient, T, A.light_ambient);
+    cr *= I;
+    cg *= I;
+    cb *= I;
+  }
   return make_float3(cr, cg, cb);
 }
 
@@ -105,10 +124,21 @@ __device__ __forceinline__ float4 march_deferred(const RenderArgs& A, const RayA
   int queued = 0;      // warp-uniform: tasks in the queue
   unsigned mine = 0;   // this lane's queue slots
 
-  // shade every queued task (one per lane), then each lane adds its own colours in order
+  // shade every queued task (one per lane), then each lane adds its own colours in order;
+  // with secondary rays the whole warp first marches each task's light ray together
   auto drain = [&]() {
     __syncwarp();
-    if (lane < queued) Q.col[lane] = shade_task<ST, (SHADE & 3) == 2>(A, R, Q.task[lane]);
+    if constexpr ((SHADE & kShadeShadow) != 0) {
+      for (int q = 0; q < queued; ++q) {
+        const float3 x = task_point(A, Q.task[q]);
+        const float T = warp_shadow_transmittance<ST>(A, R, s_tf, x.x, x.y, x.z);
+        if (lane == 0) Q.T[q] = T;
+      }
+      __syncwarp();
+    }
+    if (lane < queued)
+      Q.col[lane] = shade_task<ST, (SHADE & 3) == 2, (SHADE & kShadeShadow) != 0>(
+          A, R, Q.task[lane], Q.T[lane]);
     __syncwarp();
     for (unsigned m = mine; m != 0; m &= m - 1) {
       const int q = __ffs(m) - 1;

@@ -69,15 +69,24 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
   if (grid.x == 0 || grid.y == 0) return AMR_OK;
   cudaError_t e;
   if (shade & kShadeShadow) {
-    // secondary rays to the point light: per-ray schedule, trilinear, FP32 linear storages
+    // secondary rays to the point light: per-ray schedule (a lane marches its samples'
+    // light rays) or deferred shading (the warp marches each queued sample's light ray
+    // together); trilinear, FP32 linear storages
     if constexpr (ST == ST_PTR || ST == ST_ATLAS_LINEAR) {
-      if (interp != 1 || schedule != 0)
-        return fail(c, AMR_ERR_ARG, "secondary rays render trilinear with schedule 0");
-      const size_t smem = tf_bytes;
       const int base = shade & 3;
-      if (base == 0) e = launch_tiles(march_kernel<ST, 1, kShadeShadow>, smem, s, a);
-      else if (base == 1) e = launch_tiles(march_kernel<ST, 1, 1 | kShadeShadow>, smem, s, a);
-      else e = launch_tiles(march_kernel<ST, 1, 2 | kShadeShadow>, smem, s, a);
+      if (interp != 1 || (schedule != 0 && schedule != 3) || (schedule == 3 && base == 0))
+        return fail(c, AMR_ERR_ARG,
+                    "secondary rays render trilinear with schedule 0, or 3 with shade = 1");
+      if (schedule == 3) {
+        const size_t smem = ((tf_bytes + 15) & ~(size_t)15) + 4 * sizeof(DeferArea);
+        if (base == 1) e = launch_tiles(deferred_kernel<ST, 1 | kShadeShadow>, smem, s, a);
+        else e = launch_tiles(deferred_kernel<ST, 2 | kShadeShadow>, smem, s, a);
+      } else {
+        const size_t smem = tf_bytes;
+        if (base == 0) e = launch_tiles(march_kernel<ST, 1, kShadeShadow>, smem, s, a);
+        else if (base == 1) e = launch_tiles(march_kernel<ST, 1, 1 | kShadeShadow>, smem, s, a);
+        else e = launch_tiles(march_kernel<ST, 1, 2 | kShadeShadow>, smem, s, a);
+      }
     } else {
       return fail(c, AMR_ERR_ARG, "secondary rays need the ptr or atlas_linear storage, FP32 cells");
     }

@@ -74,13 +74,16 @@ using namespace amr;
 
 extern "C" amr_status amr_render_host_noalloc(amr_ctx* c, const amr_camera* cam,
                                               const float* tf_rgba_host, int32_t tf_n,
-                                              const amr_render_params* params,
+                                              const amr_render_params* params_in,
                                               float* out_rgba_host, void* cuda_stream,
                                               uint64_t* samples_out) {
   if (!c) return AMR_ERR_ARG;
   if (!c->device_built) return fail(c, AMR_ERR_STATE, "render before amr_build_kdtree");
-  if (!cam || !params || !tf_rgba_host || !out_rgba_host)
+  if (!cam || !params_in || !tf_rgba_host || !out_rgba_host)
     return fail(c, AMR_ERR_ARG, "NULL argument");
+  // the schedule follows the whole frame, not the bands it is rendered in
+  const amr_render_params resolved = resolve_render_schedule(cam, *params_in);
+  const amr_render_params* params = &resolved;
   if (tf_n < 2 || (size_t)tf_n > kTfMax)
     return fail(c, AMR_ERR_ARG, "tf_n must be in [2, 2048] (the no-alloc staging limit)");
   if (cam->width <= 0 || (size_t)cam->width * sizeof(float4) * kTileRows > kBandBytes)

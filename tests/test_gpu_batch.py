@@ -110,11 +110,22 @@ def test_batch_graph_replay_and_autotune(amr, c1):
     p, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1)
     views, offsets, total = amr.make_views(cams, tfi)
     out = torch.zeros((total,), device="cuda")
+    # the default schedule (AMR_SCHEDULE_AUTO) renders Phong batches with deferred shading,
+    # so the autotuner also searches samples per iteration on the best tile
     best, ms = ctx.amr_batch_autotune(views, tfs, p, out, reps=2)
-    assert len(ms) == 9 and all(m > 0 for m in ms)
+    assert len(ms) == 13 and all(m > 0 for m in ms)
     assert (best.tile_w, best.tile_h) in SHAPES and best.rays_per_thread in (1, 2, 4)
-    k = SHAPES.index((best.tile_w, best.tile_h)) * 3 + (1, 2, 4).index(best.rays_per_thread)
-    assert ms[k] == min(ms)
+    k = int(np.argmin(ms))
+    if k < 9:
+        assert best.samples_per_iter == 0
+        assert k == SHAPES.index((best.tile_w, best.tile_h)) * 3 + (1, 2, 4).index(best.rays_per_thread)
+    else:
+        assert best.samples_per_iter == (4, 8, 16, 32)[k - 9]
+    # the per-ray schedule has no samples-per-iteration knob
+    p0, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1, schedule=0)
+    _, ms0 = ctx.amr_batch_autotune(views, tfs, p0, out, reps=1)
+    assert all(m > 0 for m in ms0[:9]) and all(m == -1.0 for m in ms0[9:])
+    ctx.amr_batch_autotune(views, tfs, p, out, reps=2)  # keep the deferred choice
     n_ref = ctx.amr_render_batch(views, tfs, p, out, count_samples=True)  # autotuned config
     ref = out.clone()
     s = torch.cuda.Stream()
@@ -165,6 +176,7 @@ def test_batch_rejects_malformed_batches(amr, c1):
     rejects(v=v4)
     rejects(cfg=amr.batch_config(32, 8, 1))           # unsupported tile
     rejects(cfg=amr.batch_config(16, 8, 0))
+    rejects(cfg=amr.batch_config(16, 8, 1, 0, 65))    # samples per iteration beyond 64
     big, _, tot = amr.make_views([cams[0]] * 129, [0] * 129)
     rejects(v=big, o=torch.zeros((tot,), device="cuda"))
     p2, _ = params_pair(amr, w["vmin"], w["vmax"], row0=3)

@@ -151,8 +151,8 @@ def test_learned_render_with_zero_threshold_is_the_plain_march(mods, c1_learned)
             pl, _ = params_pair(amr, w["vmin"], w["vmax"], shade=shade, learned=mode, tau=0.0)
             img, n = gpu_render(ctx, w["camera"], w["tf"], pl)
             assert np.array_equal(img, plain) and n == n_plain
-    # a threshold above every prediction skips everything
-    pl, _ = params_pair(amr, w["vmin"], w["vmax"], learned=1, tau=1.5)
+    # a threshold above every prediction skips everything (every segment asks the MLP)
+    pl, _ = params_pair(amr, w["vmin"], w["vmax"], learned=1, tau=1.5, learned_min_samples=1)
     img, n = gpu_render(ctx, w["camera"], w["tf"], pl)
     assert n == 0 and np.all(img == 0)
 
@@ -201,7 +201,7 @@ def test_coarse_factor_scales_the_sample_count(mods, c1_learned):
     for cf in (2, 4, 16):
         # tau above every prediction: every segment is sampled coarsely
         pl, _ = params_pair(amr, w["vmin"], w["vmax"], ert_eps=0.0, learned=2, tau=1.5,
-                            coarse_factor=cf)
+                            coarse_factor=cf, learned_min_samples=1)
         img, n = gpu_render(ctx, w["camera"], w["tf"], pl)
         assert np.all(np.isfinite(img))
         counts.append(n)
@@ -232,3 +232,27 @@ def test_checkpoint_resume_continues_training(mods, tmp_path):
     # (gradients are summed with atomics, so the last bits may differ between runs)
     for u, w in ((a.params, b.params), (a.m, b.m), (a.v, b.v)):
         torch.testing.assert_close(u, w, rtol=1e-5, atol=1e-8)
+
+
+def test_learned_min_samples_limits_the_proposal(mods, c1_learned):
+    # segments shorter than learned_min_samples are sampled as the plain march samples
+    # them: with tau above every prediction, only the longer segments are skipped
+    torch, amr, proposal = mods
+    from paper_1212_3333_gb300 import _lib
+
+    w, ctx = c1_learned
+    proposal.Proposal(seed=7).install(ctx)
+    p, _ = params_pair(amr, w["vmin"], w["vmax"], ert_eps=0.0)
+    _, n_plain = gpu_render(ctx, w["camera"], w["tf"], p)
+    kept = []
+    for m in (1, 4, 16, 1 << 22):
+        pl, _ = params_pair(amr, w["vmin"], w["vmax"], ert_eps=0.0, learned=1, tau=1.5,
+                            learned_min_samples=m)
+        _, n = gpu_render(ctx, w["camera"], w["tf"], pl)
+        kept.append(n)
+    assert kept[0] == 0 and kept[0] < kept[1] < kept[2] <= kept[3] == n_plain
+    for m in (0, (1 << 22) + 1):
+        pl, _ = params_pair(amr, w["vmin"], w["vmax"], learned=1, learned_min_samples=m)
+        with pytest.raises(amr.AmrError) as e:
+            gpu_render(ctx, w["camera"], w["tf"], pl)
+        assert e.value.status == _lib.AMR_ERR_ARG

@@ -65,26 +65,29 @@ def test_tree_matches_oracle_ratio3():
     _tree_equal(h)
 
 
+@pytest.mark.parametrize("halo", [1, 2])
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
-def test_halo_equals_level_value(seed):
-    """Every brick cell (interior and one-cell halo) equals the level value V_l of the
-    cell it stands for, rounded to float32 (the product reads coarse values from coarse
-    bricks that are already rounded, so a few ulps may separate them)."""
+def test_halo_equals_level_value(seed, halo):
+    """Every brick cell (interior and the one- or two-cell halo) equals the level value
+    V_l of the cell it stands for, rounded to float32 (the product reads coarse values from
+    coarse bricks that are already rounded, so a few ulps may separate them)."""
     h = random_hierarchy(seed, n0=8, num_levels=3, patches_per_level=5, max_size=9, tiles=3)
     ctx = amr.from_hierarchy(h)
-    ctx.amr_build_host("ptr")
+    ctx.amr_build_host("ptr", halo=halo)
     o = oracle.Oracle(h)
     worst = 0.0
+    H = halo
     for p in range(h.num_patches):
         b = h.patch_box[p]
         l = int(h.patch_level[p])
         n = b[3:] - b[:3]
-        br = ctx.amr_get_brick(p).reshape(n[2] + 2, n[1] + 2, n[0] + 2)
-        for k in range(n[2] + 2):
-            for j in range(n[1] + 2):
-                for i in range(n[0] + 2):
-                    interior = 1 <= i <= n[0] and 1 <= j <= n[1] and 1 <= k <= n[2]
-                    v = o.V(l, b[0] + i - 1, b[1] + j - 1, b[2] + k - 1)
+        br = ctx.amr_get_brick(p).reshape(n[2] + 2 * H, n[1] + 2 * H, n[0] + 2 * H)
+        for k in range(n[2] + 2 * H):
+            for j in range(n[1] + 2 * H):
+                for i in range(n[0] + 2 * H):
+                    interior = (H <= i < n[0] + H and H <= j < n[1] + H and
+                                H <= k < n[2] + H)
+                    v = o.V(l, b[0] + i - H, b[1] + j - H, b[2] + k - H)
                     if interior:
                         assert br[k, j, i] == np.float32(v)
                     else:
@@ -103,18 +106,19 @@ def test_atlas_packing_is_valid():
     assert 0.0 < st.atlas_efficiency <= st.atlas_efficiency_halo <= 1.0
 
 
+@pytest.mark.parametrize("halo", [1, 2])
 @pytest.mark.parametrize("seed", [3, 5])
-def test_brick_bytes_and_packing_efficiency_follow_their_definitions(seed):
+def test_brick_bytes_and_packing_efficiency_follow_their_definitions(seed, halo):
     """Memory statistics (the quantities of the paper's Table 2): one FP32 value per cell,
-    bricks carrying a one-cell halo (Sec. 4), packing efficiency = data cells / atlas cells
-    (Sec. 4.1), with and without the halos."""
+    bricks carrying a one-cell halo (Sec. 4; two with AMR_STORE_HALO2), packing efficiency =
+    data cells / atlas cells (Sec. 4.1), with and without the halos."""
     h = random_hierarchy(seed, n0=8, num_levels=3, patches_per_level=8, max_size=12, tiles=5)
     n = (h.patch_box[:, 3:] - h.patch_box[:, :3]).astype(np.int64)
     cells = int(np.prod(n, axis=1).sum())
-    halo_cells = int(np.prod(n + 2, axis=1).sum())
+    halo_cells = int(np.prod(n + 2 * halo, axis=1).sum())
     for storage in ("ptr", "atlas_linear"):
         ctx = amr.from_hierarchy(h)
-        ctx.amr_build_host(storage)
+        ctx.amr_build_host(storage, halo=halo)
         st = ctx.amr_get_stats()
         assert st.num_patches == h.num_patches
         assert st.num_cells == cells

@@ -62,11 +62,15 @@ def test_type_a_nodes_match_oracle(name, make):
     np.testing.assert_array_equal(box, nb[want])
 
 
+@pytest.mark.parametrize("halo", [1, 2])
 @pytest.mark.parametrize("name,make", HIERS)
-def test_leaf_faces_by_brute_force(name, make):
+def test_leaf_faces_by_brute_force(name, make, halo):
+    # a face bit: with a one-cell halo, the slab of one level cell beyond the face lies in
+    # the leaf's patch and overlaps only that patch's leaves; with a two-cell halo, the
+    # slab lies in the root and overlaps only leaves of the leaf's level
     h = make()
     ctx = amr.from_hierarchy(h)
-    ctx.amr_build_host("ptr")
+    ctx.amr_build_host("ptr", halo=halo)
     o = oracle.Oracle(h)
     lbox, lpatch, llevel = o.leaves()
     axis, split, left, right, leaf = o.nodes()
@@ -87,8 +91,12 @@ def test_leaf_faces_by_brute_force(name, make):
                 else:
                     q[a], q[3 + a] = b[3 + a], b[3 + a] + sc
                 inside_patch = q[a] >= fbox[a] and q[3 + a] <= fbox[3 + a]
+                inside_root = q[a] >= root[a] and q[3 + a] <= root[3 + a]
                 over = np.all((lbox[:, :3] < q[3:]) & (lbox[:, 3:] > q[:3]), axis=1)
-                want = bool(inside_patch and np.all(lpatch[over] == lpatch[m]))
+                if halo == 1:
+                    want = bool(inside_patch and np.all(lpatch[over] == lpatch[m]))
+                else:
+                    want = bool(inside_root and np.all(llevel[over] == llevel[m]))
                 assert bool((faces[m] >> (2 * a + side)) & 1) == want, (name, m, a, side)
                 for only, k in ((0, fnode[m, 2 * a + side]), (1, fnode[m, 6 + 2 * a + side])):
                     u = q.copy() if only else np.concatenate(
@@ -101,3 +109,16 @@ def test_leaf_faces_by_brute_force(name, make):
                     if axis[k] >= 0:  # deepest: no child holds it
                         assert not _contains(nb[left[k]], u) and not _contains(nb[right[k]], u)
     assert faces.any()
+
+
+@pytest.mark.parametrize("name,make", HIERS)
+def test_same_level_faces_cover_the_same_patch_faces(name, make):
+    # a face onto the same unrefined patch is a face onto the same level
+    h = make()
+    c1c, c2c = amr.from_hierarchy(h), amr.from_hierarchy(h)
+    c1c.amr_build_host("ptr")
+    c2c.amr_build_host("ptr", halo=2)
+    f1, n1 = c1c.amr_get_leaf_faces()
+    f2, n2 = c2c.amr_get_leaf_faces()
+    assert np.all((f1 & f2) == f1)
+    np.testing.assert_array_equal(n1, n2)  # the lookup starts do not depend on the halo
