@@ -45,9 +45,13 @@ def _peaks():
 
 
 def _march_sha() -> str:
+    """sha1 (12 hex digits) of the sources the frame kernels compile from: every
+    march*.cuh header, amr_device.h and storage16.h."""
     h = hashlib.sha1()
-    for f in ("march.cuh", "march_launch.cuh", "amr_device.h"):
-        with open(os.path.join(ROOT, "paper_1212_3333_gb300", "csrc", f), "rb") as fh:
+    d = os.path.join(ROOT, "paper_1212_3333_gb300", "csrc")
+    names = sorted(f for f in os.listdir(d) if f.startswith("march") and f.endswith(".cuh"))
+    for f in names + ["amr_device.h", "storage16.h"]:
+        with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
@@ -56,23 +60,43 @@ def _variant(storage: str, gradient: bool, dtype: str) -> str:
     return f"{storage}{'+grad' if gradient else ''}/{dtype}"
 
 
-def _profiled_traffic(shade: int, variant: str, size: int):
-    """dram bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "march_c2_traffic.md")
-    if not os.path.exists(path):
+def _profiled_counters(shade: int, variant: str, size: int, schedule: int):
+    """ncu counters of the frame kernel from the committed summary
+    (profiles/march_counters.json), if they were taken on the current kernel sources;
+    else None.  One entry per (sources hash, variant, shade, size, schedule)."""
+    path = os.path.join(ROOT, "profiles", "march_counters.json")
+    try:
+        with open(path) as f:
+            entries = json.load(f)["entries"]
+    except Exception:
         return None
     sha = _march_sha()
-    for line in open(path):
-        parts = line.strip().split("|")
-        parts = [p.strip() for p in parts if p.strip()]
-        if (len(parts) >= 5 and parts[0] == sha and parts[1] == variant and parts[2] == str(shade)
-                and parts[3] == str(size)):
-            try:
-                return float(parts[4])
-            except ValueError:
-                return None
+    for e in entries:
+        if (e.get("sources") == sha and e.get("variant") == variant and e.get("shade") == shade
+                and e.get("size") == size and e.get("schedule", 0) == schedule):
+            return e
     return None
+
+
+def _l1_peak_gbs(sm_mhz):
+    """L1 data throughput of the whole chip at the SM clock sampled during the timed region:
+    ncu's peak rate of L1 data-pipe wavefronts per cycle over all SMs (a property of the
+    chip, recorded in the counters summary) times the 128 bytes one wavefront moves;
+    without that figure, the nominal 128 B per cycle per SM."""
+    import torch
+
+    per_clk, kind = None, None
+    try:
+        with open(os.path.join(ROOT, "profiles", "march_counters.json")) as f:
+            per_clk = 128.0 * float(json.load(f)["l1_lsu_wavefronts_peak_per_cycle"])
+            kind = ("ncu l1tex__data_pipe_lsu_wavefronts.sum.peak_sustained x 128 B x median "
+                    "SM clock under load")
+    except Exception:
+        pass
+    if per_clk is None:
+        per_clk = 128.0 * torch.cuda.get_device_properties(0).multi_processor_count
+        kind = "nominal 128 B/clk/SM x SMs x median SM clock under load"
+    return per_clk * (sm_mhz or 2070.0) * 1e6 / 1e9, kind
 
 
 class ClockSampler:
@@ -182,12 +206,12 @@ def cpu_baseline(hier, cam, tf, vmin, vmax, shade, budget_s=15.0, seed=0):
                       f"({total_samples} samples, {total_s:.1f} s), FP64 oracle, {threads} threads"}
 
 
-def learned_eval(amr, ctx, hier, vmin, vmax, tf, args, taus=(1e-4, 3e-4, 1e-3, 3e-3, 1e-2)):
+def learned_eval(amr, ctx, hier, vmin, vmax, tf, args, taus=(1e-4, 1e-3, 1e-2)):
     """Learned segment proposal on the same hierarchy: log segments from 256 seeded poses
     (seeds 1000-1255), train the MLP with the library's kernels, then time held-out views
     (seeds 2000-2007) at the bench size: plain march, exact min/max skipping, and min/max +
-    learned skipping (and 4x / 16x / 64x coarser sampling) for each tau, PSNR against the
-    plain march."""
+    learned skipping (and 16x / 64x coarser sampling) for each tau and each minimum segment
+    length the proposal is asked about, PSNR against the plain march."""
     import torch
 
     import synth
@@ -221,11 +245,15 @@ def learned_eval(amr, ctx, hier, vmin, vmax, tf, args, taus=(1e-4, 3e-4, 1e-3, 3
 
     base = dict(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
     configs = {"plain": {}, "minmax": {"skip": 1}}
-    for tau in taus:
-        configs[f"skip@{tau:g}"] = {"skip": 1, "learned": 1, "tau": tau}
-        for cf in (4, 16, 64):
-            configs[f"coarse{cf}@{tau:g}"] = {"skip": 1, "learned": 2, "tau": tau,
-                                              "coarse_factor": cf}
+    # the proposal is asked about segments of at least m samples (m1: every segment)
+    for m in (1, 8, 32):
+        for tau in taus:
+            configs[f"skip@{tau:g}/m{m}"] = {"skip": 1, "learned": 1, "tau": tau,
+                                             "learned_min_samples": m}
+            for cf in (16, 64):
+                configs[f"coarse{cf}@{tau:g}/m{m}"] = {"skip": 1, "learned": 2, "tau": tau,
+                                                       "coarse_factor": cf,
+                                                       "learned_min_samples": m}
     res = {k: {"ms": 0.0, "psnr_min": float("inf"), "samples": 0} for k in configs}
     views = [synth.orbit_camera(2000 + s, size, size) for s in range(args.heldout)]
     for cam in views:
@@ -331,7 +359,10 @@ def lod_eval(amr, ctx, vmin, vmax, cam, tf, out, args, lods=(0.5, 1.0, 2.0, 4.0)
 
 def shadow_eval(amr, ctx, vmin, vmax, args, size=512):
     """Secondary rays to a central point light (the paper's global-illumination example):
-    frame time at `size`² with and without them, Phong, light step half a level-0 cell."""
+    frame time at `size`² without them, and with them under the per-ray loop (each lane
+    marches its samples' light rays) and under deferred shading (the default for Phong:
+    a warp marches each queued sample's light ray together); Phong, light step half a
+    level-0 cell."""
     import torch
     import synth
 
@@ -340,10 +371,14 @@ def shadow_eval(amr, ctx, vmin, vmax, args, size=512):
     out = torch.empty((size, size, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     res = {"size": size}
-    for name, kw in (("plain", {}), ("shadow", {"shadow": 1, "light": (0.5, 0.5, 0.5),
-                                                "light_step": 0.5 / 128, "light_ambient": 0.2})):
+    light = {"shadow": 1, "light": (0.5, 0.5, 0.5), "light_step": 0.5 / 128,
+             "light_ambient": 0.2}
+    for name, kw in (("plain", {}), ("shadow_per_ray", dict(light, schedule=0)),
+                     ("shadow", dict(light, schedule=3))):
         prm = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
                                      **kw)
+        if args.shade != 1 and kw.get("schedule") == 3:
+            continue
         n = ctx.amr_render(cam, tf, prm, out, count_samples=True)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -353,7 +388,9 @@ def shadow_eval(amr, ctx, vmin, vmax, args, size=512):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / 2
         res[name] = {"ms": ms, "frames_per_s": 1e3 / ms, "samples": n}
-    res["slowdown"] = res["shadow"]["ms"] / res["plain"]["ms"]
+    best = "shadow" if "shadow" in res else "shadow_per_ray"
+    res["slowdown"] = res[best]["ms"] / res["plain"]["ms"]
+    res["slowdown_per_ray"] = res["shadow_per_ray"]["ms"] / res["plain"]["ms"]
     return res
 
 
@@ -372,7 +409,9 @@ def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5, lo=256, hi=
     cams = [synth.orbit_camera(5000 + v, int(sd), int(sd)) for v, sd in enumerate(sides)]
     tfi = [v % 4 for v in range(n_views)]
     tfs = torch.as_tensor(np.stack(synth.tf_variants()), device="cuda")
-    p0 = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
+    # the separate launches use the batch's schedule (like for like)
+    p0 = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
+                                schedule=schedule, samples_per_iter=16)
     p = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
                                schedule=schedule, samples_per_iter=16)
     views, offsets, total = amr.make_views(cams, tfi)
@@ -412,6 +451,7 @@ def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5, lo=256, hi=
     ms_graph = timed(g.replay, reps=2)
     same = same and bool(torch.equal(out, ref))
     names = [f"{tw}x{th}/r{r}" for tw, th in ((8, 8), (16, 8), (16, 16)) for r in (1, 2, 4)]
+    names += [f"best tile/spi{k}" for k in (4, 8, 16, 32)]
     bps = BYTES_PER_SAMPLE[args.shade]
     return {"views": n_views, "sides": [lo, hi], "schedule": schedule,
             "pixels": int(sum(int(sd) ** 2 for sd in sides)),
@@ -421,15 +461,17 @@ def batch_eval(amr, ctx, vmin, vmax, args, peak, n_views=64, seed=5, lo=256, hi=
             "batched_graph": {"ms": ms_graph, "gsamples_s": samples / ms_graph / 1e6,
                               "frac_hbm": samples * bps / (ms_graph * 1e-3) / 1e9 / peak},
             "speedup_vs_separate": ms_sep / ms_graph,
-            "autotune": {"best": f"{best.tile_w}x{best.tile_h}/r{best.rays_per_thread}",
+            "autotune": {"best": f"{best.tile_w}x{best.tile_h}/r{best.rays_per_thread}"
+                                 f"/spi{best.samples_per_iter or p.samples_per_iter}",
                          "tuned_on_views": tune_views, "ms": dict(zip(names, table)),
                          "seconds": tune_s}}
 
 
 def schedules_eval(amr, ctx, vmin, vmax, tf, args, sizes=(2048, 1024, 512), spi=16):
-    """The frame march under the per-ray loop (schedule 0), persistent refill (2) and
-    deferred shading (3) at several image sizes (the C2 orbit view): Gsamples/s and
-    whether each image equals the per-ray one bit for bit."""
+    """The frame march under the per-ray loop (schedule 0), persistent refill (2),
+    deferred shading (3) and the library's default choice (auto) at several image sizes
+    (the C2 orbit view): Gsamples/s and whether each image equals the per-ray one bit for
+    bit."""
     import torch
     import synth
 
@@ -440,7 +482,7 @@ def schedules_eval(amr, ctx, vmin, vmax, tf, args, sizes=(2048, 1024, 512), spi=
         ref = torch.empty((size, size, 4), dtype=torch.float32, device="cuda")
         out = torch.empty_like(ref)
         row = {}
-        for sched in (0, 2, 3):
+        for sched in (0, 2, 3, -1):
             p = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
                                        schedule=sched, samples_per_iter=spi)
             if sched == 3 and args.shade != 1:
@@ -455,10 +497,44 @@ def schedules_eval(amr, ctx, vmin, vmax, tf, args, sizes=(2048, 1024, 512), spi=
             b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b) / 3
-            row[str(sched)] = {"ms": ms, "gsamples_s": n / ms / 1e6,
-                               "identical_to_per_ray": bool(torch.equal(dst, ref))}
+            row["auto" if sched < 0 else str(sched)] = {
+                "ms": ms, "gsamples_s": n / ms / 1e6,
+                "identical_to_per_ray": bool(torch.equal(dst, ref))}
         res[str(size)] = row
     return {"samples_per_iter": spi, "by_size": res}
+
+
+def halo_eval(amr, hier, vmin, vmax, tf, args):
+    """Bricks with a one- and a two-cell halo (the second lets gradient neighbours beyond
+    faces onto the same level read the sample's brick): Phong + gradient bricks, the
+    per-ray loop at 2048² and deferred shading at 1024² (the C2 orbit view)."""
+    import torch
+    import synth
+
+    stream = torch.cuda.current_stream()
+    res = {}
+    for halo in (1, 2):
+        ctx = amr.from_hierarchy(hier)
+        ctx.amr_build_kdtree("ptr", gradient=True, halo=halo)
+        row = {"brick_mb": ctx.amr_get_stats().brick_bytes / 1e6}
+        for size, sched in ((2048, 0), (1024, 3)):
+            cam = synth.orbit_camera(2, size, size)
+            out = torch.empty((size, size, 4), dtype=torch.float32, device="cuda")
+            p = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=1, ert_eps=args.ert,
+                                       schedule=sched)
+            n = ctx.amr_render(cam, tf, p, out, count_samples=True)
+            ctx.amr_render(cam, tf, p, out)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                ctx.amr_render(cam, tf, p, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 3
+            row[f"{size}/s{sched}"] = {"ms": ms, "gsamples_s": n / ms / 1e6}
+        res[f"halo{halo}"] = row
+        ctx.amr_destroy()
+    return res
 
 
 def c3_eval(amr, args, peak):
@@ -522,7 +598,9 @@ def _config(hier, args, storage, size=SIZE):
                          f"{'Phong' if args.shade else 'unshaded'} trilinear; step 0.5 h^l; "
                          f"ERT eps {args.ert}"),
             "storage": storage + ("+gradient bricks" if getattr(args, "gradient", 0) and
-                                  storage != "oracle" else ""),
+                                  storage != "oracle" else "") +
+                       (", two-cell halo" if getattr(args, "halo", 1) == 2 and
+                        storage != "oracle" else ""),
             "cells": getattr(args, "dtype", "f32"),
             "image": [size, size], "shade": args.shade,
             "schedule": getattr(args, "schedule", 0),
@@ -549,6 +627,10 @@ def main():
     ap.add_argument("--schedules", type=int, default=1,
                     help="time schedules 0 / 2 / 3 at 2048, 1024 and 512 pixels")
     ap.add_argument("--gradient", type=int, default=1, help="build gradient bricks")
+    ap.add_argument("--halo", type=int, default=2, choices=[1, 2],
+                    help="brick halo cells (2: gradient neighbours beyond faces onto the "
+                         "same level read the sample's brick)")
+    ap.add_argument("--halos", type=int, default=1, help="time one- and two-cell halos")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"],
                     help="brick cell storage type (interpolation and compositing stay FP32)")
     ap.add_argument("--learned", type=int, default=1, help="evaluate the learned proposal")
@@ -588,7 +670,7 @@ def main():
     tf = torch.as_tensor(tf_h, device="cuda")
     ctx = amr.from_hierarchy(hier, args.dtype)
     t0 = time.perf_counter()
-    ctx.amr_build_kdtree(args.storage, gradient=bool(args.gradient))
+    ctx.amr_build_kdtree(args.storage, gradient=bool(args.gradient), halo=args.halo)
     build_s = time.perf_counter() - t0
     st = ctx.amr_get_stats()
     params = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
@@ -650,10 +732,26 @@ def main():
     peak, peak_kind = _peaks()
     bps = BYTES_PER_SAMPLE[args.shade] * CELL_BYTES[args.dtype] // 4
     variant = _variant(args.storage, bool(args.gradient), args.dtype)
-    achieved = samples * bps / (kern_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": _profiled_traffic(args.shade, variant, size),
-            "peak_kind": peak_kind, "bytes_per_sample": bps,
+    # the march is bound by neither HBM nor any throughput unit (ncu: L1 about a third of
+    # its peak, issue slots under half busy, a third of the lanes active): the roofline is
+    # the one its gathers would hit first, L1, with SURVEY's algorithmic stencil bytes
+    stencil = samples * bps / (kern_ms * 1e-3) / 1e9
+    l1_peak, l1_kind = _l1_peak_gbs(clk["sm_mhz"] if clk else None)
+    prof = _profiled_counters(args.shade, variant, size, args.schedule)
+    traffic = prof["dram_bytes"] if prof else None
+    roof = {"bound": "l1", "achieved": stencil, "peak": l1_peak, "unit": "GB/s",
+            "frac": stencil / l1_peak, "peak_kind": l1_kind, "traffic": traffic,
+            "stencil_gbs": stencil, "bytes_per_sample": bps,
+            "l1_frac": prof["l1tex_throughput_pct"] / 100.0 if prof else None,
+            "lane_efficiency": prof["threads_per_inst"] / 32.0 if prof else None,
+            "issue_active": prof["issue_active_pct"] / 100.0 if prof else None,
+            "l1_bytes_per_sample": (prof["l1tex_t_bytes"] / samples
+                                    if prof and prof.get("l1tex_t_bytes") else None),
+            "hbm": {"peak": peak, "peak_kind": peak_kind, "stencil_frac": stencil / peak,
+                    "dram_frac": (traffic / (kern_ms * 1e-3) / 1e9 / peak
+                                  if traffic else None)},
+            "counters": (f"profiles/march_counters.json, sources {prof['sources']}"
+                         if prof else "stale or missing for the current kernel sources"),
             "kernel": {0: "march_kernel", 1: "wave_kernel", 2: "persist_kernel",
                        3: "deferred_kernel"}[args.schedule] +
                       f"<{variant}, trilinear, {'phong' if args.shade else 'plain'}>",
@@ -711,6 +809,8 @@ def main():
                 amr, ctx, vmin, vmax, args, peak, lo=64, hi=256, tune_views=64, schedule=3)
     if args.schedules and world == 1:
         extra["schedules"] = schedules_eval(amr, ctx, vmin, vmax, tf, args)
+    if args.halos and world == 1 and args.shade == 1 and args.dtype == "f32":
+        extra["halo"] = halo_eval(amr, hier, vmin, vmax, tf, args)
     if args.c3 and world == 1:
         extra["c3"] = c3_eval(amr, args, peak)
     if args.learned and world == 1:
