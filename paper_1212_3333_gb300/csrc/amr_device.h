@@ -10,6 +10,8 @@
 //   DLeaf  leaves[M]  96 B each, canonical (pre-order) leaf id order, with the
 //                      addressing of the leaf's brick.
 //   DPatch patches[P] 48 B each: where a patch's brick lives and how to address it.
+//   uint32 macro[G]   per cell of a grid over the root (at most 2^21 cells): the node slot
+//                      where a point location may start.
 //   bricks            one brick per patch with a one- or two-cell halo (Sec. 4), x fastest,
 //                      in the layout of the chosen storage strategy.
 #pragma once
@@ -109,6 +111,12 @@ struct RayArgs {
   double lod_scale;
   float lod_scale_f;
   int32_t n_leaves;     // leaves of the unpruned tree (ids at or above are pruned leaves)
+  // macro grid over the root (cells of macro_cell finest cells per axis, macro_dims of
+  // them): per cell the slot of the deepest node holding the whole cell, where an
+  // unpruned point location may start
+  const uint32_t* macro;
+  int32_t macro_cell;
+  int32_t macro_dims[3];
 };
 
 struct RenderArgs {

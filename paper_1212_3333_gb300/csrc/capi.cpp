@@ -66,6 +66,9 @@ void fill_ray(const amr_ctx* c, const amr_camera* cam, int row0, int rows, RayAr
   ra->row0 = row0;
   ra->rows = rows;
   ra->lod = c->dev.lod;
+  ra->macro = c->dev.macro;
+  ra->macro_cell = c->dev.macro_cell;
+  for (int a = 0; a < 3; ++a) ra->macro_dims[a] = c->dev.macro_dims[a];
   ra->levels = c->tree.lod_levels;  // levels a pruned node can have
   ra->lod_scale = 0.0;
   ra->lod_scale_f = 0.0f;

@@ -80,6 +80,9 @@ struct DeviceState {
   int32_t* lod = nullptr;                        // per node slot: (id << 5 | level) or -1
   int32_t* face_node = nullptr;                  // per leaf and face: node slot (neighbour start)
   int4* node_box = nullptr;                      // per node slot: box lo, hi (ropes)
+  uint32_t* macro = nullptr;                     // macro grid: point-location start slots
+  int32_t macro_cell = 1;                        // finest cells per macro cell per axis
+  int32_t macro_dims[3] = {1, 1, 1};
   int device = -1;
 };
 

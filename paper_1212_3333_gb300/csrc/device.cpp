@@ -1,5 +1,6 @@
 // Upload of the tree, leaves, patch table and bricks to the device, in one of the four
 // brick storage strategies (Sec. 4.1 packed pool, Sec. 4.2 handle table, rebuilt for CUDA).
+#include <algorithm>
 #include <cstring>
 #include <deque>
 
@@ -72,6 +73,45 @@ std::vector<DNode> layout_nodes(const Tree& t, const int64_t* root, std::vector<
       q.push_back(rc);
     }
     out[slot] = d;
+  }
+  return out;
+}
+
+// Macro grid over the root for point location: cells of G finest cells per axis (G = the
+// finest cells of one level-0 cell, doubled until the grid has at most 2^21 cells), each
+// holding the slot of the deepest node whose box contains the whole cell.  A point lies
+// in its cell, so a descent from that node reaches the same leaf as one from the root.
+std::vector<uint32_t> macro_grid(const std::vector<DNode>& nodes, const int64_t* root, int64_t R,
+                                 int32_t* cell, int32_t* dims) {
+  int64_t G = std::max<int64_t>(R, 1), ext[3], n[3];
+  for (int a = 0; a < 3; ++a) ext[a] = root[3 + a] - root[a];
+  for (;;) {
+    for (int a = 0; a < 3; ++a) n[a] = (ext[a] + G - 1) / G;
+    if (n[0] * n[1] * n[2] <= ((int64_t)1 << 21)) break;
+    G *= 2;
+  }
+  *cell = (int32_t)G;
+  for (int a = 0; a < 3; ++a) dims[a] = (int32_t)n[a];
+  std::vector<uint32_t> out((size_t)(n[0] * n[1] * n[2]), 0u);
+#pragma omp parallel for schedule(static)
+  for (long long gi = 0; gi < (long long)out.size(); ++gi) {
+    const int64_t g[3] = {gi % n[0], (gi / n[0]) % n[1], gi / (n[0] * n[1])};
+    int64_t lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = root[a] + g[a] * G;
+      hi[a] = std::min(root[a] + (g[a] + 1) * G, root[3 + a]);
+    }
+    uint32_t i = 0;
+    for (int depth = 0; depth < kMaxDepth; ++depth) {
+      const DNode& nd = nodes[i];
+      const uint32_t ax = nd.meta >> 30;
+      if (ax == (uint32_t)kLeafAxis) break;
+      const uint32_t c0 = nd.meta & kIndexMask;
+      if (hi[ax] <= nd.split) i = c0;
+      else if (lo[ax] >= nd.split) i = c0 + 1;
+      else break;
+    }
+    out[(size_t)gi] = i;
   }
   return out;
 }
@@ -215,6 +255,7 @@ void release_device(amr_ctx* c) {
   cudaFree(d.lod);
   cudaFree(d.face_node);
   cudaFree(d.node_box);
+  cudaFree(d.macro);
   cudaFree(d.leaves);
   cudaFree(d.patches);
   cudaFree(d.pool);
@@ -283,6 +324,10 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   CK(cudaMalloc(&d.leaves, std::max<size_t>(1, M + ML) * sizeof(DLeaf)));
   CK(cudaMalloc(&d.patches, P * sizeof(DPatch)));
   CK(cudaMalloc(&d.counters, kNumCounters * sizeof(unsigned long long)));
+  const std::vector<uint32_t> macro = macro_grid(nodes, c->root, c->R, &d.macro_cell, d.macro_dims);
+  CK(cudaMalloc(&d.macro, macro.size() * sizeof(uint32_t)));
+  CK(cudaMemcpyAsync(d.macro, macro.data(), macro.size() * sizeof(uint32_t),
+                     cudaMemcpyHostToDevice, stream));
   CK(cudaMemsetAsync(d.counters, 0, kNumCounters * sizeof(unsigned long long), stream));
 
   amr_status st;

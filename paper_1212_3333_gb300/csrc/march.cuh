@@ -451,11 +451,22 @@ __device__ __forceinline__ int next_leaf(const DNode* __restrict__ nodes,
   return descend(nodes, R, px, py, rf, start, pid0, tau0, e0, pid1, tau1, e1, lod_min);
 }
 
+// Node slot where the unpruned point location of finest cell f (inside the root) may start:
+// the macro-grid cell's deepest node holding the whole cell.
+__device__ __forceinline__ uint32_t macro_start(const RayArgs& R, int f0, int f1, int f2) {
+  const int g0 = (f0 - R.root_f[0]) / R.macro_cell;
+  const int g1 = (f1 - R.root_f[1]) / R.macro_cell;
+  const int g2 = (f2 - R.root_f[2]) / R.macro_cell;
+  return __ldg(R.macro + g0 + R.macro_dims[0] * (g1 + R.macro_dims[1] * g2));
+}
+
 // Point location by integer finest-cell coordinates (left iff f_a < split), stopping at a
 // pruned node when lod_min says so.
 __device__ __forceinline__ int locate_cell(const DNode* __restrict__ nodes, const RayArgs& R,
                                            int lod_min, int f0, int f1, int f2) {
-  uint32_t i = 0;
+  // unpruned: start at the macro-grid cell's node (a pruned descent must pass every
+  // type-(a) node above the leaf, so it starts at the root)
+  uint32_t i = lod_min >= kNoLod ? macro_start(R, f0, f1, f2) : 0u;
   for (int depth = 0; depth < kMaxDepth; ++depth) {
     const DNode nd = nodes[i];
     const uint32_t ax = nd.meta >> 30;
@@ -1163,7 +1174,8 @@ __device__ __noinline__ float shadow_transmittance(const RenderArgs& A, const Ra
 // schedule; every lane must call it with the same start point).  Round r takes the 32
 // consecutive samples 32 r .. 32 r + 31, one per lane: neighbouring lanes read
 // neighbouring cells.  A lane keeps the leaf of its last point, tries the leaf of the last
-// point of the previous round next, and otherwise locates its point from the root; the
+// point of the previous round next, and otherwise locates its point (from its macro-grid
+// cell's node); the
 // lanes that need it descend together, so a round pays one descent's latency however
 // many leaves its points span.  The round's factors exp(-kappa a delta) are multiplied in
 // a fixed tree order into T, so T is the same in every lane and differs from the per-lane
@@ -1201,7 +1213,7 @@ __device__ __forceinline__ float warp_shadow_transmittance(const RenderArgs& A, 
             f[2] < w2.y)
           lid = last;
       }
-      if (lid < 0) lid = locate_cell_from(A.nodes, 0u, f[0], f[1], f[2]);
+      if (lid < 0) lid = locate_cell_from(A.nodes, macro_start(R, f[0], f[1], f[2]), f[0], f[1], f[2]);
       if (lid < 0) {
         bad = true;
       } else {
