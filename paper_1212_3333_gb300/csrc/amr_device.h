@@ -89,6 +89,8 @@ struct DLevel {
   float inv_sc;      // 1 / sc
   float hmin;        // min_a h^l_a as float (gradient floor, pruning filter)
   float inv_step;    // 1 / step as float
+  float ginv[3];     // 0.5 / h^l_a as float (central-difference scale; exactly
+                     // 0.5f * (float)inv_h[a], halving being exact)
   double hmin_d;     // min_a h^l_a (exact pruning decisions)
 };
 

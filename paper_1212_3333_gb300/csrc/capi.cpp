@@ -97,6 +97,7 @@ void fill_levels(const amr_ctx* c, DLevel* lv, double step_factor) {
     d.inv_sc = 1.0f / (float)d.sc;
     d.hmin = (float)hmin;
     d.inv_step = (float)(1.0 / d.step);
+    for (int a = 0; a < 3; ++a) d.ginv[a] = 0.5f * (float)d.inv_h[a];
   }
 }
 

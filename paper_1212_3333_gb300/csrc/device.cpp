@@ -134,6 +134,12 @@ amr_status upload_bricks(amr_ctx* c, const std::vector<std::vector<T>>& bricks,
   td.filterMode = cudaFilterModePoint;
   td.readMode = cudaReadModeElementType;
   td.normalizedCoords = 0;
+  if (storage == AMR_STORE_PTR || storage == AMR_STORE_TEXOBJ) {
+    // the kernels address a per-patch brick with 32-bit element offsets
+    for (size_t p = 0; p < P; ++p)
+      if (bricks[p].size() >= ((size_t)1 << 31))
+        return fail(c, AMR_ERR_CAPACITY, "a brick holds 2^31 cells or more");
+  }
   if (storage == AMR_STORE_PTR) {
     // one pool, each brick 128-byte aligned; the table holds the device addresses
     std::vector<size_t> off(P);

@@ -520,8 +520,17 @@ __device__ __forceinline__ BrickRef leaf_brick(const DPatch* __restrict__ pt, co
   return b;
 }
 
+// In-brick element offsets: 32-bit for the per-patch storages (a brick holds fewer than
+// 2^31 cells, checked at upload), 64-bit for the atlases, whose strides span the atlas.
+template <int ST> struct BrickIndex { using type = long long; };
+template <> struct BrickIndex<ST_PTR> { using type = int; };
+template <> struct BrickIndex<ST_PTR_F16> { using type = int; };
+template <> struct BrickIndex<ST_PTR_BF16> { using type = int; };
+template <> struct BrickIndex<ST_TEXOBJ> { using type = int; };
+
 template <int ST>
-__device__ __forceinline__ float fetch(const RenderArgs& A, const BrickRef& b, long long lin, int i,
+__device__ __forceinline__ float fetch(const RenderArgs& A, const BrickRef& b,
+                                       typename BrickIndex<ST>::type lin, int i,
                                        int j, int k) {
   if constexpr (ST == ST_PTR) {
     return __ldg(reinterpret_cast<const float*>(b.base) + lin);
@@ -557,7 +566,8 @@ __device__ __forceinline__ float4 unpack_bf164(uint2 u) {
 }
 
 template <int ST>
-__device__ __forceinline__ float4 fetch4(const RenderArgs& A, const BrickRef& b, long long lin,
+__device__ __forceinline__ float4 fetch4(const RenderArgs& A, const BrickRef& b,
+                                         typename BrickIndex<ST>::type lin,
                                          int i, int j, int k) {
   if constexpr (ST == ST_PTR) {
     return __ldg(reinterpret_cast<const float4*>(b.gbase) + lin);
@@ -612,7 +622,8 @@ __device__ __forceinline__ Corners trilinear_fetch(const RenderArgs& A, const Br
   c.wx = bx - (float)ix;
   c.wy = by - (float)iy;
   c.wz = bz - (float)iz;
-  const long long l0 = (long long)ix + (long long)b.sy * iy + (long long)b.sz * iz;
+  using I = typename BrickIndex<ST>::type;
+  const I l0 = (I)ix + (I)b.sy * iy + (I)b.sz * iz;
   c.v[0] = fetch<ST>(A, b, l0, ix, iy, iz);
   c.v[1] = fetch<ST>(A, b, l0 + 1, ix + 1, iy, iz);
   c.v[2] = fetch<ST>(A, b, l0 + b.sy, ix, iy + 1, iz);
@@ -638,7 +649,8 @@ __device__ __forceinline__ float cell_at(const RenderArgs& A, const BrickRef& b,
   i = min(max(i, 0), b.dim[0] - 1);
   j = min(max(j, 0), b.dim[1] - 1);
   k = min(max(k, 0), b.dim[2] - 1);
-  return fetch<ST>(A, b, (long long)i + (long long)b.sy * j + (long long)b.sz * k, i, j, k);
+  using I = typename BrickIndex<ST>::type;
+  return fetch<ST>(A, b, (I)i + (I)b.sy * j + (I)b.sz * k, i, j, k);
 }
 
 // State of the segment being sampled.
@@ -917,7 +929,8 @@ __device__ __forceinline__ void gradient(const RenderArgs& A, const RayArgs& R, 
       const int iy = min(max((int)beta[1], 1), b.dim[1] - 3);
       const int iz = min(max((int)beta[2], 1), b.dim[2] - 3);
       const float wx = beta[0] - (float)ix, wy = beta[1] - (float)iy, wz = beta[2] - (float)iz;
-      const long long l0 = (long long)ix + (long long)b.sy * iy + (long long)b.sz * iz;
+      using I = typename BrickIndex<ST>::type;
+      const I l0 = (I)ix + (I)b.sy * iy + (I)b.sz * iz;
       const float4 q000 = fetch4<ST>(A, b, l0, ix, iy, iz);
       const float4 q100 = fetch4<ST>(A, b, l0 + 1, ix + 1, iy, iz);
       const float4 q010 = fetch4<ST>(A, b, l0 + b.sy, ix, iy + 1, iz);
@@ -934,11 +947,11 @@ __device__ __forceinline__ void gradient(const RenderArgs& A, const RayArgs& R, 
         return fmaf(wz, c1 - c0, c0);
       };
       g[0] = tri(q000.y, q100.y, q010.y, q110.y, q001.y, q101.y, q011.y, q111.y) *
-             (0.5f * (float)lv.inv_h[0]);
+             lv.ginv[0];
       g[1] = tri(q000.z, q100.z, q010.z, q110.z, q001.z, q101.z, q011.z, q111.z) *
-             (0.5f * (float)lv.inv_h[1]);
+             lv.ginv[1];
       g[2] = tri(q000.w, q100.w, q010.w, q110.w, q001.w, q101.w, q011.w, q111.w) *
-             (0.5f * (float)lv.inv_h[2]);
+             lv.ginv[2];
       return;
     }
     if (inner) {
@@ -947,9 +960,10 @@ __device__ __forceinline__ void gradient(const RenderArgs& A, const RayArgs& R, 
       const int iy = min(max((int)beta[1], 1), b.dim[1] - 3);
       const int iz = min(max((int)beta[2], 1), b.dim[2] - 3);
       const float wx = beta[0] - (float)ix, wy = beta[1] - (float)iy, wz = beta[2] - (float)iz;
-      const long long l0 = (long long)ix + (long long)b.sy * iy + (long long)b.sz * iz;
+      using I = typename BrickIndex<ST>::type;
+      const I l0 = (I)ix + (I)b.sy * iy + (I)b.sz * iz;
       auto V = [&](int dx, int dy, int dz) {
-        return fetch<ST>(A, b, l0 + dx + (long long)b.sy * dy + (long long)b.sz * dz, ix + dx,
+        return fetch<ST>(A, b, l0 + dx + (I)b.sy * dy + (I)b.sz * dz, ix + dx,
                          iy + dy, iz + dz);
       };
       float c[2][2][2];
@@ -981,9 +995,9 @@ __device__ __forceinline__ void gradient(const RenderArgs& A, const RayArgs& R, 
       const float gy1 = fmaf(wx, dyv[1][1] - dyv[1][0], dyv[1][0]);
       const float gz0 = fmaf(wx, dzv[0][1] - dzv[0][0], dzv[0][0]);
       const float gz1 = fmaf(wx, dzv[1][1] - dzv[1][0], dzv[1][0]);
-      g[0] = fmaf(wz, gx1 - gx0, gx0) * (0.5f * (float)lv.inv_h[0]);
-      g[1] = fmaf(wz, gy1 - gy0, gy0) * (0.5f * (float)lv.inv_h[1]);
-      g[2] = fmaf(wy, gz1 - gz0, gz0) * (0.5f * (float)lv.inv_h[2]);
+      g[0] = fmaf(wz, gx1 - gx0, gx0) * lv.ginv[0];
+      g[1] = fmaf(wz, gy1 - gy0, gy0) * lv.ginv[1];
+      g[2] = fmaf(wy, gz1 - gz0, gz0) * lv.ginv[2];
       return;
     }
   }
@@ -1003,9 +1017,9 @@ __device__ __forceinline__ void gradient(const RenderArgs& A, const RayArgs& R, 
     d[1] += ax == 1 ? sg * v : 0.0f;
     d[2] += ax == 2 ? sg * v : 0.0f;
   }
-  g[0] = d[0] * (0.5f * (float)lv.inv_h[0]);
-  g[1] = d[1] * (0.5f * (float)lv.inv_h[1]);
-  g[2] = d[2] * (0.5f * (float)lv.inv_h[2]);
+  g[0] = d[0] * lv.ginv[0];
+  g[1] = d[1] * lv.ginv[1];
+  g[2] = d[2] * lv.ginv[2];
 }
 
 // A segment ready for sampling: its state, first sample position and step in brick
