@@ -56,8 +56,9 @@ def _march_sha() -> str:
     return h.hexdigest()[:12]
 
 
-def _variant(storage: str, gradient: bool, dtype: str) -> str:
-    return f"{storage}{'+grad' if gradient else ''}/{dtype}"
+def _variant(storage: str, gradient: bool, dtype: str, halo: int = 1, maxbrick: bool = False) -> str:
+    return (f"{storage}{'+grad' if gradient else ''}{'+halo2' if halo == 2 else ''}"
+            f"{'+max' if maxbrick else ''}/{dtype}")
 
 
 def _profiled_counters(shade: int, variant: str, size: int, schedule: int):
@@ -283,7 +284,8 @@ def learned_eval(amr, ctx, hier, vmin, vmax, tf, args, taus=(1e-4, 1e-3, 1e-2)):
 
 
 def precision_eval(amr, hier, vmin, vmax, cam, tf, out, args, peak):
-    """Cell storage precision: FP32 / FP16 / BF16 bricks (pointer table, gradient bricks),
+    """Cell storage precision: FP32 / FP16 / BF16 bricks (pointer table, gradient bricks and
+    the bench's halo and stencil-maximum options),
     each timed plain and Phong, with PSNR and max-abs of its Phong image against the
     FP32-storage image of the same view."""
     import torch
@@ -294,7 +296,7 @@ def precision_eval(amr, hier, vmin, vmax, cam, tf, out, args, peak):
     for dtype, e in (("f32", 4), ("f16", 2), ("bf16", 2)):
         t0 = time.perf_counter()
         ctx = amr.from_hierarchy(hier, dtype)
-        ctx.amr_build_kdtree("ptr", gradient=True)
+        ctx.amr_build_kdtree("ptr", gradient=True, halo=args.halo, maxbrick=bool(args.maxbrick))
         r = {"brick_mb": ctx.amr_get_stats().brick_bytes / 1e6,
              "build_s": time.perf_counter() - t0}
         for shade in (0, 1):
@@ -600,11 +602,14 @@ def _config(hier, args, storage, size=SIZE):
             "storage": storage + ("+gradient bricks" if getattr(args, "gradient", 0) and
                                   storage != "oracle" else "") +
                        (", two-cell halo" if getattr(args, "halo", 1) == 2 and
-                        storage != "oracle" else ""),
+                        storage != "oracle" else "") +
+                       (", stencil-maximum bricks" if getattr(args, "maxbrick", 0) and
+                        storage == "ptr" else ""),
             "cells": getattr(args, "dtype", "f32"),
             "image": [size, size], "shade": args.shade,
             "schedule": getattr(args, "schedule", 0),
-            "l2": "inputs larger than L2: 602 MB of bricks vs 129 MB L2, no flush"}
+            "l2": ("inputs larger than L2: 602-677 MB of bricks (plus gradient and "
+                   "stencil-maximum bricks) vs 129 MB L2, no flush")}
 
 
 def main():
@@ -631,6 +636,8 @@ def main():
                     help="brick halo cells (2: gradient neighbours beyond faces onto the "
                          "same level read the sample's brick)")
     ap.add_argument("--halos", type=int, default=1, help="time one- and two-cell halos")
+    ap.add_argument("--maxbrick", type=int, default=1,
+                    help="build stencil-maximum bricks (one-load test of transparent samples)")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"],
                     help="brick cell storage type (interpolation and compositing stay FP32)")
     ap.add_argument("--learned", type=int, default=1, help="evaluate the learned proposal")
@@ -670,7 +677,8 @@ def main():
     tf = torch.as_tensor(tf_h, device="cuda")
     ctx = amr.from_hierarchy(hier, args.dtype)
     t0 = time.perf_counter()
-    ctx.amr_build_kdtree(args.storage, gradient=bool(args.gradient), halo=args.halo)
+    ctx.amr_build_kdtree(args.storage, gradient=bool(args.gradient), halo=args.halo,
+                         maxbrick=bool(args.maxbrick) and args.storage == "ptr")
     build_s = time.perf_counter() - t0
     st = ctx.amr_get_stats()
     params = amr.amr_default_params(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert,
@@ -731,7 +739,8 @@ def main():
         return
     peak, peak_kind = _peaks()
     bps = BYTES_PER_SAMPLE[args.shade] * CELL_BYTES[args.dtype] // 4
-    variant = _variant(args.storage, bool(args.gradient), args.dtype)
+    variant = _variant(args.storage, bool(args.gradient), args.dtype, args.halo,
+                       bool(args.maxbrick) and args.storage == "ptr")
     # the march is bound by neither HBM nor any throughput unit (ncu: L1 about a third of
     # its peak, issue slots under half busy, a third of the lanes active): the roofline is
     # the one its gathers would hit first, L1, with SURVEY's algorithmic stencil bytes

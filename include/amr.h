@@ -80,7 +80,15 @@ typedef enum {
    * brick, as a face onto the same unrefined patch does with one cell.  The halo cells
    * hold V_l like the first layer.  Not in the paper; results agree with the one-cell
    * layout to FP32 rounding. */
-  AMR_STORE_HALO2 = 0x200
+  AMR_STORE_HALO2 = 0x200,
+  /* flag (AMR_STORE_PTR only): also build stencil-maximum bricks - per cell the largest of
+   * the eight cells of the trilinear stencil it starts, in the cell type.  A trilinear
+   * value never exceeds its stencil's maximum and the transfer function's lookup is
+   * monotone, so a sample whose stencil maximum maps to zero opacity (with one table entry
+   * of margin for rounding) is transparent; the per-ray and deferred marches decide such
+   * samples with one load instead of eight.  Images and sample counts are unchanged (each
+   * sample is still taken); not in the paper. */
+  AMR_STORE_MAXBRICK = 0x400
 } amr_storage;
 
 /* Pinhole camera.  Pixel (i, j), row 0 at the top, has the ray o = eye,

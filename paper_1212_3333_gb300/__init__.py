@@ -74,19 +74,22 @@ class AmrContext:
 
     # ----------------------------------------------------------------- lifecycle
     @staticmethod
-    def _storage_code(storage, gradient: bool, halo: int = 1) -> int:
+    def _storage_code(storage, gradient: bool, halo: int = 1, maxbrick: bool = False) -> int:
         st = STORAGES[storage] if isinstance(storage, str) else int(storage)
         if halo not in (1, 2):
             raise ValueError("halo must be 1 or 2")
-        return st | (AMR_STORE_GRADIENT if gradient else 0) | (_lib.AMR_STORE_HALO2 if halo == 2 else 0)
+        return (st | (AMR_STORE_GRADIENT if gradient else 0) |
+                (_lib.AMR_STORE_HALO2 if halo == 2 else 0) |
+                (_lib.AMR_STORE_MAXBRICK if maxbrick else 0))
 
     def amr_build_kdtree(self, storage="ptr", stream=None, gradient: bool = False,
-                         halo: int = 1) -> None:
-        st = self._storage_code(storage, gradient, halo)
+                         halo: int = 1, maxbrick: bool = False) -> None:
+        st = self._storage_code(storage, gradient, halo, maxbrick)
         _check(self._lib.amr_build_kdtree(self._h, st, C.c_void_p(_stream_ptr(stream))), self._h)
 
-    def amr_build_host(self, storage="ptr", gradient: bool = False, halo: int = 1) -> None:
-        st = self._storage_code(storage, gradient, halo)
+    def amr_build_host(self, storage="ptr", gradient: bool = False, halo: int = 1,
+                       maxbrick: bool = False) -> None:
+        st = self._storage_code(storage, gradient, halo, maxbrick)
         _check(self._lib.amr_build_host(self._h, st), self._h)
 
     def amr_destroy(self) -> None:

@@ -23,6 +23,7 @@ DTYPES = {"f32": AMR_F32, "f16": AMR_F16, "bf16": AMR_BF16}
 AMR_STORE_PTR, AMR_STORE_TEXOBJ, AMR_STORE_ATLAS_LINEAR, AMR_STORE_ATLAS_TEX3D = 0, 1, 2, 3
 AMR_STORE_GRADIENT = 0x100
 AMR_STORE_HALO2 = 0x200
+AMR_STORE_MAXBRICK = 0x400
 AMR_MLP_FEATURES, AMR_MLP_PARAMS, AMR_MLP_PACKED_BYTES = 12, 9217, 23440
 STORAGES = {"ptr": AMR_STORE_PTR, "texobj": AMR_STORE_TEXOBJ,
             "atlas_linear": AMR_STORE_ATLAS_LINEAR, "atlas_tex3d": AMR_STORE_ATLAS_TEX3D}

@@ -34,6 +34,7 @@ constexpr uint32_t kFaceLeaf = 0x80000000u;  // face-table entry names a leaf (i
 constexpr int kNumCounters = 8;
 constexpr int kQueueCounter = 5;       // counters[5]: head of the batched work queue
 constexpr int kShadeShadowBit = 4;     // kernel shading variant bit: secondary rays
+constexpr int kShadeMaxBit = 8;        // kernel variant bit: stencil-maximum opacity test
 constexpr int kMaxBatchViews = 128;
 // status bits raised by kernels (OR-ed into counters[1])
 constexpr unsigned long long kStatusCapacity = 1ull;   // segment or sample bound hit
@@ -156,6 +157,7 @@ struct RenderArgs {
   int32_t samples_per_iter;      // refill schedule: samples per lane between warp steps
   int32_t coarse_factor;         // learned mode 2: step multiplier below tau
   int32_t learned_min_samples;   // learned modes: segments shorter than this skip the MLP
+  long long mdelta;              // stencil-maximum brick = value brick + mdelta bytes (ptr)
 };
 
 struct TraceArgs {

@@ -160,11 +160,20 @@ amr_status launch_st(amr_ctx* c, const BatchArgs& b, const amr_batch_config& cfg
 amr_status launch_batch(amr_ctx* c, const BatchArgs& b, int storage, int shade, int schedule,
                         const amr_batch_config& cfg, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
+  const bool mx = (shade & kShadeMaxBit) != 0;  // the stencil-maximum test
+  shade &= ~kShadeMaxBit;
   if (storage != ST_PTR) return fail(c, AMR_ERR_ARG, "batched rendering needs the ptr storage (FP32)");
   if (schedule == 3) {
-    if (shade == 1) return launch_st<ST_PTR, 1, true>(c, b, cfg, s);
-    if (shade == 2) return launch_st<ST_PTR, 2, true>(c, b, cfg, s);
+    if (shade == 1) return mx ? launch_st<ST_PTR, 1 | kShadeMaxBit, true>(c, b, cfg, s)
+                              : launch_st<ST_PTR, 1, true>(c, b, cfg, s);
+    if (shade == 2) return mx ? launch_st<ST_PTR, 2 | kShadeMaxBit, true>(c, b, cfg, s)
+                              : launch_st<ST_PTR, 2, true>(c, b, cfg, s);
     return fail(c, AMR_ERR_ARG, "deferred shading renders with shade = 1");
+  }
+  if (mx) {
+    if (shade == 0) return launch_st<ST_PTR, kShadeMaxBit, false>(c, b, cfg, s);
+    if (shade == 1) return launch_st<ST_PTR, 1 | kShadeMaxBit, false>(c, b, cfg, s);
+    return launch_st<ST_PTR, 2 | kShadeMaxBit, false>(c, b, cfg, s);
   }
   if (shade == 0) return launch_st<ST_PTR, 0, false>(c, b, cfg, s);
   if (shade == 1) return launch_st<ST_PTR, 1, false>(c, b, cfg, s);

@@ -259,6 +259,37 @@ amr_status build_gradient_bricks(amr_ctx* c) {
   return AMR_OK;
 }
 
+// Stencil-maximum bricks: per cell c the largest of the eight cells c + {0, 1}^3 - the
+// cells of the trilinear stencil whose lower corner is c - and +infinity in the outer
+// layer, which no stencil starts at.  A trilinear value never exceeds its corners'
+// maximum, so a sample whose stencil maximum the transfer function maps to zero opacity
+// is transparent; the kernels test that with one load instead of eight.
+amr_status build_max_bricks(amr_ctx* c) {
+  const size_t P = c->patches.size();
+  c->mbricks.assign(P, {});
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long long pi = 0; pi < (long long)P; ++pi) {
+    const size_t p = (size_t)pi;
+    const int64_t H = c->halo;
+    const int64_t d0 = c->patches[p].n[0] + 2 * H, d1 = c->patches[p].n[1] + 2 * H,
+                  d2 = c->patches[p].n[2] + 2 * H;
+    const std::vector<float>& v = c->bricks[p];
+    std::vector<float>& m = c->mbricks[p];
+    m.assign(v.size(), INFINITY);
+    auto at = [&](int64_t i, int64_t j, int64_t k) { return v[(size_t)(i + d0 * (j + d1 * k))]; };
+    for (int64_t k = 0; k + 1 < d2; ++k)
+      for (int64_t j = 0; j + 1 < d1; ++j)
+        for (int64_t i = 0; i + 1 < d0; ++i) {
+          float mx = at(i, j, k);
+          for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+              for (int dx = 0; dx < 2; ++dx) mx = std::max(mx, at(i + dx, j + dy, k + dz));
+          m[(size_t)(i + d0 * (j + d1 * k))] = mx;
+        }
+  }
+  return AMR_OK;
+}
+
 // Next-fit decreasing height in 3D over square bases; returns the container height.
 static int64_t nfdh(const std::vector<std::array<int64_t, 3>>& ext, const std::vector<int>& order,
                     int64_t W, std::vector<int64_t>& org) {

@@ -223,15 +223,19 @@ amr_status amr_build_host(amr_ctx* c, amr_storage storage_flags) {
   const int storage = (int)storage_flags & 0xff;
   const bool gradient = ((int)storage_flags & AMR_STORE_GRADIENT) != 0;
   const int halo = ((int)storage_flags & AMR_STORE_HALO2) ? 2 : 1;
+  const bool maxb = ((int)storage_flags & AMR_STORE_MAXBRICK) != 0;
   if (storage < AMR_STORE_PTR || storage > AMR_STORE_ATLAS_TEX3D ||
-      ((int)storage_flags & ~(0xff | AMR_STORE_GRADIENT | AMR_STORE_HALO2)))
+      ((int)storage_flags & ~(0xff | AMR_STORE_GRADIENT | AMR_STORE_HALO2 | AMR_STORE_MAXBRICK)))
     return fail(c, AMR_ERR_ARG, "unknown storage");
+  if (maxb && storage != AMR_STORE_PTR)
+    return fail(c, AMR_ERR_ARG, "stencil-maximum bricks need the ptr storage");
   if (c->host_built && c->halo != halo) {
     // bricks, leaf ranges and face bits depend on the halo: build them again
     if (c->device_built) release_device(c);
     c->host_built = false;
     c->bricks.clear();
     c->gbricks.clear();
+    c->mbricks.clear();
     c->packing = Packing();
   }
   c->halo = halo;
@@ -258,6 +262,10 @@ amr_status amr_build_host(amr_ctx* c, amr_storage storage_flags) {
       amr_status s = build_gradient_bricks(c);
       if (s != AMR_OK) return s;
     }
+    if (maxb && c->mbricks.empty()) {
+      amr_status s = build_max_bricks(c);
+      if (s != AMR_OK) return s;
+    }
     if (c->dtype == AMR_F16) {
       // binary16 tops out at 65504: refuse data that would be stored as infinity
       auto over = [](float v) { return std::isfinite(v) && std::isinf(storage_round(AMR_F16, v)); };
@@ -273,10 +281,12 @@ amr_status amr_build_host(amr_ctx* c, amr_storage storage_flags) {
   } catch (const std::bad_alloc&) {
     return fail(c, AMR_ERR_OOM, "out of host memory during the build");
   }
-  if ((c->storage != storage || c->want_gradient != gradient) && c->device_built)
+  if ((c->storage != storage || c->want_gradient != gradient || c->want_max != maxb) &&
+      c->device_built)
     release_device(c);
   c->storage = storage;
   c->want_gradient = gradient;
+  c->want_max = maxb;
   c->build_seconds +=
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   c->err.clear();
@@ -406,6 +416,7 @@ static amr_status prepare_render(amr_ctx* c, const amr_camera* cam, int32_t tf_n
   a->light_ambient = (float)p->light_ambient;
   a->coarse_factor = p->coarse_factor;
   a->learned_min_samples = p->learned_min_samples;
+  a->mdelta = c->dev.mpool ? (long long)((char*)c->dev.mpool - (char*)c->dev.pool) : 0;
   if (c->dtype != AMR_F32 && (p->interp != AMR_INTERP_TRILINEAR || p->schedule == 1))
     return fail(c, AMR_ERR_ARG, "16-bit cells render trilinear with schedule 0, 2 or 3");
   if (p->learned != 0) {
@@ -428,11 +439,16 @@ static int kernel_storage(const amr_ctx* c) {
   return c->storage + (c->dtype == AMR_F16 ? 4 : 5);
 }
 
-// shading variant: 2 = Phong reading the gradient bricks (trilinear only), when built
+// shading variant: 2 = Phong reading the gradient bricks (trilinear only), when built;
+// plus the stencil-maximum opacity test (trilinear, per-ray or deferred schedule, no
+// secondary rays or proposal), when those bricks were built
 static int kernel_shade(const amr_ctx* c, const amr_render_params* p) {
   int sh = p->shade;
   if (p->shade && p->interp == AMR_INTERP_TRILINEAR && c->want_gradient && c->dev.gpool_bytes)
     sh = 2;
+  if (c->dev.mpool && p->interp == AMR_INTERP_TRILINEAR && !p->shadow &&
+      (p->learned || p->schedule == 0 || p->schedule == 3))
+    sh |= kShadeMaxBit;
   return sh | (p->shadow ? kShadeShadowBit : 0);
 }
 

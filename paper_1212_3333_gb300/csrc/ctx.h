@@ -63,6 +63,7 @@ struct DeviceState {
   size_t pool_bytes = 0;
   void* gpool = nullptr; // gradient bricks, same layout, float4 per cell
   size_t gpool_bytes = 0;
+  void* mpool = nullptr; // stencil-maximum bricks, same offsets as pool (ptr storage)
   std::vector<void*> garrays;                    // gradient cudaArray_t per patch
   std::vector<cudaTextureObject_t> gtexobjs;
   void* gatlas_array = nullptr;
@@ -102,6 +103,8 @@ struct amr_ctx {
   int halo = 1;                            // brick halo width in cells (1, or 2 with
                                            // AMR_STORE_HALO2: faces onto the same level)
   std::vector<std::vector<float4>> gbricks; // per patch: value and central differences
+  bool want_max = false;                   // build stencil-maximum bricks too (ptr storage)
+  std::vector<std::vector<float>> mbricks;  // per patch: max of the 8 cells of each stencil
   std::vector<float> leaf_vmin, leaf_vmax;
   amr::Packing packing;
   int storage = -1;
@@ -122,6 +125,7 @@ amr_status build_tree(amr_ctx* c);
 // bricks.cpp
 amr_status build_bricks(amr_ctx* c);
 amr_status build_gradient_bricks(amr_ctx* c);
+amr_status build_max_bricks(amr_ctx* c);
 amr_status pack_atlas(amr_ctx* c);
 // device.cpp
 amr_status upload(amr_ctx* c, void* stream);

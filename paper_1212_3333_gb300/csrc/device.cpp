@@ -239,6 +239,29 @@ amr_status upload_bricks(amr_ctx* c, const std::vector<std::vector<T>>& bricks,
   return AMR_OK;
 }
 
+// Stencil-maximum bricks of the pointer storage: a second pool with the value pool's
+// offsets (the same brick sizes and alignment), so a brick's maximum brick lies at a fixed
+// byte distance (mpool - pool) from it.
+template <typename T>
+amr_status upload_max_pool(amr_ctx* c, const std::vector<std::vector<T>>& mb, cudaStream_t stream) {
+  DeviceState& d = c->dev;
+  const size_t P = mb.size();
+  const size_t align = 128 / sizeof(T);
+  std::vector<size_t> off(P);
+  size_t elems = 0;
+  for (size_t p = 0; p < P; ++p) {
+    off[p] = elems;
+    elems += (mb[p].size() + align - 1) / align * align;
+  }
+  if (elems * sizeof(T) != d.pool_bytes)
+    return fail(c, AMR_ERR_STATE, "stencil-maximum pool does not match the brick pool");
+  CK(cudaMalloc(&d.mpool, elems * sizeof(T)));
+  for (size_t p = 0; p < P; ++p)
+    CK(cudaMemcpyAsync((T*)d.mpool + off[p], mb[p].data(), mb[p].size() * sizeof(T),
+                       cudaMemcpyHostToDevice, stream));
+  return AMR_OK;
+}
+
 }  // namespace
 
 void release_device(amr_ctx* c) {
@@ -257,6 +280,7 @@ void release_device(amr_ctx* c) {
   if (d.atlas_array) cudaFreeArray((cudaArray_t)d.atlas_array);
   if (d.gatlas_array) cudaFreeArray((cudaArray_t)d.gatlas_array);
   cudaFree(d.gpool);
+  cudaFree(d.mpool);
   cudaFree(d.nodes);
   cudaFree(d.lod);
   cudaFree(d.face_node);
@@ -340,6 +364,10 @@ amr_status upload(amr_ctx* c, void* stream_v) {
   if (c->dtype == AMR_F32) {
     st = upload_bricks<float>(c, c->bricks, pt, false, stream);
     if (st != AMR_OK) return st;
+    if (c->want_max && c->storage == AMR_STORE_PTR) {
+      st = upload_max_pool<float>(c, c->mbricks, stream);
+      if (st != AMR_OK) return st;
+    }
     if (c->want_gradient) {
       st = upload_bricks<float4>(c, c->gbricks, pt, true, stream);
       if (st != AMR_OK) return st;
@@ -357,6 +385,17 @@ amr_status upload(amr_ctx* c, void* stream_v) {
       }
       st = upload_bricks<uint16_t>(c, b16, pt, false, stream);
       if (st != AMR_OK) return st;
+      if (c->want_max && c->storage == AMR_STORE_PTR) {
+        // the maximum of the rounded cells is the rounded maximum (rounding is monotone)
+#pragma omp parallel for schedule(dynamic, 4)
+        for (long long pi = 0; pi < (long long)P; ++pi) {
+          const size_t p = (size_t)pi;
+          const std::vector<float>& m = c->mbricks[p];
+          for (size_t i = 0; i < m.size(); ++i) b16[p][i] = storage_bits(c->dtype, m[i]);
+        }
+        st = upload_max_pool<uint16_t>(c, b16, stream);
+        if (st != AMR_OK) return st;
+      }
     }
     if (c->want_gradient) {
       std::vector<std::vector<ushort4>> g16(P);

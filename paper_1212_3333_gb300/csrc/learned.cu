@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(128) log_kernel(const __grid_constant__ Render
     const float a_in = Acc;
     SegSetup g;
     setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
-    sample_segment<ST, 1, 0>(A, A.ray, s_tf, g, lv, 0.f, 0.f, 0.f, C0, C1, C2, Acc, nsamp);
+    sample_segment<ST, 1, 0>(A, A.ray, s_tf, nullptr, g, lv, 0.f, 0.f, 0.f, C0, C1, C2, Acc, nsamp);
     const uint32_t h = mix32((uint32_t)i * 0x9E3779B1u ^ mix32((uint32_t)j + L.seed * 0x85EBCA77u) ^
                              ((uint32_t)seg * 0xC2B2AE3Du));
     if ((float)(h >> 8) * (1.0f / 16777216.0f) < L.keep_prob) {
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
       const DLevel& lv = A.lv[lf.level];
       SegSetup g;
       setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
-      if (sample_segment<ST, 1, SHADE>(A, A.ray, s_tf, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
+      if (sample_segment<ST, 1, SHADE>(A, A.ray, s_tf, s_nz, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
         live = false;  // early ray termination
     }
     if (lid >= 0) {
@@ -235,7 +235,13 @@ amr_status launch_learned(amr_ctx* c, const RenderArgs& a, int storage, int shad
   const size_t smem = learned_smem(a.tf_n);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if (storage == ST_PTR) {
+  const bool mx = (shade & kShadeMaxBit) != 0;  // stencil-maximum test (pointer storage)
+  shade &= ~kShadeMaxBit;
+  if (storage == ST_PTR && mx) {
+    if (shade == 0) e = launch_one(learned_kernel<ST_PTR, kShadeMaxBit>, grid, block, smem, s, a);
+    else if (shade == 1) e = launch_one(learned_kernel<ST_PTR, 1 | kShadeMaxBit>, grid, block, smem, s, a);
+    else e = launch_one(learned_kernel<ST_PTR, 2 | kShadeMaxBit>, grid, block, smem, s, a);
+  } else if (storage == ST_PTR) {
     if (shade == 0) e = launch_one(learned_kernel<ST_PTR, 0>, grid, block, smem, s, a);
     else if (shade == 1) e = launch_one(learned_kernel<ST_PTR, 1>, grid, block, smem, s, a);
     else e = launch_one(learned_kernel<ST_PTR, 2>, grid, block, smem, s, a);

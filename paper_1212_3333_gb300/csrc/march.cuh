@@ -642,6 +642,80 @@ __device__ __forceinline__ float trilinear(const RenderArgs& A, const BrickRef& 
   return trilinear_fetch<ST>(A, b, bx, by, bz).value();
 }
 
+// The trilinear stencil of a brick position, as trilinear_fetch computes it (clamped into
+// the brick): its lower corner's element offset and the weights.
+template <int ST>
+struct Stencil {
+  typename BrickIndex<ST>::type l0;
+  float wx, wy, wz;
+};
+
+template <int ST>
+__device__ __forceinline__ Stencil<ST> stencil_at(const BrickRef& b, float bx, float by, float bz) {
+  bx = fminf(fmaxf(bx, 0.0f), (float)(b.dim[0] - 1));
+  by = fminf(fmaxf(by, 0.0f), (float)(b.dim[1] - 1));
+  bz = fminf(fmaxf(bz, 0.0f), (float)(b.dim[2] - 1));
+  const int ix = min((int)bx, b.dim[0] - 2);
+  const int iy = min((int)by, b.dim[1] - 2);
+  const int iz = min((int)bz, b.dim[2] - 2);
+  using I = typename BrickIndex<ST>::type;
+  Stencil<ST> st;
+  st.wx = bx - (float)ix;
+  st.wy = by - (float)iy;
+  st.wz = bz - (float)iz;
+  st.l0 = (I)ix + (I)b.sy * iy + (I)b.sz * iz;
+  return st;
+}
+
+// Trilinear value of a stencil (the arithmetic of Corners::value on the same cells).
+template <int ST>
+__device__ __forceinline__ float stencil_value(const RenderArgs& A, const BrickRef& b,
+                                               const Stencil<ST>& st) {
+  static_assert(ST == ST_PTR || ST == ST_PTR_F16 || ST == ST_PTR_BF16,
+                "stencil-maximum bricks belong to the pointer storage");
+  Corners c;
+  c.wx = st.wx;
+  c.wy = st.wy;
+  c.wz = st.wz;
+  const auto l0 = st.l0;
+  c.v[0] = fetch<ST>(A, b, l0, 0, 0, 0);
+  c.v[1] = fetch<ST>(A, b, l0 + 1, 0, 0, 0);
+  c.v[2] = fetch<ST>(A, b, l0 + b.sy, 0, 0, 0);
+  c.v[3] = fetch<ST>(A, b, l0 + b.sy + 1, 0, 0, 0);
+  c.v[4] = fetch<ST>(A, b, l0 + b.sz, 0, 0, 0);
+  c.v[5] = fetch<ST>(A, b, l0 + b.sz + 1, 0, 0, 0);
+  c.v[6] = fetch<ST>(A, b, l0 + b.sz + b.sy, 0, 0, 0);
+  c.v[7] = fetch<ST>(A, b, l0 + b.sz + b.sy + 1, 0, 0, 0);
+  return c.value();
+}
+
+// The stencil-maximum brick's cell at offset lin (pointer storage; the maximum of the
+// eight stencil cells starting there, in the cell type): the value brick shifted by
+// A.mdelta bytes.
+template <int ST>
+__device__ __forceinline__ float fetch_max(const RenderArgs& A, const BrickRef& b,
+                                           typename BrickIndex<ST>::type lin) {
+  if constexpr (ST == ST_PTR) {
+    return __ldg(reinterpret_cast<const float*>(b.base + A.mdelta) + lin);
+  } else if constexpr (ST == ST_PTR_F16) {
+    return __half2float(__ldg(reinterpret_cast<const __half*>(b.base + A.mdelta) + lin));
+  } else if constexpr (ST == ST_PTR_BF16) {
+    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(b.base + A.mdelta) + lin));
+  } else {
+    return __int_as_float(0x7f800000);  // no maximum bricks: never transparent
+  }
+}
+
+// Whether every value up to m - and so a trilinear value whose stencil's maximum is m - maps
+// to zero opacity: tf_lookup's index of m (the same FP32 arithmetic, monotone in the
+// value), plus one entry of margin for the last-bit rounding of the interpolation, and
+// every table entry up to the next one after it transparent (nz: prefix counts of the
+// non-transparent entries).
+__device__ __forceinline__ bool stencil_transparent(const RenderArgs& A, const int* nz, float m) {
+  const float u = fminf(fmaxf((m - A.vmin) * A.inv_range, 0.0f), 1.0f) * (float)(A.tf_n - 1);
+  return nz[min((int)u + 3, A.tf_n)] == 0;
+}
+
 // Nearest cell value at integer brick index (clamped).
 template <int ST>
 __device__ __forceinline__ float cell_at(const RenderArgs& A, const BrickRef& b, int i, int j,
@@ -1145,6 +1219,21 @@ __device__ __forceinline__ const int* tf_nonzero_prefix(const RenderArgs& A, con
 // multiply T by exp(-kappa * 0 * delta) = 1 exactly, so both marchers skip them: the same
 // T bit for bit, without their stencils.
 
+// A light sample at brick position (bx, by, bz) whose stencil maximum maps to zero
+// opacity (stencil-maximum bricks present: mdelta != 0) contributes the factor 1 exactly.
+template <int ST>
+__device__ __forceinline__ bool light_sample_transparent(const RenderArgs& A, const int* nz,
+                                                         const BrickRef& b, float bx, float by,
+                                                         float bz) {
+  if constexpr (ST == ST_PTR) {
+    if (A.mdelta == 0) return false;
+    const Stencil<ST> st = stencil_at<ST>(b, bx, by, bz);
+    return stencil_transparent(A, nz, fetch_max<ST>(A, b, st.l0));
+  } else {
+    return false;
+  }
+}
+
 // One lane marches the whole light ray, sample by sample (the per-ray schedule).
 // Consecutive samples usually stay in one leaf, which is reused.
 template <int ST>
@@ -1174,9 +1263,11 @@ __device__ __noinline__ float shadow_transmittance(const RenderArgs& A, const Ra
       clear = tf_transparent(s_nz, A.tf_n, lf.vmin, lf.vmax, A.vmin, A.inv_range);
     }
     if (clear) continue;
-    const float v = trilinear<ST>(A, b, fmaf(P[0], inv_sc, 0.5f - (float)b.lo[0]),
-                                  fmaf(P[1], inv_sc, 0.5f - (float)b.lo[1]),
-                                  fmaf(P[2], inv_sc, 0.5f - (float)b.lo[2]));
+    const float bx = fmaf(P[0], inv_sc, 0.5f - (float)b.lo[0]);
+    const float by = fmaf(P[1], inv_sc, 0.5f - (float)b.lo[1]);
+    const float bz = fmaf(P[2], inv_sc, 0.5f - (float)b.lo[2]);
+    if (light_sample_transparent<ST>(A, s_nz, b, bx, by, bz)) continue;  // factor 1
+    const float v = trilinear<ST>(A, b, bx, by, bz);
     const float a_tf = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range).w;
     T *= expf(-A.kappa * a_tf * L.delta);
     if (T <= 1e-4f) return 0.0f;
@@ -1247,11 +1338,14 @@ __device__ __forceinline__ float warp_shadow_transmittance(const RenderArgs& A, 
     if (__any_sync(FULL, bad)) return T;  // malformed tree: the per-lane march stops too
     float term = 1.0f;
     if (valid && !clear) {
-      const float v = trilinear<ST>(A, b, fmaf(P[0], inv_sc, 0.5f - (float)b.lo[0]),
-                                    fmaf(P[1], inv_sc, 0.5f - (float)b.lo[1]),
-                                    fmaf(P[2], inv_sc, 0.5f - (float)b.lo[2]));
-      const float a_tf = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range).w;
-      term = expf(-A.kappa * a_tf * L.delta);
+      const float bx = fmaf(P[0], inv_sc, 0.5f - (float)b.lo[0]);
+      const float by = fmaf(P[1], inv_sc, 0.5f - (float)b.lo[1]);
+      const float bz = fmaf(P[2], inv_sc, 0.5f - (float)b.lo[2]);
+      if (!light_sample_transparent<ST>(A, s_nz, b, bx, by, bz)) {
+        const float v = trilinear<ST>(A, b, bx, by, bz);
+        const float a_tf = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range).w;
+        term = expf(-A.kappa * a_tf * L.delta);
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) term *= __shfl_down_sync(FULL, term, off);
@@ -1333,15 +1427,98 @@ __device__ __forceinline__ bool sample_one(const RenderArgs& A, const RayArgs& R
                                             C2, Acc);
 }
 
+// Samples of a segment whose stencil maxima are tested in groups (stencil-maximum bricks):
+// the maxima of G consecutive samples are loaded together, so a run of transparent
+// samples pays one load latency per group; a sample that may be opaque is then evaluated
+// in full.  Every sample is counted as it is taken, in order.  Unshaded, the group's
+// evaluations are unrolled; shaded (a large evaluation) they run in a rolled loop that
+// rotates the loaded maxima through registers.  G = 0 (shaded): one test per sample.
+#ifndef AMR_MAX_GROUP_PLAIN
+#define AMR_MAX_GROUP_PLAIN 4
+#endif
+#ifndef AMR_MAX_GROUP_SHADED
+#define AMR_MAX_GROUP_SHADED 4
+#endif
+
+template <int ST, int SHADE, int G>
+__device__ __forceinline__ bool sample_segment_grouped(const RenderArgs& A, const RayArgs& R,
+                                                       const float4* s_tf, const int* nz,
+                                                       const SegSetup& g, const DLevel& lv,
+                                                       float Lx, float Ly, float Lz, float& C0,
+                                                       float& C1, float& C2, float& Acc,
+                                                       unsigned& nsamp) {
+  const int n = g.s.n;
+  if constexpr (G == 0) {
+    for (int k = 0; k < n; ++k) {
+      ++nsamp;
+      float beta[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
+      const Stencil<ST> st = stencil_at<ST>(g.s.brick, beta[0], beta[1], beta[2]);
+      if (stencil_transparent(A, nz, fetch_max<ST>(A, g.s.brick, st.l0))) continue;
+      const float v = stencil_value<ST>(A, g.s.brick, st);
+      if (composite_sample<ST, 1, SHADE>(A, R, s_tf, g, lv, k, beta, v, Lx, Ly, Lz, C0, C1, C2,
+                                         Acc))
+        return true;
+    }
+    return false;
+  } else {
+    for (int k0 = 0; k0 < n; k0 += G) {
+      float m[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        const int k = min(k0 + j, n - 1);
+        const Stencil<ST> st = stencil_at<ST>(g.s.brick, fmaf((float)k, g.db[0], g.b0[0]),
+                                              fmaf((float)k, g.db[1], g.b0[1]),
+                                              fmaf((float)k, g.db[2], g.b0[2]));
+        m[j] = fetch_max<ST>(A, g.s.brick, st.l0);
+      }
+      auto one = [&](int k, float mk) -> int {  // 1: stop (early termination)
+        ++nsamp;
+        if (stencil_transparent(A, nz, mk)) return 0;  // opacity zero: nothing to composite
+        float beta[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
+        const Stencil<ST> st = stencil_at<ST>(g.s.brick, beta[0], beta[1], beta[2]);
+        const float v = stencil_value<ST>(A, g.s.brick, st);
+        return composite_sample<ST, 1, SHADE>(A, R, s_tf, g, lv, k, beta, v, Lx, Ly, Lz, C0, C1,
+                                              C2, Acc) ? 1 : 0;
+      };
+      if constexpr ((SHADE & 3) == 0) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          if (k0 + j >= n) break;
+          if (one(k0 + j, m[j])) return true;
+        }
+      } else {
+#pragma unroll 1
+        for (int j = 0; j < G; ++j) {
+          if (k0 + j >= n) break;
+          const float mj = m[0];
+#pragma unroll
+          for (int q = 0; q + 1 < G; ++q) m[q] = m[q + 1];
+          if (one(k0 + j, mj)) return true;
+        }
+      }
+    }
+    return false;
+  }
+}
+
 // March the samples of one segment front to back.  Returns true when early ray
-// termination stops the ray inside the segment.
+// termination stops the ray inside the segment.  nz: the prefix counts of the transfer
+// function's non-transparent entries (read by the stencil-maximum test only).
 template <int ST, int INTERP, int SHADE>
 __device__ __forceinline__ bool sample_segment(const RenderArgs& A, const RayArgs& R,
-                                               const float4* s_tf,
+                                               const float4* s_tf, const int* nz,
                                                const SegSetup& g, const DLevel& lv, float Lx,
                                                float Ly, float Lz, float& C0, float& C1, float& C2,
                                                float& Acc, unsigned& nsamp) {
-  if constexpr (INTERP == 1 && SHADE == 0) {
+  if constexpr (INTERP == 1 && (SHADE & kShadeMaxBit) != 0) {
+    constexpr int G = (SHADE & 3) == 0 ? AMR_MAX_GROUP_PLAIN : AMR_MAX_GROUP_SHADED;
+    return sample_segment_grouped<ST, SHADE, G>(A, R, s_tf, nz, g, lv, Lx, Ly, Lz, C0, C1, C2,
+                                                Acc, nsamp);
+  } else if constexpr (INTERP == 1 && SHADE == 0) {
     // software pipeline: the cells of sample k + 1 are requested before sample k is
     // composited (unshaded only: with shading the extra live registers spill, measured
     // 13 % slower on C2 at 2048^2; unshaded 2 % faster)
@@ -1441,7 +1618,8 @@ __device__ __forceinline__ float4 march_ray(const RenderArgs& A, const RayArgs& 
       }
       SegSetup g;
       setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g, lmin);
-      if (sample_segment<ST, INTERP, SHADE>(A, R, s_tf, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
+      if (sample_segment<ST, INTERP, SHADE>(A, R, s_tf, s_nz, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc,
+                                            nsamp))
         pid1 = kPidOut;  // early ray termination
       pid0 = pid1;
       tau0 = tau1;
@@ -1492,7 +1670,7 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
   auto march_pixel = [&](int i, int jr) {
     const int j = R.row0 + jr;
     if (i < R.width && jr < R.rows && j < R.height) {
-      if constexpr (SHADE == 0) {
+      if constexpr ((SHADE & ~kShadeMaxBit) == 0) {
         // unshaded: the ray frame lives in shared memory (read once per segment), leaving
         // the registers to the sample loop (measured 6 % faster on C2 at 2048^2; with
         // shading the extra shared-memory reads cost more than the spills they save).  One

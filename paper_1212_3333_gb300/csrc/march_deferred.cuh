@@ -92,11 +92,18 @@ __device__ __forceinline__ float3 shade_task(const RenderArgs& A, const RayArgs&
 // The march of pixel (i, j) of view R by one lane of a warp whose 32 lanes all call this
 // together (lanes without a pixel pass active = false); Q is the warp's queue area.
 // Returns premultiplied RGBA (zero for inactive lanes); adds to nsamp and status.
+// samples whose stencil maxima the deferred loop loads together (stencil-maximum bricks)
+#ifndef AMR_DEFER_GROUP
+#define AMR_DEFER_GROUP 4
+#endif
+constexpr int kDeferGroup = AMR_DEFER_GROUP;
+
 template <int ST, int SHADE>
 __device__ __forceinline__ float4 march_deferred(const RenderArgs& A, const RayArgs& R, int i,
                                                  int j, bool active, const float4* s_tf,
                                                  const int* s_nz, DeferArea& Q, unsigned& nsamp,
                                                  unsigned long long& status) {
+  constexpr bool MX = (SHADE & kShadeMaxBit) != 0;  // the stencil-maximum test
   const unsigned FULL = 0xffffffffu;
   const int lane = (int)(threadIdx.x + blockDim.x * threadIdx.y) & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -205,24 +212,27 @@ __device__ __forceinline__ float4 march_deferred(const RenderArgs& A, const RayA
         break;
       }
     }
-    // samples: every lane passes each step, so the queue operations are warp-wide
-    for (int step = 0; step < A.samples_per_iter; ++step) {
+    // one sample step of every lane (the queue operations are warp-wide); mj: the sample's
+    // stencil maximum when the stencil-maximum test is on
+    auto take = [&](float mj) {
       bool opaque = false;
       float beta[3], cr = 0.f, cg = 0.f, cb = 0.f, w = 0.f;
       if (live && k < g.s.n) {
         ++nsamp;
 #pragma unroll
         for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
-        const float v = trilinear<ST>(A, g.s.brick, beta[0], beta[1], beta[2]);
-        const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
-        if (c.w > 0.0f) {
-          const float alpha = -expm1f(-A.kappa * c.w * g.delta);
-          w = (1.0f - Acc) * alpha;
-          Acc += w;
-          cr = c.x;
-          cg = c.y;
-          cb = c.z;
-          opaque = true;
+        if (!(MX && stencil_transparent(A, s_nz, mj))) {  // else opacity zero
+          const float v = trilinear<ST>(A, g.s.brick, beta[0], beta[1], beta[2]);
+          const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
+          if (c.w > 0.0f) {
+            const float alpha = -expm1f(-A.kappa * c.w * g.delta);
+            w = (1.0f - Acc) * alpha;
+            Acc += w;
+            cr = c.x;
+            cg = c.y;
+            cb = c.z;
+            opaque = true;
+          }
         }
         ++k;
       }
@@ -255,6 +265,33 @@ __device__ __forceinline__ float4 march_deferred(const RenderArgs& A, const RayA
         }
         queued += __popc(om);
       }
+    };
+    if constexpr (MX) {
+      // the stencil maxima of a lane's next kDeferGroup samples are loaded together, then
+      // the steps take them in a rolled loop that rotates them through registers
+      for (int step = 0; step < A.samples_per_iter;) {
+        float m[kDeferGroup];
+#pragma unroll
+        for (int q = 0; q < kDeferGroup; ++q) {
+          m[q] = __int_as_float(0x7f800000);
+          if (live && k < g.s.n) {
+            const int kk = min(k + q, g.s.n - 1);
+            const Stencil<ST> st = stencil_at<ST>(g.s.brick, fmaf((float)kk, g.db[0], g.b0[0]),
+                                                  fmaf((float)kk, g.db[1], g.b0[1]),
+                                                  fmaf((float)kk, g.db[2], g.b0[2]));
+            m[q] = fetch_max<ST>(A, g.s.brick, st.l0);
+          }
+        }
+#pragma unroll 1
+        for (int jj = 0; jj < kDeferGroup && step < A.samples_per_iter; ++jj, ++step) {
+          const float mj = m[0];
+#pragma unroll
+          for (int q = 0; q + 1 < kDeferGroup; ++q) m[q] = m[q + 1];
+          take(mj);
+        }
+      }
+    } else {
+      for (int step = 0; step < A.samples_per_iter; ++step) take(0.0f);
     }
   }
   if (queued != 0) drain();

@@ -67,6 +67,11 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
   const dim3 grid((unsigned)((a.ray.width + 7) / 8), (unsigned)((a.ray.rows + 15) / 16));
   const size_t tf_bytes = (size_t)a.tf_n * sizeof(float4) + (size_t)(a.tf_n + 1) * sizeof(int);
   if (grid.x == 0 || grid.y == 0) return AMR_OK;
+  // the stencil-maximum opacity test: pointer storages, trilinear, schedules 0 and 3
+  constexpr bool kPtr = ST == ST_PTR || ST == ST_PTR_F16 || ST == ST_PTR_BF16;
+  const bool mx = kPtr && (shade & kShadeMaxBit) != 0 && interp == 1 &&
+                  !(shade & kShadeShadow) && (schedule == 0 || schedule == 3);
+  shade &= ~kShadeMaxBit;
   cudaError_t e;
   if (shade & kShadeShadow) {
     // secondary rays to the point light: per-ray schedule (a lane marches its samples'
@@ -95,6 +100,13 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
     if (interp != 1 || (shade != 1 && shade != 2))
       return fail(c, AMR_ERR_ARG, "deferred shading renders trilinear with shade = 1");
     const size_t smem = ((tf_bytes + 15) & ~(size_t)15) + 4 * sizeof(DeferArea);
+    if constexpr (kPtr) {
+      if (mx) {
+        if (shade == 1) e = launch_tiles(deferred_kernel<ST, 1 | kShadeMaxBit>, smem, s, a);
+        else e = launch_tiles(deferred_kernel<ST, 2 | kShadeMaxBit>, smem, s, a);
+        goto launched;
+      }
+    }
     if (shade == 1) e = launch_tiles(deferred_kernel<ST, 1>, smem, s, a);
     else e = launch_tiles(deferred_kernel<ST, 2>, smem, s, a);
   } else if (schedule == 2) {
@@ -109,6 +121,14 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
     if (interp != 1 || schedule != 0)
       return fail(c, AMR_ERR_ARG, "16-bit storage renders trilinear with schedule 0, 2 or 3");
     const size_t smem = tf_bytes;
+    if constexpr (kPtr) {
+      if (mx) {
+        if (shade == 0) e = launch_tiles(march_kernel<ST, 1, kShadeMaxBit>, smem, s, a);
+        else if (shade == 1) e = launch_tiles(march_kernel<ST, 1, 1 | kShadeMaxBit>, smem, s, a);
+        else e = launch_tiles(march_kernel<ST, 1, 2 | kShadeMaxBit>, smem, s, a);
+        goto launched;
+      }
+    }
     if (shade == 0) e = launch_tiles(march_kernel<ST, 1, 0>, smem, s, a);
     else if (shade == 1) e = launch_tiles(march_kernel<ST, 1, 1>, smem, s, a);
     else e = launch_tiles(march_kernel<ST, 1, 2>, smem, s, a);
@@ -122,6 +142,14 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
     else e = launch_one(march_kernel<ST, 0, 1, false>, grid, block, smem, s, a);
   } else if (schedule == 0) {
     const size_t smem = tf_bytes;
+    if constexpr (kPtr) {
+      if (mx) {
+        if (shade == 0) e = launch_tiles(march_kernel<ST, 1, kShadeMaxBit>, smem, s, a);
+        else if (shade == 1) e = launch_tiles(march_kernel<ST, 1, 1 | kShadeMaxBit>, smem, s, a);
+        else e = launch_tiles(march_kernel<ST, 1, 2 | kShadeMaxBit>, smem, s, a);
+        goto launched;
+      }
+    }
     if (interp == 1 && shade == 0) e = launch_tiles(march_kernel<ST, 1, 0>, smem, s, a);
     else if (interp == 1 && shade == 1) e = launch_tiles(march_kernel<ST, 1, 1>, smem, s, a);
     else if (interp == 1 && shade == 2) e = launch_tiles(march_kernel<ST, 1, 2>, smem, s, a);
@@ -135,6 +163,7 @@ amr_status launch_storage(amr_ctx* c, const RenderArgs& a, int interp, int shade
     else if (interp == 0 && shade == 0) e = launch_one(wave_kernel<ST, 0, 0>, grid, block, smem, s, a);
     else e = launch_one(wave_kernel<ST, 0, 1>, grid, block, smem, s, a);
   }
+launched:
   if (e != cudaSuccess)
     return fail(c, AMR_ERR_CUDA, std::string("march launch: ") + cudaGetErrorString(e));
   return AMR_OK;
