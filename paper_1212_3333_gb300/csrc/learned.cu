@@ -109,6 +109,25 @@ __global__ void __launch_bounds__(128) log_kernel(const __grid_constant__ Render
   }
 }
 
+// The learned march samples a segment as the plain march does; with stencil-maximum bricks
+// it tests every sample's maximum on its own (AMR_LEARNED_GROUP 0) or G at a time.
+#ifndef AMR_LEARNED_GROUP
+#define AMR_LEARNED_GROUP 0
+#endif
+template <int ST, int SHADE>
+__device__ __forceinline__ bool sample_learned(const RenderArgs& A, const float4* s_tf,
+                                               const int* s_nz, const SegSetup& g,
+                                               const DLevel& lv, float Lx, float Ly, float Lz,
+                                               float& C0, float& C1, float& C2, float& Acc,
+                                               unsigned& nsamp) {
+  if constexpr ((SHADE & kShadeMaxBit) != 0)
+    return sample_segment_grouped<ST, SHADE, AMR_LEARNED_GROUP>(A, A.ray, s_tf, s_nz, g, lv, Lx,
+                                                                Ly, Lz, C0, C1, C2, Acc, nsamp);
+  else
+    return sample_segment<ST, 1, SHADE>(A, A.ray, s_tf, s_nz, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc,
+                                        nsamp);
+}
+
 template <int ST, int SHADE>
 __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __grid_constant__ RenderArgs A) {
   extern __shared__ float4 smem[];
@@ -208,7 +227,7 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
       const DLevel& lv = A.lv[lf.level];
       SegSetup g;
       setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
-      if (sample_segment<ST, 1, SHADE>(A, A.ray, s_tf, s_nz, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
+      if (sample_learned<ST, SHADE>(A, s_tf, s_nz, g, lv, Lx, Ly, Lz, C0, C1, C2, Acc, nsamp))
         live = false;  // early ray termination
     }
     if (lid >= 0) {

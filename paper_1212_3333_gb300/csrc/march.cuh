@@ -1655,6 +1655,11 @@ __device__ __forceinline__ void stage_tf(const float4* __restrict__ tf, int n, f
 // marching its own 8x4 tile once - used for the per-patch texture storage, whose fetches
 // need more registers than the queue loop leaves (C2 2048^2 unshaded: 44.5 against 9.3
 // Gsamples/s with the queue).
+#ifndef AMR_WARP_TILE_W
+#define AMR_WARP_TILE_W 8  // pixel tile of one warp: AMR_WARP_TILE_W x (32 / AMR_WARP_TILE_W)
+#endif
+static_assert(AMR_WARP_TILE_W == 4 || AMR_WARP_TILE_W == 8 || AMR_WARP_TILE_W == 16,
+              "warp tile width");
 template <int ST, int INTERP, int SHADE, bool QUEUE = true>
 __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
     march_kernel(const __grid_constant__ RenderArgs A) {
@@ -1686,8 +1691,9 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
     }
   };
   if constexpr (QUEUE) {
-    const int tiles_x = (R.width + 7) / 8;
-    const int n_tiles = tiles_x * ((R.rows + 3) / 4);
+    constexpr int TW = AMR_WARP_TILE_W, TH = 32 / TW;
+    const int tiles_x = (R.width + TW - 1) / TW;
+    const int n_tiles = tiles_x * ((R.rows + TH - 1) / TH);
     // each pass takes one tile, and the queue hands out every tile once
     for (;;) {
       int t = 0;
@@ -1697,7 +1703,7 @@ __global__ void __launch_bounds__(128, kMinBlocks<SHADE>)
       }
       t = __shfl_sync(0xffffffffu, t, 0);
       if (t >= n_tiles) break;
-      march_pixel((t % tiles_x) * 8 + (lane & 7), (t / tiles_x) * 4 + (lane >> 3));
+      march_pixel((t % tiles_x) * TW + lane % TW, (t / tiles_x) * TH + lane / TW);
     }
   } else {
     march_pixel(blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
