@@ -986,46 +986,68 @@ __device__ __forceinline__ int segment_count(const RayArgs& R, int px, int py, c
 // differences, or one 32-cell stencil (the differences along an axis are lerps of the two
 // outer cell pairs, combined bilinearly in the other axes).  Otherwise each neighbour goes
 // through neighbour_at (cross-leaf lookups), in one rolled loop.
+// Whether both gradient neighbours of brick position beta on every axis read the segment's
+// own brick (beyond the FP32 error margin): then the brick's cells give the gradient.
+__device__ __forceinline__ bool gradient_inner(const SegState& s, const float* beta) {
+  const float m = s.margin;
+  bool inner = true;
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    inner = inner && (beta[q] - 1.0f >= s.bl[q] + m) && (beta[q] + 1.0f < s.bh[q] - m);
+  return inner;
+}
+
+// The eight gradient-brick cells (V, central differences) of the trilinear stencil at an
+// inner brick position, and the weights.
+struct GradCorners {
+  float4 q[8];  // x fastest, then y, then z (as Corners)
+  float wx, wy, wz;
+  __device__ __forceinline__ float tri(int c) const {  // component c = 1, 2, 3 (y, z, w)
+    auto e = [&](int i) { return c == 1 ? q[i].y : c == 2 ? q[i].z : q[i].w; };
+    const float c00 = fmaf(wx, e(1) - e(0), e(0)), c10 = fmaf(wx, e(3) - e(2), e(2));
+    const float c01 = fmaf(wx, e(5) - e(4), e(4)), c11 = fmaf(wx, e(7) - e(6), e(6));
+    const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
+    return fmaf(wz, c1 - c0, c0);
+  }
+  __device__ __forceinline__ void gradient(const DLevel& lv, float* g) const {
+    g[0] = tri(1) * lv.ginv[0];
+    g[1] = tri(2) * lv.ginv[1];
+    g[2] = tri(3) * lv.ginv[2];
+  }
+};
+
+template <int ST>
+__device__ __forceinline__ GradCorners grad_fetch(const RenderArgs& A, const BrickRef& b,
+                                                  const float* beta) {
+  const int ix = min(max((int)beta[0], 1), b.dim[0] - 3);
+  const int iy = min(max((int)beta[1], 1), b.dim[1] - 3);
+  const int iz = min(max((int)beta[2], 1), b.dim[2] - 3);
+  GradCorners c;
+  c.wx = beta[0] - (float)ix;
+  c.wy = beta[1] - (float)iy;
+  c.wz = beta[2] - (float)iz;
+  using I = typename BrickIndex<ST>::type;
+  const I l0 = (I)ix + (I)b.sy * iy + (I)b.sz * iz;
+  c.q[0] = fetch4<ST>(A, b, l0, ix, iy, iz);
+  c.q[1] = fetch4<ST>(A, b, l0 + 1, ix + 1, iy, iz);
+  c.q[2] = fetch4<ST>(A, b, l0 + b.sy, ix, iy + 1, iz);
+  c.q[3] = fetch4<ST>(A, b, l0 + b.sy + 1, ix + 1, iy + 1, iz);
+  c.q[4] = fetch4<ST>(A, b, l0 + b.sz, ix, iy, iz + 1);
+  c.q[5] = fetch4<ST>(A, b, l0 + b.sz + 1, ix + 1, iy, iz + 1);
+  c.q[6] = fetch4<ST>(A, b, l0 + b.sz + b.sy, ix, iy + 1, iz + 1);
+  c.q[7] = fetch4<ST>(A, b, l0 + b.sz + b.sy + 1, ix + 1, iy + 1, iz + 1);
+  return c;
+}
+
 template <int ST, int INTERP, int GB>
 __device__ __forceinline__ void gradient(const RenderArgs& A, const RayArgs& R, const SegState& s,
                                          const float* beta,
                                          int k, const DLevel& lv, float* g) {
   if constexpr (INTERP == 1) {
-    const float m = s.margin;
-    bool inner = true;
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      inner = inner && (beta[q] - 1.0f >= s.bl[q] + m) && (beta[q] + 1.0f < s.bh[q] - m);
+    const bool inner = gradient_inner(s, beta);
     if (GB && inner) {
       // gradient brick: trilinear interpolation of the per-cell central differences
-      const BrickRef& b = s.brick;
-      const int ix = min(max((int)beta[0], 1), b.dim[0] - 3);
-      const int iy = min(max((int)beta[1], 1), b.dim[1] - 3);
-      const int iz = min(max((int)beta[2], 1), b.dim[2] - 3);
-      const float wx = beta[0] - (float)ix, wy = beta[1] - (float)iy, wz = beta[2] - (float)iz;
-      using I = typename BrickIndex<ST>::type;
-      const I l0 = (I)ix + (I)b.sy * iy + (I)b.sz * iz;
-      const float4 q000 = fetch4<ST>(A, b, l0, ix, iy, iz);
-      const float4 q100 = fetch4<ST>(A, b, l0 + 1, ix + 1, iy, iz);
-      const float4 q010 = fetch4<ST>(A, b, l0 + b.sy, ix, iy + 1, iz);
-      const float4 q110 = fetch4<ST>(A, b, l0 + b.sy + 1, ix + 1, iy + 1, iz);
-      const float4 q001 = fetch4<ST>(A, b, l0 + b.sz, ix, iy, iz + 1);
-      const float4 q101 = fetch4<ST>(A, b, l0 + b.sz + 1, ix + 1, iy, iz + 1);
-      const float4 q011 = fetch4<ST>(A, b, l0 + b.sz + b.sy, ix, iy + 1, iz + 1);
-      const float4 q111 = fetch4<ST>(A, b, l0 + b.sz + b.sy + 1, ix + 1, iy + 1, iz + 1);
-      auto tri = [&](float v000, float v100, float v010, float v110, float v001, float v101,
-                     float v011, float v111) {
-        const float c00 = fmaf(wx, v100 - v000, v000), c10 = fmaf(wx, v110 - v010, v010);
-        const float c01 = fmaf(wx, v101 - v001, v001), c11 = fmaf(wx, v111 - v011, v011);
-        const float c0 = fmaf(wy, c10 - c00, c00), c1 = fmaf(wy, c11 - c01, c01);
-        return fmaf(wz, c1 - c0, c0);
-      };
-      g[0] = tri(q000.y, q100.y, q010.y, q110.y, q001.y, q101.y, q011.y, q111.y) *
-             lv.ginv[0];
-      g[1] = tri(q000.z, q100.z, q010.z, q110.z, q001.z, q101.z, q011.z, q111.z) *
-             lv.ginv[1];
-      g[2] = tri(q000.w, q100.w, q010.w, q110.w, q001.w, q101.w, q011.w, q111.w) *
-             lv.ginv[2];
+      grad_fetch<ST>(A, s.brick, beta).gradient(lv, g);
       return;
     }
     if (inner) {
@@ -1373,26 +1395,18 @@ __device__ __forceinline__ void phong(const RenderArgs& A, const DLevel& lv, con
   cb = fminf(fmaxf(fmaf(cb, diff, spec), 0.0f), 1.0f);
 }
 
-// Sample k of a segment (Sec. 3: emission-absorption compositing; Sec. 4: gradient
-// shading), composited front to back into (C, Acc).  Returns true when early ray
-// termination stops the ray at this sample.
-// Colour, opacity and compositing of sample k with value v at brick position beta.
-template <int ST, int INTERP, int SHADE>
-__device__ __forceinline__ bool composite_sample(const RenderArgs& A, const RayArgs& R,
-                                                 const float4* s_tf, const SegSetup& g,
-                                                 const DLevel& lv, int k, const float* beta,
-                                                 float v, float Lx, float Ly, float Lz,
-                                                 float& C0, float& C1, float& C2, float& Acc) {
+// Opacity, shading and compositing of a sample whose transfer-function entry c has non-zero
+// opacity (gr: its gradient, read when shading).  Returns true at early ray termination.
+template <int ST, int SHADE>
+__device__ __forceinline__ bool finish_sample(const RenderArgs& A, const RayArgs& R,
+                                              const float4* s_tf, const SegSetup& g,
+                                              const DLevel& lv, const float* beta, float4 c,
+                                              const float* gr, float Lx, float Ly, float Lz,
+                                              float& C0, float& C1, float& C2, float& Acc) {
   const SegState& s = g.s;
-  const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
-  if (c.w <= 0.0f) return false;
   const float alpha = -expm1f(-A.kappa * c.w * g.delta);
   float cr = c.x, cg = c.y, cb = c.z;
-  if constexpr ((SHADE & 3) >= 1) {
-    float gr[3];
-    gradient<ST, INTERP, ((SHADE & 3) == 2)>(A, R, s, beta, k, lv, gr);
-    phong(A, lv, gr, Lx, Ly, Lz, cr, cg, cb);
-  }
+  if constexpr ((SHADE & 3) >= 1) phong(A, lv, gr, Lx, Ly, Lz, cr, cg, cb);
   if constexpr ((SHADE & kShadeShadow) != 0) {
     // the sample in finest-cell units: beta = X / sc - lo + 0.5
     const float sc = (float)lv.sc;
@@ -1412,6 +1426,21 @@ __device__ __forceinline__ bool composite_sample(const RenderArgs& A, const RayA
   return Acc >= A.ert_thresh;
 }
 
+// Sample k of a segment with value v at brick position beta (Sec. 3: emission-absorption
+// compositing; Sec. 4: gradient shading), composited front to back into (C, Acc).
+// Returns true when early ray termination stops the ray at this sample.
+template <int ST, int INTERP, int SHADE>
+__device__ __forceinline__ bool composite_sample(const RenderArgs& A, const RayArgs& R,
+                                                 const float4* s_tf, const SegSetup& g,
+                                                 const DLevel& lv, int k, const float* beta,
+                                                 float v, float Lx, float Ly, float Lz,
+                                                 float& C0, float& C1, float& C2, float& Acc) {
+  const float4 c = tf_lookup(s_tf, A.tf_n, v, A.vmin, A.inv_range);
+  if (c.w <= 0.0f) return false;
+  float gr[3] = {0.0f, 0.0f, 0.0f};
+  if constexpr ((SHADE & 3) >= 1) gradient<ST, INTERP, ((SHADE & 3) == 2)>(A, R, g.s, beta, k, lv, gr);
+  return finish_sample<ST, SHADE>(A, R, s_tf, g, lv, beta, c, gr, Lx, Ly, Lz, C0, C1, C2, Acc);
+}
 
 template <int ST, int INTERP, int SHADE>
 __device__ __forceinline__ bool sample_one(const RenderArgs& A, const RayArgs& R,
@@ -1439,6 +1468,26 @@ __device__ __forceinline__ bool sample_one(const RenderArgs& A, const RayArgs& R
 #ifndef AMR_MAX_GROUP_SHADED
 #define AMR_MAX_GROUP_SHADED 4
 #endif
+
+// Sample k of a segment whose stencil maximum did not prove it transparent: its value
+// stencil, then composite_sample.  (Reading value and gradient together from the gradient
+// brick's cells for such samples measured 9 % slower on C2 at 2048^2 Phong: many of them
+// still map to zero opacity, and those then load 128 bytes instead of 32.)  Returns true
+// at early ray termination.
+template <int ST, int SHADE>
+__device__ __forceinline__ bool sample_candidate(const RenderArgs& A, const RayArgs& R,
+                                                 const float4* s_tf, const SegSetup& g,
+                                                 const DLevel& lv, int k, float Lx, float Ly,
+                                                 float Lz, float& C0, float& C1, float& C2,
+                                                 float& Acc) {
+  float beta[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
+  const Stencil<ST> st = stencil_at<ST>(g.s.brick, beta[0], beta[1], beta[2]);
+  const float v = stencil_value<ST>(A, g.s.brick, st);
+  return composite_sample<ST, 1, SHADE>(A, R, s_tf, g, lv, k, beta, v, Lx, Ly, Lz, C0, C1, C2,
+                                        Acc);
+}
 
 template <int ST, int SHADE, int G>
 __device__ __forceinline__ bool sample_segment_grouped(const RenderArgs& A, const RayArgs& R,
@@ -1476,13 +1525,8 @@ __device__ __forceinline__ bool sample_segment_grouped(const RenderArgs& A, cons
       auto one = [&](int k, float mk) -> int {  // 1: stop (early termination)
         ++nsamp;
         if (stencil_transparent(A, nz, mk)) return 0;  // opacity zero: nothing to composite
-        float beta[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) beta[a] = fmaf((float)k, g.db[a], g.b0[a]);
-        const Stencil<ST> st = stencil_at<ST>(g.s.brick, beta[0], beta[1], beta[2]);
-        const float v = stencil_value<ST>(A, g.s.brick, st);
-        return composite_sample<ST, 1, SHADE>(A, R, s_tf, g, lv, k, beta, v, Lx, Ly, Lz, C0, C1,
-                                              C2, Acc) ? 1 : 0;
+        return sample_candidate<ST, SHADE>(A, R, s_tf, g, lv, k, Lx, Ly, Lz, C0, C1, C2, Acc)
+                   ? 1 : 0;
       };
       if constexpr ((SHADE & 3) == 0) {
 #pragma unroll
