@@ -156,3 +156,25 @@ def test_maxbrick_learned_march_bit_identical(amr, c1):
         ia, na = gpu_render(a, w["camera"], w["tf"], p)
         ib, nb = gpu_render(b, w["camera"], w["tf"], p)
         assert na == nb and np.array_equal(ia, ib), (mode, tau)
+
+
+@pytest.mark.parametrize("gradient", [False, True])
+def test_maxbrick_every_sample_opaque_bit_identical(amr, c1, gradient):
+    # every sample opaque (a transfer function with non-zero opacity everywhere, no early
+    # termination): the stencil-maximum test never proves a sample transparent, and the
+    # image and the sample count equal those of the per-ray loop without the bricks bit
+    # for bit
+    w, o = c1
+    tf = np.array(synth.ramp_tf(), dtype=np.float64)
+    tf[:, 3] = 0.02 + 0.05 * np.linspace(0.0, 1.0, tf.shape[0])
+    tf = tf.astype(np.float32)
+    a, b = amr.from_hierarchy(w["hier"]), amr.from_hierarchy(w["hier"])
+    a.amr_build_kdtree("ptr", gradient=gradient, halo=2)
+    b.amr_build_kdtree("ptr", gradient=gradient, halo=2, maxbrick=True)
+    cam = synth.orbit_camera(5, 128, 96)
+    p, op = params_pair(amr, w["vmin"], w["vmax"], shade=1, schedule=0, ert_eps=0.0)
+    ia, na = gpu_render(a, cam, tf, p)
+    ib, nb = gpu_render(b, cam, tf, p)
+    assert na == nb and np.array_equal(ia, ib)
+    ref, _ = o.render(cam, tf, op)
+    assert_image_close(ib, ref, what="every sample opaque")
