@@ -4,7 +4,8 @@
 // a view).  Every block pops a tile with one atomic, builds that view's ray arguments in
 // shared memory and marches the tile's pixels with the same per-pixel code as the
 // single-view kernel, so each view's image is bit-identical to its own amr_render.  Up to
-// eight transfer functions are staged in shared memory once per block.  With schedule 3
+// eight transfer functions are read from global memory (L1-cached); their prefix counts of
+// non-transparent entries are staged in shared memory once per block.  With schedule 3
 // each warp marches its rays with the deferred-shading loop instead of the per-ray loop.
 // The view table travels in the kernel's parameter block, so a call is one memset and one
 // launch and can be captured in a CUDA graph.  The paper renders one view per pass; batching is an
@@ -26,25 +27,24 @@ __global__ void __launch_bounds__(TW * TH,
                                   (128 * (DEFER ? AMR_MIN_BLOCKS_DEFERRED : kMinBlocks<SHADE>)) /
                                       (TW * TH))
     batch_kernel(const __grid_constant__ BatchArgs B) {
-  constexpr int NT = TW * TH;
   const RenderArgs& A = B.A;
   extern __shared__ float4 smem[];
   const int tf_n = A.tf_n;
-  float4* s_tf = smem;                                             // [n_tf][tf_n]
-  int* s_nz = reinterpret_cast<int*>(smem + B.n_tf * tf_n);        // [n_tf][tf_n + 1]
+  // the transfer functions are read where they are (global memory, cached in L1): staging
+  // all of them in every block took up to 160 KB of an SM's shared memory away from the
+  // L1 cache that serves the brick reads; only their prefix counts are staged
+  int* s_nz = reinterpret_cast<int*>(smem);                        // [n_tf][tf_n + 1]
   __shared__ RayArgs s_ray;
   __shared__ int s_item, s_tf_idx, s_w, s_h, s_item0, s_tiles_x;
   __shared__ long long s_out;
   const int tid = threadIdx.x + TW * threadIdx.y;
-  for (int k = tid; k < B.n_tf * tf_n; k += NT) s_tf[k] = A.tf[k];
-  __syncthreads();
   if (tid < B.n_tf) {
     int acc = 0;
     int* nz = s_nz + tid * (tf_n + 1);
-    const float4* tf = s_tf + tid * tf_n;
+    const float4* tf = A.tf + tid * tf_n;
     nz[0] = 0;
     for (int k = 0; k < tf_n; ++k) {
-      acc += tf[k].w != 0.0f ? 1 : 0;
+      acc += __ldg(&tf[k].w) != 0.0f ? 1 : 0;
       nz[k + 1] = acc;
     }
   }
@@ -97,15 +97,14 @@ __global__ void __launch_bounds__(TW * TH,
     const int tx = t % s_tiles_x, ty = t / s_tiles_x;
     const int W = s_w, H = s_h;
     const int i = tx * TW + (int)threadIdx.x;
-    const float4* tf = s_tf + s_tf_idx * tf_n;
+    const float4* tf = A.tf + s_tf_idx * tf_n;
     const int* nz = s_nz + s_tf_idx * (tf_n + 1);
     float4* out = A.out + s_out;
     for (int r = 0; r < rpt; ++r) {
       const int j = (ty * rpt + r) * TH + (int)threadIdx.y;
       if constexpr (DEFER) {
         // every lane of the warp takes part, with or without a pixel
-        const size_t nz_bytes = (size_t)B.n_tf * (tf_n + 1) * sizeof(int);
-        const size_t area = ((size_t)B.n_tf * tf_n * sizeof(float4) + nz_bytes + 15) & ~(size_t)15;
+        const size_t area = ((size_t)B.n_tf * (tf_n + 1) * sizeof(int) + 15) & ~(size_t)15;
         DeferArea& Q = reinterpret_cast<DeferArea*>(reinterpret_cast<char*>(smem) + area)[tid >> 5];
         const bool act = i < W && j < H;
         const float4 c = march_deferred<ST, SHADE>(A, s_ray, i, j, act, tf, nz, Q, nsamp, status);
@@ -125,8 +124,7 @@ __global__ void __launch_bounds__(TW * TH,
 template <int ST, int SHADE, int TW, int TH, bool DEFER>
 amr_status launch_shape(amr_ctx* c, const BatchArgs& b, int blocks_per_sm, cudaStream_t s) {
   auto k = batch_kernel<ST, SHADE, TW, TH, DEFER>;
-  size_t smem = (size_t)b.n_tf * b.A.tf_n * (sizeof(float4) + sizeof(int)) +
-                (size_t)b.n_tf * sizeof(int);
+  size_t smem = (size_t)b.n_tf * (b.A.tf_n + 1) * sizeof(int);
   if (DEFER) smem = ((smem + 15) & ~(size_t)15) + (TW * TH / 32) * sizeof(DeferArea);
   cudaError_t e = cudaSuccess;
   if (smem > 48 * 1024)
