@@ -13,8 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "ctx.h"
-#include "march.cuh"
-#include "march_deferred.cuh"
+#include "march_launch.cuh"
 
 namespace amr {
 
@@ -124,15 +123,16 @@ __global__ void __launch_bounds__(TW * TH,
 template <int ST, int SHADE, int TW, int TH, bool DEFER>
 amr_status launch_shape(amr_ctx* c, const BatchArgs& b, int blocks_per_sm, cudaStream_t s) {
   auto k = batch_kernel<ST, SHADE, TW, TH, DEFER>;
+  constexpr int kThreads = TW * TH;
   size_t smem = (size_t)b.n_tf * (b.A.tf_n + 1) * sizeof(int);
-  if (DEFER) smem = ((smem + 15) & ~(size_t)15) + (TW * TH / 32) * sizeof(DeferArea);
+  if (DEFER) smem = ((smem + 15) & ~(size_t)15) + (kThreads / 32) * sizeof(DeferArea);
   cudaError_t e = cudaSuccess;
   if (smem > 48 * 1024)
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, sms = 0, occ = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, TW * TH, smem);
+  if (e == cudaSuccess) e = fit_carveout(k, smem, kThreads, occ);
   if (e != cudaSuccess) return fail(c, AMR_ERR_CUDA, std::string("batch launch setup: ") + cudaGetErrorString(e));
   const int per_sm = blocks_per_sm > 0 ? std::min(blocks_per_sm, std::max(occ, 1)) : std::max(occ, 1);
   const int grid = std::max(1, std::min(sms * per_sm, b.n_items));
