@@ -27,8 +27,11 @@ cudaError_t fit_carveout(K kernel, size_t smem, int threads, int& occ) {
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
   if (e != cudaSuccess || occ <= 0 || max_smem <= 0) return e;
-  const long long need = (long long)occ * ((long long)smem + reserved);
+  // a block's shared memory: the dynamic part, the kernel's static arrays, the reserve
+  const long long need = (long long)occ * ((long long)smem + (long long)fa.sharedSizeBytes + reserved);
   const int pct = (int)std::min(100LL, (need * 100 + max_smem - 1) / max_smem);
   return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
