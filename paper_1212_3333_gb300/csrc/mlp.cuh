@@ -107,8 +107,15 @@ __device__ __forceinline__ void mlp_relu_pack(const float (&acc)[2][8][4], uint3
 // Warp-cooperative forward pass.  xs: this warp's staging rows in shared memory,
 // [32][kStride1] bf16, row r = the features of lane r (zero-padded to 16).  All 32 lanes
 // must call it together.  Returns the prediction for the calling lane's row.
-__device__ __forceinline__ float mlp_forward_warp(const unsigned char* wsm,
-                                                  const __nv_bfloat16* xs, float* ys, int lane) {
+// An out-of-line call: the pass's accumulator and fragment registers are live only inside
+// it, so the learned march around it keeps its ray state in registers (spills 60 -> 16
+// bytes per thread; 8 held-out C2 2048^2 views, coarse16 at tau 1e-2: 160.2 -> 154.5 ms).
+// Its 152 mma.sync per 32 rows are the bound: about 500 SM cycles per call at full
+// throughput (B fragments by ldmatrix instead of 32-bit loads: 526 -> 501, no gain in the
+// march).
+static __device__ __noinline__ float mlp_forward_warp(const unsigned char* wsm,
+                                                      const __nv_bfloat16* xs, float* ys,
+                                                      int lane) {
   const int g = lane >> 2, t = lane & 3;
   const float* bias = reinterpret_cast<const float*>(wsm + kPackB);
   uint32_t a1[2][1][4];
