@@ -741,9 +741,10 @@ def main():
     bps = BYTES_PER_SAMPLE[args.shade] * CELL_BYTES[args.dtype] // 4
     variant = _variant(args.storage, bool(args.gradient), args.dtype, args.halo,
                        bool(args.maxbrick) and args.storage == "ptr")
-    # the march is bound by neither HBM nor any throughput unit (ncu: L1 about a third of
-    # its peak, issue slots under half busy, a third of the lanes active): the roofline is
-    # the one its gathers would hit first, L1, with SURVEY's algorithmic stencil bytes
+    # the march is bound by neither HBM nor any throughput unit (ncu: L1 data pipe at a
+    # fifth of its peak, issue slots half busy, under half of the lanes active): the
+    # roofline is the one its gathers would hit first, L1, with the algorithmic stencil
+    # bytes (8 cells per trilinear sample, 7 stencils with central-difference shading)
     stencil = samples * bps / (kern_ms * 1e-3) / 1e9
     l1_peak, l1_kind = _l1_peak_gbs(clk["sm_mhz"] if clk else None)
     prof = _profiled_counters(args.shade, variant, size, args.schedule)
