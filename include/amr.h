@@ -316,6 +316,8 @@ amr_status amr_batch_autotune(amr_ctx* ctx, const amr_view* views, int32_t n_vie
 #define AMR_MLP_PARAMS 9217      /* W1[64][12] b1[64] W2[64][64] b2[64] W3[64][64] b3[64]
                                     W4[1][64] b4[1], FP32, W[out][in] row-major */
 #define AMR_MLP_PACKED_BYTES 23440 /* inference image: BF16 weights, padded rows, FP32 biases */
+#define AMR_MLP_GRAD_BLOCKS 152    /* blocks of the gradient pass (at most) */
+#define AMR_MLP_GRAD_SCRATCH (AMR_MLP_GRAD_BLOCKS * (AMR_MLP_PARAMS + 1)) /* floats */
 
 /* Record training data: the plain march of one view (no early termination) writes, for each
  * segment a seeded hash keeps with probability keep_prob, its 12 features to
@@ -344,10 +346,16 @@ amr_status amr_mlp_forward(const void* packed_dev, const float* x_dev, int64_t n
  * t_dev[n_total]; with perm_a coprime to n_total, consecutive batches walk a pseudo-random
  * permutation (perm_a = 1, perm_b = 0: rows first .. first + n - 1).  The forward rounds
  * weights and activations to BF16 as inference does; the backward is FP32.  Overwrites
- * grad_dev and loss_dev[0].  Asynchronous.  Limits: n_total, perm_a < 2^31. */
+ * grad_dev and loss_dev[0].  scratch_dev: caller-owned device buffer of AMR_MLP_GRAD_SCRATCH
+ * floats (no contents expected; overwritten) holding each block's partial sums, which a
+ * second kernel adds in a fixed order: the same inputs give the same gradient and loss bit
+ * for bit.  A scratch buffer must not be shared by calls in flight on different streams.
+ * Asynchronous.  Limits: n_total, perm_a < 2^31.  Errors: AMR_ERR_ARG (a null pointer, n or
+ * n_total not positive, limits), AMR_ERR_CUDA; amr_last_error(NULL). */
 amr_status amr_mlp_loss_grad(const float* params_dev, const float* x_dev, const float* t_dev,
                              int64_t n_total, int64_t first, int64_t n, int64_t perm_a,
-                             int64_t perm_b, float* grad_dev, float* loss_dev, void* cuda_stream);
+                             int64_t perm_b, float* grad_dev, float* loss_dev, float* scratch_dev,
+                             void* cuda_stream);
 
 /* One Adam step (bias-corrected, step >= 1) on the AMR_MLP_PARAMS FP32 parameters. */
 amr_status amr_mlp_adam(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev,

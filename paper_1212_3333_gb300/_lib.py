@@ -25,6 +25,8 @@ AMR_STORE_GRADIENT = 0x100
 AMR_STORE_HALO2 = 0x200
 AMR_STORE_MAXBRICK = 0x400
 AMR_MLP_FEATURES, AMR_MLP_PARAMS, AMR_MLP_PACKED_BYTES = 12, 9217, 23440
+AMR_MLP_GRAD_BLOCKS = 152
+AMR_MLP_GRAD_SCRATCH = AMR_MLP_GRAD_BLOCKS * (AMR_MLP_PARAMS + 1)
 STORAGES = {"ptr": AMR_STORE_PTR, "texobj": AMR_STORE_TEXOBJ,
             "atlas_linear": AMR_STORE_ATLAS_LINEAR, "atlas_tex3d": AMR_STORE_ATLAS_TEX3D}
 
@@ -103,7 +105,7 @@ _SIGS = {
     "amr_mlp_pack": (C.c_int, [_P, _P, _P]),
     "amr_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
     "amr_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
-                                    C.c_int64, _P, _P, _P]),
+                                    C.c_int64, _P, _P, _P, _P]),
     "amr_mlp_adam": (C.c_int, [_P, _P, _P, _P, C.c_float, C.c_float, C.c_float, C.c_float,
                                C.c_int32, _P]),
     "amr_set_proposal": (C.c_int, [_P, _P, _P]),

@@ -83,8 +83,8 @@ constexpr size_t kGradSmem =
 __global__ void __launch_bounds__(kGradThreads, 1)
     grad_kernel(const float* __restrict__ params, const float* __restrict__ x,
                 const float* __restrict__ tgt, int64_t n_total, int64_t first, int64_t n,
-                int64_t perm_a, int64_t perm_b, float* __restrict__ grad,
-                float* __restrict__ loss_out) {
+                int64_t perm_a, int64_t perm_b, float* __restrict__ partial,
+                float* __restrict__ loss_part) {
   extern __shared__ __align__(16) float fs[];
   float* W = fs;                                        // BF16-rounded weights, FP32 biases
   float* A1 = W + kMlpParams;
@@ -217,13 +217,38 @@ __global__ void __launch_bounds__(kGradThreads, 1)
     }
     __syncthreads();
   }
+  // this block's partial sums, reduced over the blocks in a fixed order by reduce_kernel
+  // (no atomics: the gradient is the same bit for bit on every call)
+  float* part = partial + (size_t)blockIdx.x * kMlpParams;
 #pragma unroll
   for (int j = 0; j < kOwn; ++j) {
     const int k = tid + kGradThreads * j;
-    if (k < kMlpParams && g[j] != 0.0f) atomicAdd(grad + k, g[j]);
+    if (k < kMlpParams) part[k] = g[j];
   }
   for (int off = 16; off > 0; off >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, off);
-  if ((tid & 31) == 0 && loss != 0.0f) atomicAdd(loss_out, loss * inv_n);
+  __shared__ float wl[kGradThreads / 32];
+  if ((tid & 31) == 0) wl[tid >> 5] = loss;
+  __syncthreads();
+  if (tid == 0) {
+    float s = 0.0f;
+    for (int w = 0; w < kGradThreads / 32; ++w) s += wl[w];
+    loss_part[blockIdx.x] = s * inv_n;
+  }
+}
+
+// grad[k] = sum of the blocks' partials in block order; loss likewise (thread kMlpParams).
+__global__ void reduce_kernel(const float* __restrict__ partial, const float* __restrict__ loss_part,
+                              int blocks, float* __restrict__ grad, float* __restrict__ loss) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < kMlpParams) {
+    float s = 0.0f;
+    for (int b = 0; b < blocks; ++b) s += partial[(size_t)b * kMlpParams + k];
+    grad[k] = s;
+  } else if (k == kMlpParams) {
+    float s = 0.0f;
+    for (int b = 0; b < blocks; ++b) s += loss_part[b];
+    loss[0] = s;
+  }
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
@@ -281,23 +306,26 @@ amr_status amr_mlp_forward(const void* packed_dev, const float* x_dev, int64_t n
 
 amr_status amr_mlp_loss_grad(const float* params_dev, const float* x_dev, const float* t_dev,
                              int64_t n_total, int64_t first, int64_t n, int64_t perm_a,
-                             int64_t perm_b, float* grad_dev, float* loss_dev, void* stream) {
-  if (!params_dev || !x_dev || !t_dev || !grad_dev || !loss_dev || n <= 0 || n_total <= 0 ||
+                             int64_t perm_b, float* grad_dev, float* loss_dev, float* scratch_dev,
+                             void* stream) {
+  if (!params_dev || !x_dev || !t_dev || !grad_dev || !loss_dev || !scratch_dev || n <= 0 ||
+      n_total <= 0 ||
       first < 0 || perm_a <= 0 || perm_b < 0 || perm_a >= ((int64_t)1 << 31) ||
       n_total >= ((int64_t)1 << 31) || first + n >= ((int64_t)1 << 32))
     return mlp_fail(AMR_ERR_ARG, "bad MLP gradient arguments");
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemsetAsync(grad_dev, 0, kMlpParams * sizeof(float), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(loss_dev, 0, sizeof(float), st);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kGradSmem);
+  cudaError_t e = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kGradSmem);
   if (e != cudaSuccess) return mlp_fail(AMR_ERR_CUDA, cudaGetErrorString(e));
   const int64_t tiles = (n + kGradThreads - 1) / kGradThreads;
-  const int blocks = (int)std::min<int64_t>(tiles, 152);
+  const int blocks = (int)std::min<int64_t>(tiles, AMR_MLP_GRAD_BLOCKS);
+  float* partial = scratch_dev;                                        // [blocks][params]
+  float* loss_part = scratch_dev + (size_t)AMR_MLP_GRAD_BLOCKS * kMlpParams;  // [blocks]
   grad_kernel<<<blocks, kGradThreads, kGradSmem, st>>>(params_dev, x_dev, t_dev, n_total, first,
-                                                       n, perm_a, perm_b % n_total, grad_dev,
-                                                       loss_dev);
+                                                       n, perm_a, perm_b % n_total, partial,
+                                                       loss_part);
+  reduce_kernel<<<(kMlpParams + 1 + 255) / 256, 256, 0, st>>>(partial, loss_part, blocks, grad_dev,
+                                                             loss_dev);
   e = cudaGetLastError();
   return e == cudaSuccess ? AMR_OK : mlp_fail(AMR_ERR_CUDA, cudaGetErrorString(e));
 }

@@ -80,6 +80,9 @@ class Proposal:
         self.v = torch.zeros_like(self.params)
         self.grad = torch.zeros_like(self.params)
         self.loss = torch.zeros((1,), dtype=torch.float32, device="cuda")
+        # per-block partial sums of the gradient pass (reduced in a fixed order)
+        self.scratch = torch.empty((_lib.AMR_MLP_GRAD_SCRATCH,), dtype=torch.float32,
+                                   device="cuda")
         # 16-byte aligned buffer for the packed inference image
         self.packed = torch.zeros((_lib.AMR_MLP_PACKED_BYTES // 4,), dtype=torch.float32,
                                   device="cuda")
@@ -93,7 +96,8 @@ class Proposal:
         st = self._lib.amr_mlp_loss_grad(
             C.c_void_p(_dptr(self.params)), C.c_void_p(_dptr(x)), C.c_void_p(_dptr(t)), N,
             int(first), n, int(perm_a), int(perm_b), C.c_void_p(_dptr(self.grad)),
-            C.c_void_p(_dptr(self.loss)), C.c_void_p(_stream_ptr(stream)))
+            C.c_void_p(_dptr(self.loss)), C.c_void_p(_dptr(self.scratch)),
+            C.c_void_p(_stream_ptr(stream)))
         _check(st, None)
 
     def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
