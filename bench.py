@@ -211,8 +211,8 @@ def learned_eval(amr, ctx, hier, vmin, vmax, tf, args, taus=(1e-4, 1e-3, 1e-2)):
     """Learned segment proposal on the same hierarchy: log segments from 256 seeded poses
     (seeds 1000-1255), train the MLP with the library's kernels, then time held-out views
     (seeds 2000-2007) at the bench size: plain march, exact min/max skipping, and min/max +
-    learned skipping (and 16x / 64x coarser sampling) for each tau and each minimum segment
-    length the proposal is asked about, PSNR against the plain march."""
+    learned skipping (and 16x / 32x / 64x coarser sampling) for each tau and each minimum
+    segment length the proposal is asked about, PSNR against the plain march."""
     import torch
 
     import synth
@@ -247,11 +247,11 @@ def learned_eval(amr, ctx, hier, vmin, vmax, tf, args, taus=(1e-4, 1e-3, 1e-2)):
     base = dict(vmin=vmin, vmax=vmax, shade=args.shade, ert_eps=args.ert)
     configs = {"plain": {}, "minmax": {"skip": 1}}
     # the proposal is asked about segments of at least m samples (m1: every segment)
-    for m in (1, 8, 32):
+    for m in (1, 8):
         for tau in taus:
             configs[f"skip@{tau:g}/m{m}"] = {"skip": 1, "learned": 1, "tau": tau,
                                              "learned_min_samples": m}
-            for cf in (16, 64):
+            for cf in (16, 32, 64):
                 configs[f"coarse{cf}@{tau:g}/m{m}"] = {"skip": 1, "learned": 2, "tau": tau,
                                                        "coarse_factor": cf,
                                                        "learned_min_samples": m}
