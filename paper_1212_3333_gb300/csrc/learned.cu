@@ -1,7 +1,7 @@
 // Learned segment proposal fused into the ray march, and the segment log it is trained on.
 // The paper has no counterpart; the march itself is Sec. 3.3 as in march.cuh.
 //
-// learned_kernel gives each warp an 8x4 pixel tile and marches the tile's rays in rounds,
+// learned_kernel gives each warp a 4x8 pixel tile and marches the tile's rays in rounds,
 // so that the warp is converged at segment boundaries: every live lane descends to its
 // ray's next segment, drops it if exact min/max skipping proves it transparent, and stages
 // its 12 features; when some lane's segment has at least learned_min_samples samples the
@@ -129,6 +129,12 @@ __device__ __forceinline__ bool sample_learned(const RenderArgs& A, const float4
                                         nsamp);
 }
 
+#ifndef AMR_LEARNED_TILE_W
+#define AMR_LEARNED_TILE_W 4  // pixel tile of one warp: AMR_LEARNED_TILE_W x (32 / it)
+#endif
+static_assert(AMR_LEARNED_TILE_W == 2 || AMR_LEARNED_TILE_W == 4 || AMR_LEARNED_TILE_W == 8 ||
+                  AMR_LEARNED_TILE_W == 16,
+              "learned tile width");
 template <int ST, int SHADE>
 __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __grid_constant__ RenderArgs A) {
   extern __shared__ float4 smem[];
@@ -156,14 +162,17 @@ __global__ void __launch_bounds__(128, AMR_MIN_BLOCKS) learned_kernel(const __gr
 
   unsigned nsamp = 0;
   unsigned long long status = 0;
-  // one 8x4 pixel tile per warp (persistent warps over a tile queue measured slower here:
-  // 174 against 160 ms for 8 views of C2 at 2048^2, coarse16 at tau 1e-2)
-  const int tiles_x = (A.ray.width + 7) / 8;
-  const int n_tiles = tiles_x * ((A.ray.rows + 3) / 4);
+  // one pixel tile per warp (persistent warps over a tile queue measured slower here: 174
+  // against 160 ms for 8 views of C2 at 2048^2, coarse16 at tau 1e-2); tiles 4 wide and 8
+  // high keep a warp's rays together through the rounds better than 8 x 4 or 16 x 2
+  // (coarse32 at tau 1e-2: 133.8 / 142.2 / 162.1 ms)
+  constexpr int TW = AMR_LEARNED_TILE_W, TH = 32 / TW;
+  const int tiles_x = (A.ray.width + TW - 1) / TW;
+  const int n_tiles = tiles_x * ((A.ray.rows + TH - 1) / TH);
   const int t = (int)blockIdx.x * 4 + (tid >> 5);
   {
-    const int i = (t % tiles_x) * 8 + (lane & 7);
-    const int jr = (t / tiles_x) * 4 + (lane >> 3);
+    const int i = (t % tiles_x) * TW + lane % TW;
+    const int jr = (t / tiles_x) * TH + lane / TW;
     const int j = A.ray.row0 + jr;
     const bool active = t < n_tiles && i < A.ray.width && jr < A.ray.rows && j < A.ray.height;
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
@@ -263,7 +272,8 @@ size_t learned_smem(int tf_n) {
 
 amr_status launch_learned(amr_ctx* c, const RenderArgs& a, int storage, int shade, void* stream) {
   if (a.ray.width <= 0 || a.ray.rows <= 0) return AMR_OK;
-  const long long tiles = (long long)((a.ray.width + 7) / 8) * ((a.ray.rows + 3) / 4);
+  constexpr int TW = AMR_LEARNED_TILE_W, TH = 32 / TW;
+  const long long tiles = (long long)((a.ray.width + TW - 1) / TW) * ((a.ray.rows + TH - 1) / TH);
   const dim3 grid((unsigned)((tiles + 3) / 4)), block(8, 16);
   const size_t smem = learned_smem(a.tf_n);
   cudaStream_t s = (cudaStream_t)stream;
