@@ -44,6 +44,53 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def _header_functions():
+    """name -> parameter count of every function declared in include/amr.h."""
+    header = open(os.path.join(ROOT, "include", "amr.h")).read()
+    header = re.sub(r"/\*.*?\*/", " ", header, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(amr_[a-z_]+)\s*\(([^;{]*?)\)\s*;", header):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    # each ctypes signature passes as many arguments as the C declaration takes
+    decl = _header_functions()
+    for name, (_, args) in _lib._SIGS.items():
+        assert decl.get(name) == len(args), (name, decl.get(name), len(args))
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    # the binding's copies of the header's constants, read back from a C program that
+    # includes the header (enums and #defines alike)
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = ["AMR_OK", "AMR_ERR_ARG", "AMR_ERR_OVERLAP", "AMR_ERR_NOT_TILED", "AMR_ERR_STATE",
+             "AMR_ERR_OOM", "AMR_ERR_CUDA", "AMR_ERR_CAPACITY", "AMR_ERR_DEVICE", "AMR_F32",
+             "AMR_F16", "AMR_BF16", "AMR_STORE_PTR", "AMR_STORE_TEXOBJ",
+             "AMR_STORE_ATLAS_LINEAR", "AMR_STORE_ATLAS_TEX3D", "AMR_STORE_GRADIENT",
+             "AMR_STORE_HALO2", "AMR_STORE_MAXBRICK", "AMR_MLP_FEATURES", "AMR_MLP_PARAMS",
+             "AMR_MLP_PACKED_BYTES", "AMR_MLP_GRAD_BLOCKS", "AMR_MLP_GRAD_SCRATCH",
+             "AMR_MAX_BATCH_VIEWS", "AMR_SCHEDULE_AUTO", "AMR_BATCH_CANDIDATES"]
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "amr.h"\nint main(void) {\n' +
+                   "".join(f'  printf("%lld\\n", (long long)({n}));\n' for n in names) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "consts"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    for n, v in zip(names, got):
+        assert getattr(_lib, n) == v, (n, getattr(_lib, n), v)
+
+
 def test_tree_matches_oracle_c1():
     _tree_equal(synth.make_c1())
 
