@@ -157,6 +157,27 @@ def test_learned_render_with_zero_threshold_is_the_plain_march(mods, c1_learned)
     assert n == 0 and np.all(img == 0)
 
 
+@pytest.mark.parametrize("size", [(77, 53), (5, 9), (130, 31)])
+def test_learned_ragged_images_and_bands(mods, c1_learned, size):
+    # images whose sides are no multiple of the warp tile, and a band of rows: with tau = 0
+    # the learned march gives the plain march's pixels and sample count there too
+    torch, amr, proposal = mods
+    w, ctx = c1_learned
+    proposal.Proposal(seed=7).install(ctx)
+    W, H = size
+    cam = synth.orbit_camera(41, W, H)
+    p, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1)
+    plain, n_plain = gpu_render(ctx, cam, w["tf"], p)
+    pl, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1, learned=2, tau=0.0)
+    img, n = gpu_render(ctx, cam, w["tf"], pl)
+    assert np.array_equal(img, plain) and n == n_plain
+    if H > 6:
+        pb, _ = params_pair(amr, w["vmin"], w["vmax"], shade=1, learned=2, tau=0.0, row0=3,
+                            rows=H - 5)
+        band, _ = gpu_render(ctx, cam, w["tf"], pb)
+        assert np.array_equal(band, plain[3:H - 2])
+
+
 def test_learned_proposal_trains_and_keeps_psnr(mods, c1_learned):
     torch, amr, proposal = mods
     w, ctx = c1_learned
