@@ -94,7 +94,7 @@ __device__ __forceinline__ float3 shade_task(const RenderArgs& A, const RayArgs&
 // Returns premultiplied RGBA (zero for inactive lanes); adds to nsamp and status.
 // samples whose stencil maxima the deferred loop loads together (stencil-maximum bricks)
 #ifndef AMR_DEFER_GROUP
-#define AMR_DEFER_GROUP 4
+#define AMR_DEFER_GROUP 8
 #endif
 constexpr int kDeferGroup = AMR_DEFER_GROUP;
 
