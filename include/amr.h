@@ -321,10 +321,15 @@ amr_status amr_batch_autotune(amr_ctx* ctx, const amr_view* views, int32_t n_vie
 
 /* Record training data: the plain march of one view (no early termination) writes, for each
  * segment a seeded hash keeps with probability keep_prob, its 12 features to
- * features_dev[k*12 ..] and its contribution A_out - A_in to targets_dev[k], where
- * k = atomicAdd(count_dev, 1) (caller zeroes *count_dev; records with k >= capacity are
- * dropped but still counted).  Storage must be ptr or atlas_linear with FP32 cells.
- * Asynchronous. */
+ * features_dev[k*12 ..] and its contribution A_out - A_in to targets_dev[k].  Records follow
+ * pixel order (row-major within the view's rows), then segment order along the ray, and k
+ * continues from *count_dev, which grows by the view's record count (the caller zeroes it
+ * before the first view; records with k >= capacity are dropped but still counted): the
+ * same views give the same records in the same places.  A first pass counts each pixel's
+ * records into per-pixel buffers the context keeps (allocated on first use, grown for
+ * larger views); calls on one context must therefore be ordered (one stream).  Storage must
+ * be ptr or atlas_linear with FP32 cells.  Asynchronous.  Errors: AMR_ERR_ARG, AMR_ERR_OOM,
+ * AMR_ERR_CUDA. */
 amr_status amr_log_segments(amr_ctx* ctx, const amr_camera* cam, const float* tf_rgba_dev,
                             int32_t tf_n, const amr_render_params* params, float* features_dev,
                             float* targets_dev, int64_t capacity, unsigned long long* count_dev,

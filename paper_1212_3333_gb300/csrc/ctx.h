@@ -76,6 +76,9 @@ struct DeviceState {
   float4* tf_scratch = nullptr;                  // staging for amr_render_host
   int tf_scratch_n = 0;
   float4* img_scratch = nullptr;
+  int32_t* log_counts = nullptr;                 // segment log: kept records per pixel
+  unsigned long long* log_offsets = nullptr;     //   and each pixel's first record
+  size_t log_pixels = 0;                         //   capacity of both, pixels
   unsigned char* proposal = nullptr;             // packed MLP weights (amr_set_proposal)
   size_t img_scratch_bytes = 0;
   int32_t* lod = nullptr;                        // per node slot: (id << 5 | level) or -1

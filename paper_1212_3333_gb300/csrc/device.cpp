@@ -293,6 +293,8 @@ void release_device(amr_ctx* c) {
   cudaFree(d.tf_scratch);
   cudaFree(d.proposal);
   cudaFree(d.img_scratch);
+  cudaFree(d.log_counts);
+  cudaFree(d.log_offsets);
   d = DeviceState();
   c->device_built = false;
 }

@@ -53,22 +53,41 @@ struct LogArgs {
   unsigned long long* count;    // running record count (may exceed cap: records dropped)
   float keep_prob;
   uint32_t seed;
+  int32_t* counts;              // per pixel of the view: records it keeps (count pass)
+  const unsigned long long* offsets;  // per pixel: index of its first record (write pass)
 };
 
-template <int ST>
+// Whether segment seg of pixel (i, j) is logged: a seeded hash, independent of the march.
+__device__ __forceinline__ bool log_keep(const LogArgs& L, int i, int j, int seg) {
+  const uint32_t h = mix32((uint32_t)i * 0x9E3779B1u ^ mix32((uint32_t)j + L.seed * 0x85EBCA77u) ^
+                           ((uint32_t)seg * 0xC2B2AE3Du));
+  return (float)(h >> 8) * (1.0f / 16777216.0f) < L.keep_prob;
+}
+
+// WRITE = false: count the records each pixel keeps (the segments alone, no sampling);
+// WRITE = true: the march, each kept record written at its pixel's offset, so the records
+// of a view follow pixel and segment order whatever the thread schedule.
+template <int ST, bool WRITE>
 __global__ void __launch_bounds__(128) log_kernel(const __grid_constant__ RenderArgs A,
                                                   const LogArgs L) {
   extern __shared__ float4 smem[];
   float4* s_tf = smem;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  for (int k = tid; k < A.tf_n; k += blockDim.x * blockDim.y) s_tf[k] = A.tf[k];
-  __syncthreads();
+  if constexpr (WRITE) {
+    for (int k = tid; k < A.tf_n; k += blockDim.x * blockDim.y) s_tf[k] = A.tf[k];
+    __syncthreads();
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int jr = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = A.ray.row0 + jr;
   if (i >= A.ray.width || jr >= A.ray.rows || j >= A.ray.height) return;
+  const size_t pix = (size_t)jr * A.ray.width + i;
+  int kept = 0;
   RayX rx;
-  if (!make_ray(A.ray, i, j, rx)) return;
+  if (!make_ray(A.ray, i, j, rx)) {
+    if constexpr (!WRITE) L.counts[pix] = 0;
+    return;
+  }
   RayF rf;
   make_frame(A.ray, rx, rf);
   float C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
@@ -84,29 +103,65 @@ __global__ void __launch_bounds__(128) log_kernel(const __grid_constant__ Render
                               prev, pid0, tau0, e0, pid1, tau1, e1);
     if (lid < 0) break;
     prev = lid;
-    const DLeaf lf = A.leaves[lid];
-    const DLevel& lv = A.lv[lf.level];
-    int n = min(segment_count(A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv),
-                kMaxSamplesPerSegment);
-    float f[kMlpIn];
-    segment_features(A, rf, tau0, tau1, lf, Acc, f);
-    const float a_in = Acc;
-    SegSetup g;
-    setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
-    sample_segment<ST, 1, 0>(A, A.ray, s_tf, nullptr, g, lv, 0.f, 0.f, 0.f, C0, C1, C2, Acc, nsamp);
-    const uint32_t h = mix32((uint32_t)i * 0x9E3779B1u ^ mix32((uint32_t)j + L.seed * 0x85EBCA77u) ^
-                             ((uint32_t)seg * 0xC2B2AE3Du));
-    if ((float)(h >> 8) * (1.0f / 16777216.0f) < L.keep_prob) {
-      const unsigned long long idx = atomicAdd(L.count, 1ull);
-      if ((long long)idx < L.cap) {
+    if constexpr (WRITE) {
+      const DLeaf lf = A.leaves[lid];
+      const DLevel& lv = A.lv[lf.level];
+      int n = min(segment_count(A.ray, i, j, rf, pid0, tau0, e0, pid1, tau1, e1, lv),
+                  kMaxSamplesPerSegment);
+      float f[kMlpIn];
+      segment_features(A, rf, tau0, tau1, lf, Acc, f);
+      const float a_in = Acc;
+      SegSetup g;
+      setup_segment(A, rf, lf, lv, lid, pid0, pid1, tau0, e0, tau1, e1, n, i, j, g);
+      sample_segment<ST, 1, 0>(A, A.ray, s_tf, nullptr, g, lv, 0.f, 0.f, 0.f, C0, C1, C2, Acc,
+                               nsamp);
+      if (log_keep(L, i, j, seg)) {
+        const unsigned long long idx = L.offsets[pix] + (unsigned long long)kept++;
+        if ((long long)idx < L.cap) {
 #pragma unroll
-        for (int k = 0; k < kMlpIn; ++k) L.features[idx * kMlpIn + k] = f[k];
-        L.targets[idx] = Acc - a_in;
+          for (int k = 0; k < kMlpIn; ++k) L.features[idx * kMlpIn + k] = f[k];
+          L.targets[idx] = Acc - a_in;
+        }
       }
+    } else if (log_keep(L, i, j, seg)) {
+      ++kept;
     }
     pid0 = pid1;
     tau0 = tau1;
     e0 = e1;
+  }
+  if constexpr (!WRITE) L.counts[pix] = kept;
+}
+
+// Exclusive prefix sums of the view's per-pixel record counts, starting at the running
+// record count, which then grows by the view's total (one block of 1024 threads, each
+// summing a contiguous chunk).
+__global__ void __launch_bounds__(1024) log_scan_kernel(const int32_t* __restrict__ counts,
+                                                        long long n,
+                                                        unsigned long long* __restrict__ offsets,
+                                                        unsigned long long* __restrict__ count) {
+  __shared__ unsigned long long part[1024];
+  const int t = threadIdx.x;
+  const long long chunk = (n + 1023) / 1024;
+  const long long lo = min(n, (long long)t * chunk), hi = min(n, lo + chunk);
+  unsigned long long s = 0;
+  for (long long k = lo; k < hi; ++k) s += (unsigned long long)counts[k];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long run = *count;
+    for (int q = 0; q < 1024; ++q) {
+      const unsigned long long v = part[q];
+      part[q] = run;
+      run += v;
+    }
+    *count = run;
+  }
+  __syncthreads();
+  unsigned long long run = part[t];
+  for (long long k = lo; k < hi; ++k) {
+    offsets[k] = run;
+    run += (unsigned long long)counts[k];
   }
 }
 
@@ -306,12 +361,34 @@ amr_status launch_log(amr_ctx* c, const RenderArgs& a, int storage, float* featu
   const dim3 block(8, 16);
   const dim3 grid((unsigned)((a.ray.width + 7) / 8), (unsigned)((a.ray.rows + 15) / 16));
   if (grid.x == 0 || grid.y == 0) return AMR_OK;
-  LogArgs L{features, targets, cap, count, keep_prob, seed};
+  if (storage != ST_PTR && storage != ST_ATLAS_LINEAR)
+    return fail(c, AMR_ERR_ARG, "segment logging needs the ptr or atlas_linear storage");
+  // per-pixel counts and offsets of the view (grown as needed, kept with the context)
+  const size_t pixels = (size_t)a.ray.width * (size_t)a.ray.rows;
+  DeviceState& d = c->dev;
+  if (pixels > d.log_pixels) {
+    cudaFree(d.log_counts);
+    cudaFree(d.log_offsets);
+    d.log_counts = nullptr;
+    d.log_offsets = nullptr;
+    d.log_pixels = 0;
+    if (cudaMalloc(&d.log_counts, pixels * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&d.log_offsets, pixels * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(d.log_counts);
+      d.log_counts = nullptr;
+      return fail(c, AMR_ERR_OOM, "segment log: per-pixel counts");
+    }
+    d.log_pixels = pixels;
+  }
+  LogArgs L{features, targets, cap, count, keep_prob, seed, d.log_counts, d.log_offsets};
   const size_t smem = (size_t)a.tf_n * sizeof(float4);
   cudaStream_t s = (cudaStream_t)stream;
-  if (storage == ST_PTR) log_kernel<ST_PTR><<<grid, block, smem, s>>>(a, L);
-  else if (storage == ST_ATLAS_LINEAR) log_kernel<ST_ATLAS_LINEAR><<<grid, block, smem, s>>>(a, L);
-  else return fail(c, AMR_ERR_ARG, "segment logging needs the ptr or atlas_linear storage");
+  if (storage == ST_PTR) log_kernel<ST_PTR, false><<<grid, block, 0, s>>>(a, L);
+  else log_kernel<ST_ATLAS_LINEAR, false><<<grid, block, 0, s>>>(a, L);
+  log_scan_kernel<<<1, 1024, 0, s>>>(d.log_counts, (long long)pixels, d.log_offsets, count);
+  if (storage == ST_PTR) log_kernel<ST_PTR, true><<<grid, block, smem, s>>>(a, L);
+  else log_kernel<ST_ATLAS_LINEAR, true><<<grid, block, smem, s>>>(a, L);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
     return fail(c, AMR_ERR_CUDA, std::string("segment log launch: ") + cudaGetErrorString(e));

@@ -127,6 +127,16 @@ def test_segment_log_invariants(mods, c1_learned):
     # the contributions of a ray's segments add up to its opacity
     img, _ = gpu_render(ctx, cam, w["tf"], p)
     assert abs(float(tgts.double().sum()) - img[..., 3].sum()) <= 1e-4 * img[..., 3].sum()
+    # records follow pixel order, then segment order: each pixel's records are its segments,
+    # contiguous, and their contributions add up to that pixel's opacity
+    counts = np.maximum(ln, 0).astype(np.int64)
+    starts = (np.cumsum(counts) - counts)[counts > 0]
+    per_pixel = np.add.reduceat(tgts.double().cpu().numpy(), starts)
+    np.testing.assert_allclose(per_pixel, img[..., 3].reshape(-1)[counts > 0], rtol=0, atol=2e-6)
+    # and logging the same view again gives the same records in the same places
+    feats2, tgts2, seen2 = proposal.log_segments(ctx, [cam], tf, p, capacity=1 << 20,
+                                                 keep_prob=1.0)
+    assert seen2 == seen and torch.equal(feats2, feats) and torch.equal(tgts2, tgts)
     f = feats.cpu().numpy()
     t = tgts.cpu().numpy()
     assert np.all((t >= 0) & (t <= 1))
